@@ -1,0 +1,336 @@
+// Reference oracle: simulated annealing tomography.  TEST INFRASTRUCTURE ONLY
+// (see oracle.h).  FP64 throughout; follows Steps 1-4 of Sec. II-A in the
+// paper's order, with the PILA update of Eq. (6), the cost update of Eq. (7)
+// and the best-of-multiple-estimates rule of Sec. III-B.
+//
+// Readings where the paper is silent (each also listed in the design notes):
+//  * Random stream: Philox4x32-10 keyed by the chain seed, counter
+//    (stage, move, block, stream id 1).  Draw d = 4*block + word; d = 0 picks
+//    the pixel (floor(x * M / 2^32) over the mask list in raster order),
+//    d = 1 is the acceptance number N1, d = 2 + c is estimate c's uniform.
+//    A uniform is ((x >> 9) * 2 + 1) * 2^-24, exact in FP32 and FP64.
+//  * Eq. (3) with its redraw rule is the uniform law on
+//    [max(0, f - beta), min(beta, f + beta)]: one draw, same distribution.
+//  * All N_e estimates are values at the pixel drawn for the move.
+//  * Step 4 with dC == 0 accepts; with T == 0 only dC <= 0 is accepted.
+//  * Stage s = 0..S-1 runs at T_s of the chosen schedule (T_N itself is the
+//    limit that is never run).
+//  * Eq. (8): proposals from the initial image (stream id 2, counter
+//    (try, 0, block, 2)), single estimate, first Q with C' > C.
+#include "oracle.h"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+const uint32_t kStreamSat = 1u;
+const uint32_t kStreamT0 = 2u;
+
+double uniform01(uint32_t x) { return (double)((x >> 9) * 2u + 1u) * 0x1p-24; }
+
+uint32_t pick(uint32_t x, uint32_t m) { return (uint32_t)(((uint64_t)x * (uint64_t)m) >> 32); }
+
+void draw_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t stream, int nblk, uint32_t* w) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int b = 0; b < nblk; ++b) {
+        const uint32_t ctr[4] = {c0, c1, (uint32_t)b, stream};
+        or_philox4x32_10(ctr, key, w + 4 * b);
+    }
+}
+
+struct Problem {
+    int n = 0, U = 0, B = 0;
+    std::vector<int32_t> bins;   // PILA, Eq. (5)
+    std::vector<double> lens;
+    std::vector<double> pc;      // calculated projections P_c
+    const double* pm = nullptr;  // measured projections P_m
+    std::vector<int32_t> list;   // pixels that may be chosen
+    double inv_BU = 0.0;
+    double C = 0.0;              // current cost, Eq. (4)
+};
+
+int setup(Problem& pb, const or_geom* g, const uint8_t* mask, const double* pm, const double* image) {
+    pb.n = g->n;
+    pb.U = g->n_angles;
+    pb.B = g->n_bins;
+    const size_t P = (size_t)pb.n * pb.n;
+    pb.bins.assign(P * pb.U * 2, -1);
+    pb.lens.assign(P * pb.U * 2, 0.0);
+    if (or_pila(g, pb.bins.data(), pb.lens.data()) != 0) return -1;
+    pb.pc.assign((size_t)pb.U * pb.B, 0.0);
+    if (or_drt(g, image, pb.pc.data()) != 0) return -1;  // initial projections by the DRT
+    pb.pm = pm;
+    pb.list.clear();
+    for (size_t p = 0; p < P; ++p)
+        if (!mask || mask[p]) pb.list.push_back((int32_t)p);
+    pb.inv_BU = 1.0 / ((double)pb.U * pb.B);
+    pb.C = or_cost(pb.U, pb.B, pb.pc.data(), pm);
+    return 0;
+}
+
+// Eq. (7) summand total for a change df at pixel p:
+//   sum_u { 2 [P_c - P_m](alpha_u, k_u) * df * l_u + (df * l_u)^2 }.
+// Also returns the magnitude of its terms for tolerance bookkeeping.
+double eq7_sum(const Problem& pb, int p, double df, double* scale) {
+    double sum = 0.0, mag_rl = 0.0, l2 = 0.0;
+    const size_t base = (size_t)p * pb.U * 2;
+    for (int u = 0; u < pb.U; ++u) {
+        for (int slot = 0; slot < 2; ++slot) {
+            const size_t e = base + (size_t)u * 2 + slot;
+            const double l = pb.lens[e];
+            if (l == 0.0) continue;
+            const size_t cell = (size_t)u * pb.B + pb.bins[e];
+            const double r = pb.pc[cell] - pb.pm[cell];
+            sum += 2.0 * r * df * l + (df * l) * (df * l);
+            mag_rl += std::fabs(r * l);
+            l2 += l * l;
+        }
+    }
+    if (scale) *scale = 2.0 * std::fabs(df) * mag_rl + df * df * l2;
+    return sum;
+}
+
+// Eq. (6): P'_c(alpha_u, k_u) = P_c(alpha_u, k_u) + df * l_u.
+void eq6_apply(Problem& pb, int p, double df) {
+    const size_t base = (size_t)p * pb.U * 2;
+    for (int u = 0; u < pb.U; ++u)
+        for (int slot = 0; slot < 2; ++slot) {
+            const size_t e = base + (size_t)u * 2 + slot;
+            if (pb.lens[e] == 0.0) continue;
+            pb.pc[(size_t)u * pb.B + pb.bins[e]] += df * pb.lens[e];
+        }
+}
+
+double cost_after(const Problem& pb, double sum) {
+    return std::sqrt(std::fmax(0.0, pb.C * pb.C + sum * pb.inv_BU));  // Eq. (7)
+}
+
+int t0_estimate(const Problem& pb, const double* image, const or_sat_params* prm, double* t0, int32_t* found) {
+    const int Q = prm->t0_samples > 0 ? prm->t0_samples : 200;
+    const int64_t max_tries = 100LL * Q;
+    double total = 0.0;
+    int got = 0;
+    if (!pb.list.empty()) {
+        for (int64_t t = 0; t < max_tries && got < Q; ++t) {
+            uint32_t w[4];
+            draw_words(prm->seed, (uint32_t)t, 0u, kStreamT0, 1, w);
+            const int p = pb.list[pick(w[0], (uint32_t)pb.list.size())];
+            const double f = image[p];
+            const double lo = std::fmax(0.0, f - prm->beta), hi = std::fmin(prm->beta, f + prm->beta);
+            const double fc = lo + uniform01(w[2]) * (hi - lo);
+            const double Cp = cost_after(pb, eq7_sum(pb, p, fc - f, nullptr));
+            const double dC = Cp - pb.C;
+            if (dC > 0.0) {
+                total += dC;
+                ++got;
+            }
+        }
+    }
+    *found = got;
+    // Eq. (8): T0 = -sum(C' - C) / (Q ln 0.9), Q = samples actually found.
+    *t0 = got > 0 ? -total / ((double)got * std::log(0.9)) : 0.0;
+    return 0;
+}
+
+struct Choice {
+    int cstar;
+    double fbest, dfbest, sum_best, Cp_best, scale_best, gap;
+};
+
+// Sec. III-B: evaluate the N_e estimates and keep the one with the smallest
+// cost C' (the lowest index wins a tie).  gap is how far the runner-up's
+// Eq. (7) sum lies above the winner's.
+Choice best_estimate(const Problem& pb, int p, double f, const uint32_t* w, const or_sat_params* prm,
+                     std::vector<double>* sums_out) {
+    const int K = prm->bome_k;
+    const double lo = std::fmax(0.0, f - prm->beta), hi = std::fmin(prm->beta, f + prm->beta);
+    std::vector<double> local;
+    std::vector<double>& sums = sums_out ? *sums_out : local;
+    sums.assign(K, 0.0);
+    std::vector<double> fcs(K), scales(K), cps(K);
+    for (int c = 0; c < K; ++c) {
+        fcs[c] = lo + uniform01(w[2 + c]) * (hi - lo);
+        sums[c] = eq7_sum(pb, p, fcs[c] - f, &scales[c]);
+        cps[c] = cost_after(pb, sums[c]);
+    }
+    int best = 0;
+    for (int c = 1; c < K; ++c)
+        if (cps[c] < cps[best]) best = c;
+    double second = INFINITY;
+    for (int c = 0; c < K; ++c)
+        if (c != best && sums[c] < second) second = sums[c];
+    return Choice{best, fcs[best], fcs[best] - f, sums[best], cps[best], scales[best], second - sums[best]};
+}
+
+}  // namespace
+
+extern "C" double or_schedule_temp(int32_t schedule, double t0, double tn, int32_t s, int32_t n_sweeps) {
+    const double N = (double)n_sweeps, n = (double)s;
+    switch (schedule) {
+        case OR_SCHED_GEOMETRIC:  // T_n = T0 (T_N / T0)^(n/N)
+            if (t0 <= 0.0) return 0.0;
+            return t0 * std::pow(tn / t0, n / N);
+        case OR_SCHED_CUBIC:  // T_n = T0 - n^3 (T0 - T_N) / N^3, Eq. (9)
+            return t0 - n * n * n * (t0 - tn) / (N * N * N);
+        default:  // T_n = T0 - n (T0 - T_N) / N, Eq. (2)
+            return t0 - n * (t0 - tn) / N;
+    }
+}
+
+extern "C" int or_sat_t0(const or_geom* g, const uint8_t* mask, const double* pm, const double* image,
+                         const or_sat_params* prm, double* t0_out, int32_t* found_out) {
+    Problem pb;
+    if (setup(pb, g, mask, pm, image) != 0) return -1;
+    return t0_estimate(pb, image, prm, t0_out, found_out);
+}
+
+extern "C" int or_sat_run(const or_geom* g, const uint8_t* mask, const double* pm, double* image,
+                          const or_sat_params* prm, or_sat_stats* stats, or_trace_rec* trace) {
+    if (prm->bome_k < 1 || prm->bome_k > 32 || prm->n_sweeps < 0) return -2;
+    Problem pb;
+    if (setup(pb, g, mask, pm, image) != 0) return -1;
+    or_sat_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.initial_cost = pb.C;
+    // Step 1: the cooling schedule.
+    double t0 = prm->t0;
+    if (t0 <= 0.0) {
+        if (t0_estimate(pb, image, prm, &t0, &st.t0_found) != 0) return -1;
+    }
+    const double tn = prm->tn < 0.0 ? t0 / 1000.0 : prm->tn;
+    st.t0 = t0;
+    st.tn = tn;
+    const int64_t M = prm->moves_per_sweep > 0 ? prm->moves_per_sweep : (int64_t)pb.list.size();
+    const int nblk = (prm->bome_k + 2 + 3) / 4;
+    std::vector<uint32_t> w(4 * nblk);
+    int64_t rec = 0;
+    for (int s = 0; s < prm->n_sweeps && !pb.list.empty(); ++s) {
+        const double T = or_schedule_temp(prm->schedule, t0, tn, s, prm->n_sweeps);
+        for (int64_t m = 0; m < M; ++m) {
+            // Step 2: a random pixel and N_e candidate values for it.
+            draw_words(prm->seed, (uint32_t)s, (uint32_t)m, kStreamSat, nblk, w.data());
+            const int p = pb.list[pick(w[0], (uint32_t)pb.list.size())];
+            const double f = image[p];
+            // Step 3 + BoME: the estimate with the smallest cost, by Eq. (7).
+            const Choice ch = best_estimate(pb, p, f, w.data(), prm, nullptr);
+            const double dC = ch.Cp_best - pb.C;
+            // Step 4: Metropolis acceptance.
+            const double n1 = uniform01(w[1]);
+            const bool accept = (dC <= 0.0) || (T > 0.0 && n1 < std::exp(-dC / T));
+            ++st.proposed;
+            if (accept) {
+                ++st.accepted;
+                image[p] = ch.fbest;
+                eq6_apply(pb, p, ch.dfbest);
+                pb.C = ch.Cp_best;
+            }
+            if (trace) {
+                or_trace_rec& tr = trace[rec++];
+                tr.pixel = p;
+                tr.cstar = ch.cstar;
+                tr.accepted = accept ? 1 : 0;
+                tr.pad = 0;
+                tr.dS = ch.sum_best;
+                tr.dC = dC;
+                tr.fnew = image[p];
+                tr.u_acc = n1;
+                tr.temp = T;
+                tr.scale_S = ch.scale_best;
+                tr.gap_S = ch.gap;
+            }
+        }
+    }
+    st.final_cost = pb.C;
+    std::vector<double> fresh((size_t)pb.U * pb.B);
+    if (or_drt(g, image, fresh.data()) != 0) return -1;
+    st.final_cost_fresh = or_cost(pb.U, pb.B, fresh.data(), pm);
+    if (stats) *stats = st;
+    return 0;
+}
+
+extern "C" int or_sat_lockstep(const or_geom* g, const uint8_t* mask, const double* pm, double* image,
+                               const or_sat_params* prm, double t0, double tn, const or_gpu_trace* trace,
+                               int64_t n_moves, double tol, or_lockstep_report* rep) {
+    if (prm->bome_k < 1 || prm->bome_k > 32) return -2;
+    Problem pb;
+    if (setup(pb, g, mask, pm, image) != 0) return -1;
+    or_lockstep_report r;
+    r.moves = 0;
+    r.near_ties = 0;
+    r.pixel_mismatch = -1;
+    r.hard_mismatch = -1;
+    r.max_err_dS = 0.0;
+    r.max_err_dC = 0.0;
+    r.max_err_f = 0.0;
+    const int64_t M = prm->moves_per_sweep > 0 ? prm->moves_per_sweep : (int64_t)pb.list.size();
+    const int nblk = (prm->bome_k + 2 + 3) / 4;
+    std::vector<uint32_t> w(4 * nblk);
+    std::vector<double> sums;
+    int64_t idx = 0;
+    for (int s = 0; s < prm->n_sweeps && idx < n_moves && !pb.list.empty(); ++s) {
+        const double T = or_schedule_temp(prm->schedule, t0, tn, s, prm->n_sweeps);
+        for (int64_t m = 0; m < M && idx < n_moves; ++m, ++idx) {
+            const or_gpu_trace& gt = trace[idx];
+            draw_words(prm->seed, (uint32_t)s, (uint32_t)m, kStreamSat, nblk, w.data());
+            const int p = pb.list[pick(w[0], (uint32_t)pb.list.size())];
+            if (p != gt.pixel) {
+                r.pixel_mismatch = idx;
+                goto done;
+            }
+            {
+                const double f = image[p];
+                Choice ch = best_estimate(pb, p, f, w.data(), prm, &sums);
+                int c = ch.cstar;
+                if (gt.cstar != c) {
+                    // BoME near-tie: the other side's pick is within tolerance of ours.
+                    if (gt.cstar < 0 || gt.cstar >= prm->bome_k) {
+                        r.hard_mismatch = idx;
+                        goto done;
+                    }
+                    const double gap = sums[gt.cstar] - sums[c];
+                    if (gap > 2.0 * tol * ch.scale_best) {
+                        r.hard_mismatch = idx;
+                        goto done;
+                    }
+                    ++r.near_ties;
+                    c = gt.cstar;
+                }
+                const double lo = std::fmax(0.0, f - prm->beta), hi = std::fmin(prm->beta, f + prm->beta);
+                const double fc = lo + uniform01(w[2 + c]) * (hi - lo);
+                double scale = 0.0;
+                const double sum = eq7_sum(pb, p, fc - f, &scale);
+                const double Cp = cost_after(pb, sum);
+                const double dC = Cp - pb.C;
+                const double denom = Cp + pb.C;
+                const double scale_C = denom > 0.0 ? scale * pb.inv_BU / denom : std::sqrt(scale * pb.inv_BU);
+                if (scale > 0.0) r.max_err_dS = std::fmax(r.max_err_dS, std::fabs((double)gt.dS - sum) / scale);
+                if (scale_C > 0.0) r.max_err_dC = std::fmax(r.max_err_dC, std::fabs((double)gt.dC - dC) / scale_C);
+                const double n1 = uniform01(w[1]);
+                bool accept = (dC <= 0.0) || (T > 0.0 && n1 < std::exp(-dC / T));
+                if ((gt.accepted != 0) != accept) {
+                    // Acceptance near-tie: dC within tolerance of the threshold
+                    // T * (-ln N1), or of 0 when T == 0.
+                    const double thr = T > 0.0 ? -T * std::log(n1) : 0.0;
+                    if (std::fabs(dC - thr) > 2.0 * tol * scale_C && std::fabs(dC) > 2.0 * tol * scale_C) {
+                        r.hard_mismatch = idx;
+                        goto done;
+                    }
+                    ++r.near_ties;
+                    accept = gt.accepted != 0;
+                }
+                if (accept) {
+                    image[p] = fc;
+                    eq6_apply(pb, p, fc - f);
+                    pb.C = Cp;
+                }
+                r.max_err_f = std::fmax(r.max_err_f, std::fabs((double)gt.fnew - image[p]));
+            }
+        }
+    }
+done:
+    r.moves = idx;
+    if (rep) *rep = r;
+    return 0;
+}
