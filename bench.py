@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: SAT pixel-moves/s on the batched workload.
+
+Workload (per GPU): 512 independent 128x128 slices (20 seeded random
+ellipses each, disk reconstruction space, uniform 0.5 start), 120 angles over
+[0, 180), 181 bins, noiseless sinograms, BoME with 4 estimates, 50 linear
+stages with T0 from Eq. (8), FP16 PILA, all chains in one persistent launch.
+A step is one pass of the whole path over that batch: PILA build, FP64-grade
+resync, Eq. (8) temperatures, 50 stages of moves, final resync and cost.
+Metric: pixel-moves/s (one BoME selection + Metropolis decision = one move),
+whole job.  Also reported: the plain single-chain FP32 form on a sample of
+the same slices at equal final RMSE, the roofline of the sweep kernel, the
+CPU reference oracle on a bounded sample, and the end-to-end rate through the
+C-ABI with host buffers.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1411_4622_gb300 import synth  # noqa: E402
+
+WORKLOAD = "batch128x512"
+METRIC = "SAT pixel-moves/s at equal final RMSE (batched vs plain); slice p50/p99 ms"
+UNIT = "pixel-moves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--slices", type=int, default=None, help="override slices per GPU (testing)")
+    ap.add_argument("--sweeps", type=int, default=None, help="override stages (testing)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def workload(args):
+    cfg = dict(synth.WORKLOADS[WORKLOAD])
+    if args.slices:
+        cfg["slices"] = args.slices
+    if args.sweeps:
+        cfg["n_sweeps"] = args.sweeps
+    return cfg
+
+
+def make_slices(cfg, first, count):
+    n = cfg["n"]
+    mask = synth.disk_mask(n)
+    phantoms = np.stack([synth.phantom(n, cfg["ellipses"], synth.slice_seeds(first + i)[0]) * mask
+                         for i in range(count)])
+    return phantoms, mask
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(cfg, budget_s=12.0):
+    """The FP64 oracle as it stands, single-threaded, on one slice of the
+    workload; stages chosen so the sample runs for roughly budget_s."""
+    import oracle
+
+    oracle.build()
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
+    ph, mask = make_slices(cfg, 0, 1)
+    pm = oracle.drt(ph[0], U, B)
+    img0 = synth.initial_image(n, 0.5, mask)
+    kw = dict(bome_k=cfg["bome_k"], mask=mask, seed=synth.slice_seeds(0)[2], beta=cfg["beta"])
+    t = time.perf_counter()
+    oracle.sat_run(pm, img0, n_sweeps=1, **kw)
+    probe = time.perf_counter() - t
+    stages = int(max(1, min(cfg["n_sweeps"] * 4, budget_s / max(probe, 1e-3))))
+    t = time.perf_counter()
+    _, st, _ = oracle.sat_run(pm, img0, n_sweeps=stages, **kw)
+    dt = time.perf_counter() - t
+    return {"value": st["proposed"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 slice of {WORKLOAD}, {stages} stages x {st['proposed'] // stages} moves, "
+                      f"K={cfg['bome_k']}, FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, cfg):
+    import oracle
+
+    oracle.build()
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
+    ph, mask = make_slices(cfg, 0, 1)
+    pm = oracle.drt(ph[0], U, B)
+    img0 = synth.initial_image(n, 0.5, mask)
+    kw = dict(bome_k=cfg["bome_k"], mask=mask, seed=synth.slice_seeds(0)[2], beta=cfg["beta"])
+    stages = 4
+    times, moves = [], 0
+    for it in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        _, st, _ = oracle.sat_run(pm, img0, n_sweeps=stages, **kw)
+        dt = time.perf_counter() - t
+        if it >= args.warmup:
+            times.append(dt)
+            moves = st["proposed"]
+    ms = 1e3 * statistics.mean(times)
+    value = moves / (ms / 1e3)
+    sample = f"1 slice of {WORKLOAD}, {stages} stages per step, K={cfg['bome_k']}, FP64 oracle, single thread"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    cfg = workload(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, cfg)
+        return
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n, U, B, K, S = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"]
+    slices = cfg["slices"]
+    phantoms, mask = make_slices(cfg, rank * slices, slices)
+    P = n * n
+
+    # Inputs: sinograms from the phantoms through an FP32 PILA (FP64-grade projection).
+    pf = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    sino = api.pila_forward(pf, torch.tensor(phantoms, dtype=torch.float32, device="cuda")).float().contiguous()
+    init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * slices), dtype=torch.float32,
+                        device="cuda")
+    images = init.clone()
+    seed0 = synth.slice_seeds(rank * slices)[2]
+    run_kw = dict(bome_k=K, n_sweeps=S, t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    info = {}
+
+    def step():
+        images.copy_(init)
+        p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+        st = api.sat_run(p, sino, images, **run_kw)
+        if not info:
+            info.update(api.pila_info(p))
+        api.pila_free(p)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, sweep_ms = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        sweep_ms.append(st[0]["sweep_ms"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    M = int(mask.sum())
+    moves_per_step = slices * S * M
+    value = world * moves_per_step / (ms / 1e3)
+    acc = sum(s["accepted"] for s in st) / max(1, sum(s["proposed"] for s in st))
+    final = images.cpu().numpy()
+    rmse_batched = np.array([synth.rmse(final[i], phantoms[i], mask) for i in range(slices)])
+
+    # Plain form: single chain at a time, FP32 PILA, on a sample of the same slices.
+    plain_n = min(4, slices)
+    plain_imgs, plain_ms = [], 0.0
+    for i in range(plain_n):
+        im = init[i:i + 1].clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kw = dict(run_kw)
+        kw["seed"] = seed0 + i
+        e0.record(stream)
+        api.sat_run(pf, sino[i:i + 1], im, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        plain_imgs.append(im.cpu().numpy()[0])
+    rmse_plain = np.array([synth.rmse(plain_imgs[i], phantoms[i], mask) for i in range(plain_n)])
+    plain = {"value": plain_n * S * M / (plain_ms / 1e3), "unit": UNIT, "slices": plain_n, "precision": "f32",
+             "rmse_rel_diff_max": float(np.max(np.abs(rmse_batched[:plain_n] - rmse_plain) / rmse_plain))}
+
+    # End to end through the C-ABI with host (pinned) buffers.
+    sino_h = sino.cpu().pin_memory()
+    img_h = init.cpu().pin_memory()
+    e2e_ms = []
+    for it in range(2):
+        work = img_h.clone().pin_memory()
+        t = time.perf_counter()
+        p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+        api.sat_run(p, sino_h, work, **run_kw)
+        api.pila_free(p)
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e = {"value": world * moves_per_step / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sino_h.numel() * 4 + img_h.numel() * 4),
+           "d2h_bytes_per_step": int(img_h.numel() * 4)}
+
+    # Roofline of the sweep kernel (algorithmic bytes per move).
+    peak, peak_kind = peaks()
+    E = info["entries"] / P
+    bytes_per_move = info["row_records"] * info["record_bytes"] + 4 * E * (1 + acc) + 4 * (1 + acc)
+    achieved = bytes_per_move * moves_per_step / (statistics.mean(sweep_ms) / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind, "kernel": "sat_sweep_kernel",
+            "bytes_per_move": bytes_per_move, "sweep_ms": statistics.mean(sweep_ms)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "slices_per_gpu": slices, "n": n, "angles": U, "bins": B,
+                      "bome_k": K, "stages": S, "moves_per_stage": M, "pila": "f16",
+                      "l2": "flushed between timed steps (256 MB write)"},
+           "evaluations_per_s": value * K, "acceptance": acc,
+           "rmse": {"batched_mean": float(rmse_batched.mean())}, "plain": plain,
+           "latency_ms": {"slice_p50": ms, "slice_p99": max(step_ms)},
+           "e2e": e2e, "roofline": roof, "clocks": clk,
+           "gpu_launches": args.steps * (1 + 2 + 2 + 1 + 1 + 1)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    api.pila_free(pf)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

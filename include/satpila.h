@@ -1,0 +1,223 @@
+/*
+ * satpila — simulated annealing tomography with a pre-calculated intersection
+ * lengths array (PILA), for NVIDIA GB300 (sm_103a).
+ *
+ * Method: Vo, Breese & Moser, "Feasibility of Simulated Annealing Tomography".
+ * Section and equation numbers below refer to that paper.
+ *
+ * Conventions for every call
+ *  - Return value: SATPILA_OK (0) or a negative SATPILA_ERR_* code;
+ *    satpila_last_error() then returns a message for the calling thread.
+ *  - Geometry (parallel beam, unit pixels, Sec. II-B): pixel (i, j) of an
+ *    n x n image (row i from the top) has its centre at
+ *    x = j - (n-1)/2, y = (n-1)/2 - i.  Angle u is theta_u (default pi*u/U).
+ *    Ray (u, k) is the line x cos(theta_u) + y sin(theta_u) = s_k,
+ *    s_k = k - (B-1)/2, i.e. B unit-width bins centred on the axis.  A ray
+ *    exactly on a pixel edge (0 and 90 degrees only) belongs to the pixel on
+ *    its +s side.
+ *  - Layouts: images are row-major float32 [n][n]; sinograms are angle-major
+ *    [U][B]; batches are contiguous ([n_chains][U][B], [n_chains][n][n]).
+ *  - Buffers are owned by the caller.  Data pointers may be device pointers
+ *    (e.g. from torch) or host pointers; host buffers are staged through
+ *    device memory inside the call, which then returns only after the
+ *    results are back on the host.  With device buffers the call is
+ *    asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream)
+ *    except where stated.
+ *  - Handles (satpila_pila, satpila_server) are owned by the library and are
+ *    released with their *_free / *_destroy call.
+ */
+#ifndef SATPILA_H
+#define SATPILA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SATPILA_OK 0
+#define SATPILA_ERR_INVALID_ARG (-1)
+#define SATPILA_ERR_OOM (-2)
+#define SATPILA_ERR_CUDA (-3)
+#define SATPILA_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define SATPILA_ERR_BOUNDS (-5)    /* a device-side index check failed */
+#define SATPILA_ERR_BUSY (-6)      /* serving: no slot or memory free right now */
+#define SATPILA_ERR_NOT_FOUND (-7) /* serving: unknown ticket */
+#define SATPILA_ERR_PENDING (-8)   /* serving: result not ready yet */
+
+/* Thread-local message for the last failing call (never NULL). */
+const char* satpila_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int satpila_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* PILA: Eq. (5) and the surrounding text of Sec. II-B.                       */
+/* ------------------------------------------------------------------------ */
+
+#define PILA_F32 0 /* record: int32 bin0, int32 bin1, float len0, float len1 (16 B) */
+#define PILA_F16 1 /* record: int16 bin0, int16 bin1, half len0, half len1 (8 B)    */
+
+typedef struct satpila_pila satpila_pila;
+
+typedef struct {
+    int32_t n;                /* image side, >= 1 */
+    int32_t n_angles;         /* U, >= 1 */
+    int32_t n_bins;           /* B, >= 1 (<= 32767 for PILA_F16) */
+    const double* angles_rad; /* host, U angles; NULL: theta_u = pi*u/U */
+    const uint8_t* mask;      /* host, n*n reconstruction space (Sec. III, Fig. 2(c));
+                                 NULL: every pixel.  Moves pick pixels from it and
+                                 the SIRT factor matrix sums over it. */
+} pila_geom;
+
+typedef struct {
+    int32_t n, n_angles, n_bins, precision;
+    int32_t n_mask;        /* pixels in the reconstruction space */
+    int32_t record_bytes;  /* 16 or 8 */
+    int32_t row_records;   /* records stored per pixel (U, or U rounded up to even for F16) */
+    int32_t pad;
+    int64_t table_bytes;   /* device bytes of the record table */
+    int64_t entries;       /* non-empty (bin, length) pairs */
+} pila_info_t;
+
+/*
+ * Build the PILA (Eq. (5), Sec. II-B): for every pixel and angle, the detector
+ * bins whose rays cross the pixel and the exact intersection lengths.  Eq. (5)
+ * stores one {k_u, l_u} per angle; a unit pixel can meet two unit-spaced rays
+ * of one angle, so each record holds up to two entries on consecutive bins
+ * (bin1 = bin0 + 1), sorted by bin.  An empty entry has length 0 and a bin
+ * that is safe to index.  Lengths come from the closed-form chord of a unit
+ * square (computed in FP64, then rounded to the record's precision); entries
+ * shorter than 1e-12 or on bins outside [0, B) are dropped.
+ * Layout in device memory: pixel-major, angle-contiguous [n*n][row_records].
+ * Also builds the reconstruction-space pixel list and (lazily) the SIRT
+ * factor matrix.  Synchronous: returns when the table is built.
+ * Errors: INVALID_ARG (sizes, precision, B > 32767 with F16), OOM, CUDA.
+ */
+int pila_build(const pila_geom* g, int32_t precision, void* stream, satpila_pila** out);
+/* Release a PILA built by pila_build (NULL is a no-op). */
+int pila_free(satpila_pila* p);
+/* Sizes of a built PILA. */
+int pila_info(const satpila_pila* p, pila_info_t* info);
+/*
+ * Copy the table out in a precision-independent form: bins [n*n][U][2]
+ * (int32; -1 for an empty entry) and lens [n*n][U][2] (float32, the stored
+ * value dequantised).  Host or device outputs.  Synchronous.
+ */
+int pila_export(const satpila_pila* p, int32_t* bins, float* lens, void* stream);
+/*
+ * Forward projection through the PILA, i.e. the DRT of Eq. (1) with the
+ * stored lengths: sino[i][u][k] = sum over pixels p of images[i][p] * l.
+ * Accumulated exactly in 64-bit fixed point (order-independent, hence
+ * deterministic) and returned as float64 [n_images][U][B].
+ */
+int pila_forward(const satpila_pila* p, int32_t n_images, const float* images, double* sino, void* stream);
+/*
+ * SIRT factor matrix of Sec. III-D: w[u][k] = sum over reconstruction-space
+ * pixels of l^2 along ray (u, k), as float64 [U][B].
+ */
+int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Simulated annealing: Steps 1-4 of Sec. II-A, Eqs. (2)-(4), (6)-(9), BoME.  */
+/* ------------------------------------------------------------------------ */
+
+#define SAT_SCHED_LINEAR 0    /* Eq. (2) */
+#define SAT_SCHED_GEOMETRIC 1 /* T0 (TN/T0)^(n/N), the second Eq. (8) */
+#define SAT_SCHED_CUBIC 2     /* Eq. (9) */
+
+#define SAT_RESIDENT_AUTO 0   /* pick by size (and the autotuner when enabled) */
+#define SAT_RESIDENT_SMEM 1   /* residual sinogram in shared memory */
+#define SAT_RESIDENT_GLOBAL 2 /* residual sinogram in global memory (L2) */
+
+#define SAT_FLAG_NO_GRAPH 1u  /* launch kernels directly instead of a cached CUDA graph */
+#define SAT_FLAG_AUTOTUNE 2u  /* time the launch candidates once per shape and keep the best */
+
+typedef struct {
+    int32_t pixel;     /* pixel index i*n + j */
+    int32_t cstar;     /* chosen estimate (BoME) */
+    int32_t accepted;  /* Step 4 outcome */
+    int32_t pad;
+    float dS;          /* the Eq. (7) sum (before 1/(B*U)) of the chosen estimate */
+    float dC;          /* C' - C of the chosen estimate */
+    float fnew;        /* pixel value after the move */
+    float pad2;
+} sat_trace_rec;
+
+typedef struct {
+    float beta;              /* pixel values live in [0, beta] (Eq. (3)); > 0 */
+    int32_t bome_k;          /* estimates per move N_e (Sec. III-B), 1..32 */
+    int32_t n_sweeps;        /* temperature stages N (each of M moves) */
+    int32_t moves_per_sweep; /* M; 0: the number of reconstruction-space pixels */
+    double t0;               /* T0; <= 0: estimated per chain by Eq. (8) */
+    double tn;               /* T_N; < 0: T0 / 1000 */
+    int32_t schedule;        /* SAT_SCHED_* */
+    int32_t t0_samples;      /* Q of Eq. (8); 0: 200 */
+    uint64_t seed;           /* chain c uses Philox key seed + c */
+    int32_t resync_every;    /* FP64 resync of the residual every this many sweeps; 0: only at the end */
+    int32_t residency;       /* SAT_RESIDENT_* */
+    uint32_t flags;          /* SAT_FLAG_* */
+    int32_t trace_chain;     /* chain whose moves are recorded, or -1 */
+    sat_trace_rec* trace;    /* n_sweeps*M records for trace_chain (host or device), or NULL */
+    double* sweep_cost;      /* [n_chains][n_sweeps] cost after each sweep (host or device), or NULL */
+} sat_params;
+
+typedef struct {
+    double t0, tn;            /* temperatures used */
+    double initial_cost;      /* Eq. (4) of the initial image, FP64 */
+    double final_cost;        /* Eq. (4) of the final image, from a fresh FP64 projection */
+    double final_cost_incremental; /* the cost carried by Eq. (7) just before the final resync */
+    double max_resync_drift;  /* max |incremental residual - fresh residual| over all resyncs */
+    int64_t accepted, proposed;
+    int32_t t0_found;         /* uphill samples found for Eq. (8) (0 if T0 was given) */
+    int32_t status;           /* 0, or a SATPILA_ERR_* raised on the device */
+    double sweep_ms;          /* device time of the sweep kernels of this call (same for every chain),
+                                 from CUDA events on `stream` */
+} sat_stats;
+
+/*
+ * Anneal n_chains independent slices that share one PILA.  Chain c reads its
+ * measured sinogram sino_meas[c] ([U][B]) and anneals images[c] ([n][n]) in
+ * place from the given initial estimate.  Every move: pick a pixel of the
+ * reconstruction space, draw bome_k candidate values (Eq. (3)), evaluate each
+ * by Eq. (7) on the residual P_c - P_m, keep the best (BoME), accept by the
+ * Metropolis rule of Step 4 at the stage temperature, and on acceptance apply
+ * Eq. (6) to the residual.  Each chain is strictly sequential; parallelism is
+ * over angles (within a warp), estimates, and chains.
+ * Random numbers: Philox4x32-10, key = seed + c, counter (stage, move, block,
+ * 1); draw 0 picks the pixel, draw 1 is N1, draw 2 + e is estimate e.
+ * stats (host, n_chains entries, may be NULL) are filled before return; the
+ * call synchronizes `stream` at its end.
+ * Errors: INVALID_ARG, OOM, CUDA; TIMEOUT/BOUNDS if a device-side check fired
+ * (also reported per chain in stats.status).
+ */
+int sat_run(const satpila_pila* p, int32_t n_chains, const float* sino_meas, float* images,
+            const sat_params* prm, sat_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* SIRT with PILA: Eqs. (10)-(11), Sec. III-D.                                */
+/* ------------------------------------------------------------------------ */
+
+#define SIRT_SIMULTANEOUS 0 /* all pixels from the same P_c (classic SIRT) */
+#define SIRT_SEQUENTIAL 1   /* pixel by pixel in raster order over the reconstruction
+                               space, each update written into P_c through the PILA */
+
+typedef struct {
+    int32_t n_iter; /* passes N over the reconstruction space */
+    int32_t mode;   /* SIRT_* */
+    float relax;    /* multiplies the Eq. (10) increment; 1 reproduces the paper */
+    int32_t pad;
+} sirt_params;
+
+/*
+ * n_slices independent SIRT reconstructions sharing the PILA.  costs (host or
+ * device, [n_slices][n_iter], may be NULL) receives Eq. (4) after each pass.
+ * Synchronizes `stream` at its end.
+ */
+int sirt_run(const satpila_pila* p, int32_t n_slices, const float* sino_meas, float* images,
+             const sirt_params* prm, double* costs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SATPILA_H */

@@ -1,0 +1,166 @@
+"""Python binding of the satpila C-ABI: argument marshalling only.
+
+Every call forwards to libsatpila.so with the same name.  Arrays may be torch
+tensors (CUDA or CPU) or numpy arrays; device tensors are passed as device
+pointers, everything else as host pointers (the library stages host data).
+Streams default to torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import (PILA_F16, PILA_F32, SAT_FLAG_AUTOTUNE, SAT_FLAG_NO_GRAPH, SAT_RESIDENT_AUTO,  # noqa: F401
+                   SAT_RESIDENT_GLOBAL, SAT_RESIDENT_SMEM, SAT_SCHED_CUBIC, SAT_SCHED_GEOMETRIC,
+                   SAT_SCHED_LINEAR, SIRT_SEQUENTIAL, SIRT_SIMULTANEOUS, SatpilaError)
+
+TRACE_DTYPE = np.dtype([("pixel", "<i4"), ("cstar", "<i4"), ("accepted", "<i4"), ("pad", "<i4"),
+                        ("dS", "<f4"), ("dC", "<f4"), ("fnew", "<f4"), ("pad2", "<f4")])
+
+
+def _is_tensor(x) -> bool:
+    return hasattr(x, "data_ptr") and hasattr(x, "is_contiguous")
+
+
+def _ptr(x, dtype=None):
+    if x is None:
+        return None
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(x.dtype).replace("torch.", "") != np.dtype(dtype).name:
+            raise TypeError(f"expected {np.dtype(dtype).name}, got {x.dtype}")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != np.dtype(dtype):
+            raise TypeError(f"expected {np.dtype(dtype).name}, got {x.dtype}")
+        return x.ctypes.data_as(C.c_void_p)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    try:
+        import torch
+
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Pila:
+    """Owns a PILA handle; released by pila_free (or on garbage collection)."""
+
+    def __init__(self, handle, n, n_angles, n_bins, precision):
+        self.handle = handle
+        self.n, self.n_angles, self.n_bins, self.precision = n, n_angles, n_bins, precision
+
+    def close(self):
+        if self.handle:
+            L.load().pila_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pila_build(n, n_angles, n_bins, precision=PILA_F32, angles=None, mask=None, stream=None) -> Pila:
+    lib = L.load()
+    g = L.PilaGeom(int(n), int(n_angles), int(n_bins), None, None)
+    keep = []
+    if angles is not None:
+        a = np.ascontiguousarray(angles, dtype=np.float64)
+        keep.append(a)
+        g.angles_rad = a.ctypes.data_as(C.POINTER(C.c_double))
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        keep.append(m)
+        g.mask = m.ctypes.data_as(C.POINTER(C.c_uint8))
+    h = C.c_void_p()
+    L.check(lib.pila_build(C.byref(g), int(precision), _stream(stream), C.byref(h)))
+    return Pila(h, int(n), int(n_angles), int(n_bins), int(precision))
+
+
+def pila_free(p: Pila) -> None:
+    p.close()
+
+
+def pila_info(p: Pila) -> dict:
+    info = L.PilaInfo()
+    L.check(L.load().pila_info(p.handle, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in L.PilaInfo._fields_ if f != "pad"}
+
+
+def pila_export(p: Pila, bins=None, lens=None, stream=None):
+    """(bins [n*n, U, 2] int32 with -1 for empty, lens [n*n, U, 2] float32);
+    bins/lens may be given (host arrays or device tensors)."""
+    P = p.n * p.n
+    if bins is None:
+        bins = np.zeros((P, p.n_angles, 2), dtype=np.int32)
+    if lens is None:
+        lens = np.zeros((P, p.n_angles, 2), dtype=np.float32)
+    L.check(L.load().pila_export(p.handle, _ptr(bins, np.int32), _ptr(lens, np.float32), _stream(stream)))
+    return bins, lens
+
+
+def pila_forward(p: Pila, images, out=None, stream=None):
+    """DRT (Eq. (1)) through the PILA, float64 [n_images, U, B]."""
+    n_img = int(images.shape[0]) if images.ndim == 3 else 1
+    if out is None:
+        if _is_tensor(images) and images.is_cuda:
+            import torch
+
+            out = torch.empty((n_img, p.n_angles, p.n_bins), dtype=torch.float64, device=images.device)
+        else:
+            out = np.zeros((n_img, p.n_angles, p.n_bins), dtype=np.float64)
+    L.check(L.load().pila_forward(p.handle, n_img, _ptr(images, np.float32), _ptr(out, np.float64),
+                                  _stream(stream)))
+    return out
+
+
+def pila_sirt_factor(p: Pila, stream=None) -> np.ndarray:
+    w = np.zeros((p.n_angles, p.n_bins), dtype=np.float64)
+    L.check(L.load().pila_sirt_factor(p.handle, _ptr(w), _stream(stream)))
+    return w
+
+
+def sat_params(*, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn=-1.0,
+               schedule=SAT_SCHED_LINEAR, t0_samples=200, seed=0, resync_every=0,
+               residency=SAT_RESIDENT_AUTO, flags=0, trace_chain=-1, trace=None, sweep_cost=None):
+    return L.SatParams(float(beta), int(bome_k), int(n_sweeps), int(moves_per_sweep), float(t0), float(tn),
+                       int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(resync_every),
+                       int(residency), int(flags), int(trace_chain), _ptr(trace), _ptr(sweep_cost))
+
+
+def sat_run(p: Pila, sino_meas, images, stream=None, **kw) -> list[dict]:
+    """Anneal images (in place) against sino_meas; returns per-chain stats.
+
+    sino_meas: float32 [n_chains, U, B]; images: float32 [n_chains, n, n].
+    Keyword arguments are the fields of sat_params (trace: a buffer of
+    TRACE_DTYPE records or a byte tensor of the same size; sweep_cost:
+    float64 [n_chains, n_sweeps])."""
+    n_chains = int(images.shape[0]) if images.ndim == 3 else 1
+    prm = sat_params(**kw)
+    stats = (L.SatStats * max(n_chains, 1))()
+    L.check(L.load().sat_run(p.handle, n_chains, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
+                             C.byref(prm), C.cast(stats, C.c_void_p), _stream(stream)))
+    return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
+
+
+def sirt_run(p: Pila, sino_meas, images, *, n_iter=1, mode=SIRT_SIMULTANEOUS, relax=1.0, costs=None,
+             stream=None) -> None:
+    """SIRT with PILA (Eqs. (10)-(11)); images updated in place."""
+    n_sl = int(images.shape[0]) if images.ndim == 3 else 1
+    prm = L.SirtParams(int(n_iter), int(mode), float(relax), 0)
+    L.check(L.load().sirt_run(p.handle, n_sl, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
+                              C.byref(prm), _ptr(costs, np.float64), _stream(stream)))

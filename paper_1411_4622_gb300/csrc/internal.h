@@ -1,0 +1,91 @@
+// Host-side internals of libsatpila shared between translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "satpila.h"
+
+struct satpila_pila {
+    int device = 0;
+    int n = 0, U = 0, B = 0, precision = PILA_F32;
+    int record_bytes = 16;
+    int row_records = 0;      // records per pixel row
+    int64_t row_bytes = 0;    // row_records * record_bytes (multiple of 16)
+    int64_t table_bytes = 0;
+    int64_t entries = 0;
+    int n_mask = 0;
+    unsigned char* d_table = nullptr;  // [P][row_records] records
+    int32_t* d_list = nullptr;         // reconstruction-space pixels, raster order
+    uint8_t* d_mask = nullptr;         // [P]
+    double* d_cos = nullptr;           // [U]
+    double* d_sin = nullptr;           // [U]
+    double* d_w64 = nullptr;           // SIRT factor matrix [U][B], built on first use
+    float* d_w32 = nullptr;
+};
+
+namespace satpila {
+
+// Thread-local last-error message.
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SP_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ::satpila::cuda_fail(e_, #call); \
+    } while (0)
+
+// True if p is a device (or managed) pointer usable by kernels.
+bool is_device_pointer(const void* p);
+
+// ---- projector (fixed-point forward projection through the PILA) ----------
+
+enum ProjMode { PROJ_FORWARD = 0, PROJ_RESYNC = 1, PROJ_FACTOR = 2, PROJ_SIRT = 3 };
+
+struct ProjArgs {
+    const unsigned char* table;
+    int f16;
+    int row_records;
+    int n, U, B;
+    int angles_per_group, n_groups;
+    int mode;
+    int drift;                  // RESYNC: compare with the residual being replaced
+    const float* img;           // FORWARD/RESYNC/SIRT images
+    long long img_stride;
+    const uint8_t* mask;        // FACTOR pixel weights
+    double* out64;              // FORWARD [item][U][B]; FACTOR [U][B]
+    long long out_stride;
+    float* out32;               // FACTOR: float copy [U][B]
+    const float* pm;            // RESYNC/SIRT measured sinograms
+    long long pm_stride;
+    float* resid;               // RESYNC: residual P_c - P_m; SIRT: correction
+    long long resid_stride;
+    const float* w;             // SIRT: factor matrix (float)
+    double* part_sq;            // [item][group] sum of (P_c - P_m)^2
+    float* part_drift;          // [item][group]
+};
+
+int projector_smem_bytes(int angles_per_group, int B);
+int projector_plan(int U, int B, int* angles_per_group, int* n_groups);
+cudaError_t launch_projector(const ProjArgs& a, int n_items, cudaStream_t s);
+
+// Sums the per-group partials of a RESYNC/SIRT projection in a fixed order.
+struct ReduceArgs {
+    int n_items, n_groups;
+    const double* part_sq;
+    const float* part_drift;    // may be NULL
+    double inv_cells;           // 1 / (B*U)
+    double* S_out;              // per item sum of squares (may be NULL)
+    double* cost_out;           // per item Eq. (4) cost (may be NULL)
+    long long cost_stride;
+    double* drift_max;          // per item running max (may be NULL)
+};
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);
+
+// Builds the SIRT factor matrix of a PILA on first use.
+int ensure_factor(satpila_pila* p, cudaStream_t s);
+
+}  // namespace satpila

@@ -1,0 +1,232 @@
+// PILA construction (Eq. (5), Sec. II-B) and the table-level API calls.
+//
+// One thread per (pixel, angle) record.  The chord of a line through a unit
+// square depends only on its distance t to the square's centre along the
+// line's normal: with a = |cos|, b = |sin|, the square projects onto the
+// normal as a trapezoid of half-width (a+b)/2, flat top of half-width
+// |a-b|/2 and height 1/max(a,b).  The rays crossing the pixel are the bins
+// whose centre lies in [s_p - (a+b)/2, s_p + (a+b)/2) (half-open, so a ray
+// on an edge belongs to the pixel on its +s side); since a+b <= sqrt(2) < 2
+// there are at most two, on consecutive bins.  FP64 arithmetic, rounded once
+// to the record's precision.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace satpila {
+namespace {
+
+__global__ void pila_build_kernel(unsigned char* table, int f16, int row_records, int n, int U, int B,
+                                  const double* cs, const double* sn, unsigned long long* entries) {
+    const long long total = (long long)n * n * row_records;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
+    int kk[2] = {0, 0};
+    double ll[2] = {0.0, 0.0};
+    if (idx < total) {
+        const int p = (int)(idx / row_records), u = (int)(idx % row_records);
+        if (u < U) {
+            const double c = cs[u], s = sn[u];
+            const double a = fabs(c), b = fabs(s);
+            const int i = p / n, j = p % n;
+            const double x = (double)j - 0.5 * (n - 1), y = 0.5 * (n - 1) - (double)i;
+            const double sp = x * c + y * s;
+            const double half = 0.5 * (a + b), flat = 0.5 * fabs(a - b);
+            const double height = 1.0 / fmax(a, b), ab = a * b;
+            const double centre = 0.5 * (B - 1);
+            const double kfirst = ceil(sp - half + centre);
+            for (int t = 0; t < 2; ++t) {
+                const double kd = kfirst + t;
+                const double d = (kd - centre) - sp;
+                if (d < -half || d >= half) continue;
+                const double dist = fabs(d);
+                const double l = dist <= flat ? height : (half - dist) / ab;
+                if (!(l >= 1e-12)) continue;
+                if (kd < 0.0 || kd >= (double)B) continue;
+                kk[cnt] = (int)kd;
+                ll[cnt] = l;
+                ++cnt;
+            }
+        }
+        if (cnt == 0) kk[0] = kk[1] = 0;
+        if (cnt == 1) kk[1] = kk[0];
+        if (f16) {
+            const __half h0 = __double2half(ll[0]), h1 = __double2half(ll[1]);
+            const uint32_t bins = ((uint32_t)(uint16_t)kk[0]) | ((uint32_t)(uint16_t)kk[1] << 16);
+            const uint32_t lens = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+            reinterpret_cast<uint2*>(table)[idx] = make_uint2(bins, lens);
+            cnt = (__half2float(h0) != 0.0f) + (__half2float(h1) != 0.0f);
+        } else {
+            const float f0 = (float)ll[0], f1 = (float)ll[1];
+            reinterpret_cast<uint4*>(table)[idx] =
+                make_uint4((uint32_t)kk[0], (uint32_t)kk[1], __float_as_uint(f0), __float_as_uint(f1));
+            cnt = (f0 != 0.0f) + (f1 != 0.0f);
+        }
+    }
+    // warp-level count of non-empty entries
+    unsigned c = (unsigned)cnt;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(entries, (unsigned long long)c);
+}
+
+__global__ void pila_export_kernel(const unsigned char* table, int f16, int row_records, int U, long long P,
+                                   int32_t* bins, float* lens) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= P * U) return;
+    const long long p = idx / U;
+    const int u = (int)(idx % U);
+    const long long rec = p * row_records + u;
+    Entry2 e = f16 ? decode_f16(reinterpret_cast<const uint2*>(table)[rec].x,
+                                reinterpret_cast<const uint2*>(table)[rec].y)
+                   : decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
+    bins[idx * 2] = e.l0 != 0.0f ? e.k0 : -1;
+    bins[idx * 2 + 1] = e.l1 != 0.0f ? e.k1 : -1;
+    lens[idx * 2] = e.l0;
+    lens[idx * 2 + 1] = e.l1;
+}
+
+}  // namespace
+}  // namespace satpila
+
+using namespace satpila;
+
+extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, satpila_pila** out) {
+    if (!g || !out) return fail(SATPILA_ERR_INVALID_ARG, "pila_build: null argument");
+    *out = nullptr;
+    if (g->n < 1 || g->n_angles < 1 || g->n_bins < 1)
+        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: n, n_angles and n_bins must be >= 1");
+    if (precision != PILA_F32 && precision != PILA_F16)
+        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: precision must be PILA_F32 or PILA_F16");
+    if (precision == PILA_F16 && g->n_bins > 32767)
+        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: PILA_F16 needs n_bins <= 32767");
+    if ((long long)g->n * g->n > (1LL << 30))
+        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: image too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto* p = new satpila_pila();
+    cudaGetDevice(&p->device);
+    p->n = g->n;
+    p->U = g->n_angles;
+    p->B = g->n_bins;
+    p->precision = precision;
+    p->record_bytes = precision == PILA_F16 ? 8 : 16;
+    p->row_records = precision == PILA_F16 ? (p->U + 1) / 2 * 2 : p->U;
+    p->row_bytes = (int64_t)p->row_records * p->record_bytes;
+    const long long P = (long long)p->n * p->n;
+    p->table_bytes = P * p->row_bytes;
+
+    // angle tables (FP64, exact zeros for |v| < 1e-12)
+    std::vector<double> cs(p->U), sn(p->U);
+    for (int u = 0; u < p->U; ++u) {
+        const double th = g->angles_rad ? g->angles_rad[u] : M_PI * (double)u / (double)p->U;
+        cs[u] = std::cos(th);
+        sn[u] = std::sin(th);
+        if (std::fabs(cs[u]) < 1e-12) cs[u] = 0.0;
+        if (std::fabs(sn[u]) < 1e-12) sn[u] = 0.0;
+    }
+    // reconstruction-space list
+    std::vector<uint8_t> mask(P, 1);
+    std::vector<int32_t> list;
+    list.reserve(P);
+    for (long long q = 0; q < P; ++q) {
+        if (g->mask) mask[q] = g->mask[q] ? 1 : 0;
+        if (mask[q]) list.push_back((int32_t)q);
+    }
+    p->n_mask = (int)list.size();
+
+    auto cleanup = [&](int code, const std::string& msg) {
+        pila_free(p);
+        return fail(code, msg);
+    };
+    unsigned long long* d_entries = nullptr;
+    if (cudaMalloc(&p->d_table, p->table_bytes) != cudaSuccess ||
+        cudaMalloc(&p->d_list, std::max<size_t>(1, list.size()) * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&p->d_mask, P) != cudaSuccess || cudaMalloc(&p->d_cos, p->U * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&p->d_sin, p->U * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d_entries, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (d_entries) cudaFree(d_entries);
+        return cleanup(SATPILA_ERR_OOM, "pila_build: device allocation failed");
+    }
+    cudaError_t e = cudaSuccess;
+    if (!list.empty())
+        e = cudaMemcpyAsync(p->d_list, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_mask, mask.data(), P, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_cos, cs.data(), p->U * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_sin, sn.data(), p->U * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_entries, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        const long long total = P * p->row_records;
+        const int threads = 256;
+        const long long blocks = (total + threads - 1) / threads;
+        pila_build_kernel<<<(unsigned)blocks, threads, 0, s>>>(p->d_table, precision == PILA_F16, p->row_records,
+                                                                p->n, p->U, p->B, p->d_cos, p->d_sin, d_entries);
+        e = cudaGetLastError();
+    }
+    unsigned long long entries = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&entries, d_entries, sizeof(entries), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_entries);
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("pila_build: ") + cudaGetErrorString(e);
+        return cleanup(SATPILA_ERR_CUDA, msg);
+    }
+    p->entries = (int64_t)entries;
+    *out = p;
+    return SATPILA_OK;
+}
+
+extern "C" int pila_free(satpila_pila* p) {
+    if (!p) return SATPILA_OK;
+    cudaFree(p->d_table);
+    cudaFree(p->d_list);
+    cudaFree(p->d_mask);
+    cudaFree(p->d_cos);
+    cudaFree(p->d_sin);
+    cudaFree(p->d_w64);
+    cudaFree(p->d_w32);
+    delete p;
+    return SATPILA_OK;
+}
+
+extern "C" int pila_info(const satpila_pila* p, pila_info_t* info) {
+    if (!p || !info) return fail(SATPILA_ERR_INVALID_ARG, "pila_info: null argument");
+    info->n = p->n;
+    info->n_angles = p->U;
+    info->n_bins = p->B;
+    info->precision = p->precision;
+    info->n_mask = p->n_mask;
+    info->record_bytes = p->record_bytes;
+    info->row_records = p->row_records;
+    info->pad = 0;
+    info->table_bytes = p->table_bytes;
+    info->entries = p->entries;
+    return SATPILA_OK;
+}
+
+extern "C" int pila_export(const satpila_pila* p, int32_t* bins, float* lens, void* stream) {
+    if (!p || !bins || !lens) return fail(SATPILA_ERR_INVALID_ARG, "pila_export: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long P = (long long)p->n * p->n;
+    const size_t cnt = (size_t)P * p->U * 2;
+    const bool dev_b = is_device_pointer(bins), dev_l = is_device_pointer(lens);
+    int32_t* db = bins;
+    float* dl = lens;
+    if (!dev_b) SP_CUDA(cudaMalloc(&db, cnt * sizeof(int32_t)));
+    if (!dev_l) SP_CUDA(cudaMalloc(&dl, cnt * sizeof(float)));
+    const long long total = P * p->U;
+    pila_export_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p->d_table, p->precision == PILA_F16,
+                                                                       p->row_records, p->U, P, db, dl);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dev_b) e = cudaMemcpyAsync(bins, db, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !dev_l) e = cudaMemcpyAsync(lens, dl, cnt * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (!dev_b) cudaFree(db);
+    if (!dev_l) cudaFree(dl);
+    if (e != cudaSuccess) return cuda_fail(e, "pila_export");
+    return SATPILA_OK;
+}

@@ -1,0 +1,69 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads without a GPU,
+exports every function include/*.h declares, and rejects bad arguments on the
+host before touching a device."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_4622_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+char\s*\*|int)\s+(\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1411_4622_gb300 import _lib
+
+    names = declared_functions()
+    assert len(names) >= 10
+    assert names == set(_lib.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.satpila_version() >= 10000
+
+
+def test_host_side_argument_checks(lib):
+    from paper_1411_4622_gb300 import _lib
+
+    out = C.c_void_p()
+    g = _lib.PilaGeom(0, 10, 11, None, None)
+    assert lib.pila_build(C.byref(g), 0, None, C.byref(out)) == _lib.ERR_INVALID_ARG
+    assert b"n_angles" in lib.satpila_last_error() or b">= 1" in lib.satpila_last_error()
+    g = _lib.PilaGeom(8, 10, 11, None, None)
+    assert lib.pila_build(C.byref(g), 7, None, C.byref(out)) == _lib.ERR_INVALID_ARG
+    g = _lib.PilaGeom(8, 10, 40000, None, None)
+    assert lib.pila_build(C.byref(g), _lib.PILA_F16, None, C.byref(out)) == _lib.ERR_INVALID_ARG
+    prm = _lib.SatParams()
+    assert lib.sat_run(None, 1, None, None, C.byref(prm), None, None) == _lib.ERR_INVALID_ARG
+    sp = _lib.SirtParams(1, 5, 1.0, 0)
+    assert lib.sirt_run(None, 1, None, None, C.byref(sp), None, None) == _lib.ERR_INVALID_ARG
+    assert lib.pila_free(None) == 0
+
+
+def test_struct_layouts_match_header():
+    from paper_1411_4622_gb300 import _lib
+
+    # sizes the C compiler gives these structs on LP64
+    assert C.sizeof(_lib.SatTraceRec) == 32
+    assert C.sizeof(_lib.PilaInfo) == 48
+    assert C.sizeof(_lib.SatParams) == 80
+    assert C.sizeof(_lib.PilaGeom) == 32
+    assert C.sizeof(_lib.SatStats) == 80

@@ -1,0 +1,356 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on
+the same seeded inputs.  Tolerances:
+  * PILA bins bit-exact; FP32 lengths within 1e-6 relative (+1e-9 absolute,
+    entries shorter than 1e-9 are edge grazes and may be absent on one side);
+    FP16 lengths within half an FP16 ulp (2^-11 relative + 6e-8);
+  * per-move Eq. (7) sums within 1e-5 of the magnitude of their terms
+    (2|df| sum|r l| + df^2 sum l^2) in FP32 mode; accept decisions identical
+    except recorded near-ties (the oracle's own margin below 2e-5 of the
+    term magnitude);
+  * final image RMSE against the phantom within 2% of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_4622_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_4622_gb300 import api as a
+    from paper_1411_4622_gb300 import build
+
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    return a
+
+
+def dev(x, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda").contiguous()
+
+
+def compact(bins, lens, floor):
+    """Drop entries shorter than floor and left-align the two slots."""
+    b = np.where(lens > floor, bins, -1).astype(np.int64)
+    l = np.where(lens > floor, lens, 0.0).astype(np.float64)
+    move = (b[..., 0] < 0) & (b[..., 1] >= 0)
+    b[move, 0], l[move, 0] = b[move, 1], l[move, 1]
+    b[move, 1], l[move, 1] = -1, 0.0
+    return b, l
+
+
+GEOMS = [(64, 90, 91, None), (37, 45, 53, None), (16, 7, 23, None), (5, 3, 7, None), (1, 4, 1, None),
+         (24, 33, 35, "random")]
+
+
+@pytest.mark.parametrize("n,U,B,ang", GEOMS)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pila_matches_oracle(api, n, U, B, ang, prec):
+    angles = None
+    if ang == "random":
+        angles = np.sort(np.random.default_rng(3).uniform(0, np.pi, U))
+    ob, ol = oracle.pila(n, U, B, angles)
+    p = api.pila_build(n, U, B, prec, angles=angles)
+    gb, gl = api.pila_export(p)
+    info = api.pila_info(p)
+    assert info["record_bytes"] == (8 if prec else 16)
+    ob_, ol_ = compact(ob, ol, 1e-9)
+    gb_, gl_ = compact(gb, gl.astype(np.float64), 1e-9)
+    if prec == 0:
+        assert np.array_equal(ob_, gb_)
+        assert np.all(np.abs(gl_ - ol_) <= 1e-6 * ol_ + 1e-9)
+    else:
+        # an FP16 length can flush to zero only below 2^-25
+        ok = (ob_ == gb_) | ((gb_ < 0) & (ol_ < 3e-8))
+        assert np.all(ok)
+        assert np.all(np.abs(gl_ - ol_) <= 2.0**-11 * ol_ + 6e-8)
+    assert info["entries"] == int((gl > 0).sum())
+    api.pila_free(p)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pila_full_size_sampled_rays(api, prec):
+    """512^2, 360 angles, 725 bins: sampled rays traversed by the oracle one
+    by one against the device table (gathered on the device)."""
+    n, U, B = 512, 360, 725
+    p = api.pila_build(n, U, B, prec)
+    P = n * n
+    bins = torch.empty((P, U, 2), dtype=torch.int32, device="cuda")
+    lens = torch.empty((P, U, 2), dtype=torch.float32, device="cuda")
+    api.pila_export(p, bins, lens)
+    rng = np.random.default_rng(11)
+    for _ in range(120):
+        u, k = int(rng.integers(U)), int(rng.integers(B))
+        pix, ln = oracle.siddon_ray(n, math.pi * u / U, k - 0.5 * (B - 1))
+        keep = ln > 1e-9
+        pix, ln = pix[keep], ln[keep]
+        if len(pix) == 0:
+            continue
+        pt = torch.tensor(pix, dtype=torch.long, device="cuda")
+        gb = bins[pt, u].cpu().numpy()
+        gl = lens[pt, u].cpu().numpy().astype(np.float64)
+        hit = gb == k
+        assert np.all(hit.sum(axis=1) == 1), (u, k)
+        got = (gl * hit).sum(axis=1)
+        tol = (1e-6 * ln + 1e-9) if prec == 0 else (2.0**-11 * ln + 6e-8)
+        assert np.all(np.abs(got - ln) <= tol)
+        # and no other pixel of this ray's angle claims bin k: total count check
+    api.pila_free(p)
+    del bins, lens
+    torch.cuda.empty_cache()
+
+
+def test_forward_projection(api):
+    n, U, B = 64, 90, 91
+    rng = np.random.default_rng(5)
+    img = rng.random((2, n, n)).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F32)
+    out = api.pila_forward(p, dev(img))
+    got = out.cpu().numpy()
+    gb, gl = api.pila_export(p)
+    # exact FP64 sum over the stored lengths
+    want = np.zeros((2, U, B))
+    for s in range(2):
+        ok = gl[:, :, s] > 0
+        pp, uu = np.nonzero(ok)
+        for i in range(2):
+            np.add.at(want[i], (uu, gb[pp, uu, s]), img[i].reshape(-1)[pp].astype(np.float64) * gl[pp, uu, s])
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    # against the oracle's ray-driven DRT (FP32 length rounding only)
+    for i in range(2):
+        drt = oracle.drt(img[i].astype(np.float64), U, B)
+        assert np.max(np.abs(got[i] - drt)) <= 2e-7 * np.max(np.abs(drt))
+    # host input/output path
+    h = api.pila_forward(p, img)
+    assert np.array_equal(h, got)
+    api.pila_free(p)
+
+
+def test_sirt_factor(api):
+    n, U = 48, 30
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    w = api.pila_sirt_factor(p)
+    want = oracle.sirt_factor(n, U, B, mask)
+    assert np.max(np.abs(w - want)) <= 1e-6 * np.max(want)
+    api.pila_free(p)
+
+
+def _plain64():
+    cfg = synth.WORKLOADS["plain64"]
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
+    ph = synth.phantom(n, cfg["ellipses"], 1000)
+    pm = oracle.drt(ph, U, B)
+    return cfg, n, U, B, ph, pm
+
+
+def _run_traced(api, p, pm, img0, S, M, **kw):
+    U, B = pm.shape
+    n = img0.shape[0]
+    trace = torch.zeros(S * M * 32, dtype=torch.uint8, device="cuda")
+    img = dev(img0).reshape(1, n, n)
+    st = api.sat_run(p, dev(pm).reshape(1, U, B), img, n_sweeps=S, trace_chain=0, trace=trace, **kw)
+    tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
+    return st[0], tr, img.cpu().numpy()[0]
+
+
+def test_sat_lockstep_plain64(api):
+    """The plain 64^2 workload (90 angles, K=1, T0=1e-2 -> 0, 20 stages):
+    every move compared with the oracle."""
+    cfg, n, U, B, ph, pm = _plain64()
+    img0 = np.full((n, n), 0.5)
+    p = api.pila_build(n, U, B, api.PILA_F32)
+    S, M = cfg["n_sweeps"], n * n
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=1, t0=cfg["t0"], tn=cfg["tn"], seed=3000,
+                              resync_every=1)
+    assert st["status"] == 0 and st["proposed"] == S * M
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=1, n_sweeps=S, seed=3000)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5 and rep["max_err_dC"] <= 1e-5, rep
+    assert rep["near_ties"] <= 1e-3 * S * M, rep
+    assert st["max_resync_drift"] <= 1e-4 * np.max(np.abs(pm))
+    api.pila_free(p)
+
+
+@pytest.mark.parametrize("K,res", [(8, 0), (8, 2), (32, 2), (3, 0)])
+def test_sat_lockstep_bome_with_mask(api, K, res):
+    """256^2-geometry slice (180 angles, 363 bins) with the disk reconstruction
+    space, Gaussian noise, BoME, T0 by Eq. (8): two stages in lockstep."""
+    n, U, B = 256, 180, 363
+    ph = synth.phantom(n, 20, 1001)
+    mask = synth.disk_mask(n)
+    pm = synth.gaussian_noise(oracle.drt(ph, U, B), 0.01, 2001)
+    img0 = synth.initial_image(n, 0.5, mask)
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    S, M = 2, 6000
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=K, t0=-1.0, tn=-1.0, seed=3001, moves_per_sweep=M,
+                              residency=res)
+    t0, found = oracle.sat_t0(pm, img0, seed=3001, mask=mask)
+    assert found == st["t0_found"] == 200
+    assert abs(st["t0"] - t0) <= 1e-4 * t0
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=K, n_sweeps=S, seed=3001,
+                                 moves_per_sweep=M, mask=mask)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5, rep
+    api.pila_free(p)
+
+
+def test_sat_batched_equals_single_and_residency_identical(api):
+    n, U = 48, 40
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    sinos = np.stack([oracle.drt(synth.phantom(n, 6, 50 + i), U, B) for i in range(5)]).astype(np.float32)
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * 5).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    kw = dict(bome_k=4, n_sweeps=6, t0=-1.0, tn=-1.0, resync_every=2)
+    outs = {}
+    for res in (1, 2):
+        imgs = dev(img0)
+        st = api.sat_run(p, dev(sinos), imgs, seed=77, residency=res, **kw)
+        outs[res] = (imgs.cpu().numpy(), [s["accepted"] for s in st], [s["final_cost"] for s in st])
+    assert np.array_equal(outs[1][0], outs[2][0]) and outs[1][1] == outs[2][1]
+    for c in (0, 3):
+        one = dev(img0[c:c + 1])
+        st = api.sat_run(p, dev(sinos[c:c + 1]), one, seed=77 + c, **kw)
+        assert np.array_equal(one.cpu().numpy()[0], outs[1][0][c])
+        assert st[0]["accepted"] == outs[1][1][c]
+    api.pila_free(p)
+
+
+def test_sat_final_rmse_plain64_vs_oracle(api):
+    cfg, n, U, B, ph, pm = _plain64()
+    img0 = np.full((n, n), 0.5)
+    p = api.pila_build(n, U, B, api.PILA_F32)
+    img = dev(img0).reshape(1, n, n)
+    st = api.sat_run(p, dev(pm).reshape(1, U, B), img, bome_k=1, n_sweeps=cfg["n_sweeps"], t0=cfg["t0"],
+                     tn=cfg["tn"], seed=3000)
+    oimg, ost, _ = oracle.sat_run(pm, img0, bome_k=1, n_sweeps=cfg["n_sweeps"], t0=cfg["t0"], tn=cfg["tn"],
+                                  seed=3000)
+    r_gpu = synth.rmse(img.cpu().numpy()[0], ph)
+    r_orc = synth.rmse(oimg, ph)
+    assert abs(r_gpu - r_orc) <= 0.02 * r_orc, (r_gpu, r_orc)
+    assert abs(st[0]["final_cost"] - ost["final_cost_fresh"]) <= 0.02 * ost["final_cost_fresh"]
+    api.pila_free(p)
+
+
+def test_sat_f16_rmse_vs_oracle(api):
+    """128^2 slice of the batched workload shape with the FP16 PILA: final
+    RMSE within 2% of the FP64 oracle's (which uses exact lengths)."""
+    n, U, B = 128, 120, 181
+    ph = synth.phantom(n, 20, 1002)
+    mask = synth.disk_mask(n)
+    pm = oracle.drt(ph, U, B)
+    img0 = synth.initial_image(n, 0.5, mask)
+    kw = dict(bome_k=4, n_sweeps=8, t0=-1.0, tn=-1.0, seed=3002)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    img = dev(img0).reshape(1, n, n)
+    api.sat_run(p, dev(pm).reshape(1, U, B), img, **kw)
+    oimg, ost, _ = oracle.sat_run(pm, img0, mask=mask, **kw)
+    r_gpu, r_orc = synth.rmse(img.cpu().numpy()[0], ph, mask), synth.rmse(oimg, ph, mask)
+    assert abs(r_gpu - r_orc) <= 0.02 * r_orc, (r_gpu, r_orc)
+    api.pila_free(p)
+
+
+def test_sat_edge_cases(api):
+    n, U = 9, 7
+    B = synth.bins_for(n)
+    pm = oracle.drt(synth.phantom(n, 3, 9), U, B)
+    p = api.pila_build(n, U, B, api.PILA_F32)
+    img0 = np.full((n, n), 0.5)
+    # no stages: image unchanged, final cost = initial cost
+    img = dev(img0).reshape(1, n, n)
+    st = api.sat_run(p, dev(pm).reshape(1, U, B), img, n_sweeps=0)
+    assert np.array_equal(img.cpu().numpy()[0], img0.astype(np.float32))
+    assert st[0]["final_cost"] == st[0]["initial_cost"] and st[0]["proposed"] == 0
+    # one move per stage, K = 32, in lockstep
+    st, tr, _ = _run_traced(api, p, pm, img0, 3, 1, bome_k=32, t0=1e-3, tn=1e-5, seed=5, moves_per_sweep=1)
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=32, n_sweeps=3, seed=5,
+                                 moves_per_sweep=1)
+    assert rep["moves"] == 3 and rep["hard_mismatch"] == -1 and rep["pixel_mismatch"] == -1
+    # empty reconstruction space: nothing moves
+    q = api.pila_build(n, U, B, api.PILA_F32, mask=np.zeros((n, n), np.uint8))
+    img = dev(img0).reshape(1, n, n)
+    st = api.sat_run(q, dev(pm).reshape(1, U, B), img, n_sweeps=2, t0=-1.0)
+    assert st[0]["proposed"] == 0 and st[0]["t0_found"] == 0
+    assert np.array_equal(img.cpu().numpy()[0], img0.astype(np.float32))
+    # invalid arguments come back as errors
+    with pytest.raises(api.SatpilaError):
+        api.sat_run(p, dev(pm).reshape(1, U, B), dev(img0).reshape(1, n, n), bome_k=33)
+    with pytest.raises(api.SatpilaError):
+        api.sat_run(p, dev(pm).reshape(1, U, B), dev(img0).reshape(1, n, n), beta=0.0)
+    # 1x1 image
+    one = api.pila_build(1, 5, 1, api.PILA_F32)
+    pm1 = oracle.drt(np.full((1, 1), 0.3), 5, 1)
+    st, tr, im = _run_traced(api, one, pm1, np.full((1, 1), 0.9), 4, 50, bome_k=2, t0=1e-3, tn=1e-4, seed=1,
+                             moves_per_sweep=50)
+    _, rep = oracle.sat_lockstep(pm1, np.full((1, 1), 0.9), tr, t0=st["t0"], tn=st["tn"], bome_k=2, n_sweeps=4,
+                                 seed=1, moves_per_sweep=50)
+    assert rep["hard_mismatch"] == -1 and abs(im[0, 0] - 0.3) < 0.05
+    for h in (p, q, one):
+        api.pila_free(h)
+
+
+def test_sat_host_buffers_match_device(api):
+    n, U = 32, 30
+    B = synth.bins_for(n)
+    pm = oracle.drt(synth.phantom(n, 5, 4), U, B).astype(np.float32).reshape(1, U, B)
+    img0 = np.full((1, n, n), 0.5, dtype=np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F16)
+    kw = dict(bome_k=4, n_sweeps=3, seed=9)
+    h = img0.copy()
+    api.sat_run(p, pm, h, **kw)
+    d = dev(img0)
+    api.sat_run(p, dev(pm), d, **kw)
+    assert np.array_equal(h, d.cpu().numpy())
+    api.pila_free(p)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sirt_vs_oracle(api, mode):
+    n, U = 32, 45
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, 6, 21) * mask
+    pm = oracle.drt(ph, U, B)
+    img0 = synth.initial_image(n, 0.5, mask)
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    img = dev(img0).reshape(1, n, n)
+    costs = torch.zeros((1, 6), dtype=torch.float64, device="cuda")
+    api.sirt_run(p, dev(pm).reshape(1, U, B), img, n_iter=6, mode=mode, costs=costs)
+    oimg, oc = oracle.sirt_run(pm, img0, 6, mode=mode, mask=mask)
+    assert np.max(np.abs(img.cpu().numpy()[0] - oimg)) <= 2e-5 * max(1.0, np.max(np.abs(oimg)))
+    assert np.allclose(costs.cpu().numpy()[0], oc, rtol=1e-4)
+    api.pila_free(p)
+
+
+def test_resync_drift_bound_512(api):
+    """One stage of the 512^2 precision workload shape (360 angles, 725
+    bins, Poisson noise) with the residual in global memory: the
+    incremental residual stays within 1e-4 * max|P_m| of a fresh one."""
+    n, U, B = 512, 360, 725
+    mask = synth.disk_mask(n)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    ph = synth.phantom(n, 40, 1003)
+    clean = api.pila_forward(p, dev(ph[None])).cpu().numpy()[0]
+    pm = synth.poisson_noise(clean, 1e5, 2003).astype(np.float32)
+    img = dev(synth.initial_image(n, 0.5, mask)).reshape(1, n, n)
+    st = api.sat_run(p, dev(pm).reshape(1, U, B), img, bome_k=8, n_sweeps=1, moves_per_sweep=100000, seed=3003,
+                     resync_every=1)
+    assert st[0]["status"] == 0
+    assert st[0]["max_resync_drift"] <= 1e-4 * float(np.max(np.abs(pm)))
+    assert abs(st[0]["final_cost_incremental"] - st[0]["final_cost"]) <= 1e-4 * st[0]["final_cost"]
+    assert st[0]["final_cost"] < st[0]["initial_cost"]
+    api.pila_free(p)
