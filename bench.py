@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=None, help="override slices per GPU (testing)")
     ap.add_argument("--sweeps", type=int, default=None, help="override stages (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     return ap.parse_args()
 
 
@@ -215,7 +216,8 @@ def main():
                         device="cuda")
     images = init.clone()
     seed0 = synth.slice_seeds(rank * slices)[2]
-    run_kw = dict(bome_k=K, n_sweeps=S, t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0)
+    run_kw = dict(bome_k=K, n_sweeps=S, t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0,
+                  residency=args.residency)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     info = {}

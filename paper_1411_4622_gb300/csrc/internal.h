@@ -63,6 +63,7 @@ struct ProjArgs {
     long long pm_stride;
     float* resid;               // RESYNC: residual P_c - P_m; SIRT: correction
     long long resid_stride;
+    int resid_pitch;            // row pitch of resid (B when 0)
     const float* w;             // SIRT: factor matrix (float)
     double* part_sq;            // [item][group] sum of (P_c - P_m)^2
     float* part_drift;          // [item][group]

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
             case PROJ_RESYNC: {
                 const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
                 const float rf = (float)r;
-                float* dst = a.resid + (long long)item * a.resid_stride + cell;
+                const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
+                float* dst = a.resid + (long long)item * a.resid_stride + (long long)(u0 + ul) * pitch + k;
                 if (a.drift) drift = fmaxf(drift, fabsf(rf - *dst));
                 *dst = rf;
                 sq += r * r;

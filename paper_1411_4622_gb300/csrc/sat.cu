@@ -22,12 +22,41 @@
 
 namespace satpila {
 
-cudaError_t launch_sweep_f32(bool smem, int jmax, const SatArgs& a, int grid, int warps, size_t smem_bytes,
-                             cudaStream_t s);
-cudaError_t launch_sweep_f16(bool smem, int jmax, const SatArgs& a, int grid, int warps, size_t smem_bytes,
-                             cudaStream_t s);
-int sweep_blocks_per_sm_f32(bool smem, int jmax, int warps, size_t smem_bytes);
-int sweep_blocks_per_sm_f16(bool smem, int jmax, int warps, size_t smem_bytes);
+using SweepFn = void (*)(const SatArgs);
+SweepFn sweep_kernel_f32_smem(int jmax, int kmax);
+SweepFn sweep_kernel_f32_glob(int jmax, int kmax);
+SweepFn sweep_kernel_f16_smem(int jmax, int kmax);
+SweepFn sweep_kernel_f16_glob(int jmax, int kmax);
+
+namespace {
+
+SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax) {
+    if (f16) return smem ? sweep_kernel_f16_smem(jmax, kmax) : sweep_kernel_f16_glob(jmax, kmax);
+    return smem ? sweep_kernel_f32_smem(jmax, kmax) : sweep_kernel_f32_glob(jmax, kmax);
+}
+
+int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : 32; }
+
+cudaError_t launch_sweep(bool f16, bool smem, int jmax, int kmax, const SatArgs& a, int grid, int warps,
+                         size_t smem_bytes, cudaStream_t s) {
+    SweepFn k = sweep_kernel(f16, smem, jmax, kmax);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    k<<<grid, warps * 32, smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+int sweep_blocks_per_sm(bool f16, bool smem, int jmax, int kmax, int warps, size_t smem_bytes) {
+    SweepFn k = sweep_kernel(f16, smem, jmax, kmax);
+    if (!k) return 0;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem_bytes) != cudaSuccess) return 0;
+    return nb;
+}
+
+}  // namespace
 
 namespace {
 
@@ -81,11 +110,11 @@ __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
                         e = decode_f32(reinterpret_cast<const uint4*>(row)[u]);
                     }
                     if (e.l0 != 0.0f) {
-                        g = fmaf(R[u * a.B + e.k0], e.l0, g);
+                        g = fmaf(R[u * a.pitch + e.k0], e.l0, g);
                         h = fmaf(e.l0, e.l0, h);
                     }
                     if (e.l1 != 0.0f) {
-                        g = fmaf(R[u * a.B + e.k1], e.l1, g);
+                        g = fmaf(R[u * a.pitch + e.k1], e.l1, g);
                         h = fmaf(e.l1, e.l1, h);
                     }
                 }
@@ -163,7 +192,7 @@ struct Plan {
 
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, Plan* pl) {
     const bool f16 = p->precision == PILA_F16;
-    const int J = f16 ? 2 * ((p->row_records + 63) / 64) : (p->U + 31) / 32;
+    const int J = f16 ? 2 * ((p->row_records + 63) / 64) : (p->U + 31) / 32;  // records per lane
     int jmax = 0;
     for (int c : {4, 8, 12, 16})
         if (J <= c) {
@@ -171,16 +200,17 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
             break;
         }
     if (!jmax) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: at most 512 angles are supported");
-    pl->J = J;
+    pl->J = jmax;  // lanes always walk jmax records; the ones past U are zero
     pl->jmax = jmax;
     pl->D = 4;
     pl->stage_bytes = f16 ? 256 * jmax : 512 * jmax;
-    pl->resid_floats = (long long)align_up((size_t)p->U * p->B, 4);
+    // rows of B + 1 cells (the last one private to the row's lane), then 2 dummy cells per lane
+    pl->resid_floats = (long long)align_up((size_t)p->U * (p->B + 1) + 64, 4);
     int dev = 0, maxopt = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t ring = 512 + (size_t)pl->D * pl->stage_bytes;
+    const size_t ring = kRingHeader + (size_t)pl->D * pl->stage_bytes;
     const size_t smem_warp = align_up(ring + (size_t)pl->resid_floats * 4, 128);
     const size_t glob_warp = align_up(ring, 128);
     bool smem = false;
@@ -193,12 +223,13 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     }
     pl->smem = smem;
     pl->warp_smem = (int)(smem ? smem_warp : glob_warp);
-    int warps = std::min<int>(kSatMaxWarps, std::max<int>(1, maxopt / pl->warp_smem));
+    // Shared-memory residuals: as many warps as fit one SM.  Global residuals:
+    // four warps per CTA so that chains spread over all SMs, one per scheduler.
+    int warps = smem ? std::min<int>(kSatMaxWarps, std::max<int>(1, maxopt / pl->warp_smem)) : 4;
     warps = std::min(warps, std::max(1, n_chains));
     pl->warps = warps;
     const size_t smem_bytes = (size_t)warps * pl->warp_smem;
-    int per_sm = f16 ? sweep_blocks_per_sm_f16(smem, jmax, warps, smem_bytes)
-                     : sweep_blocks_per_sm_f32(smem, jmax, warps, smem_bytes);
+    int per_sm = sweep_blocks_per_sm(f16, smem, jmax, kmax_for(prm->bome_k), warps, smem_bytes);
     if (per_sm < 1) per_sm = 1;
     const long long slots = (long long)sms * per_sm * warps;
     pl->spt = n_chains <= slots ? window : 1;
@@ -334,6 +365,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         pa.pm_stride = cells;
         pa.resid = ws.resid;
         pa.resid_stride = pl.resid_floats;
+        pa.resid_pitch = p->B + 1;
         pa.part_sq = ws.part_sq;
         pa.part_drift = ws.part_drift;
         ReduceArgs ra{};
@@ -358,6 +390,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         ta.n = p->n;
         ta.U = p->U;
         ta.B = p->B;
+        ta.pitch = p->B + 1;
         ta.list = p->d_list;
         ta.n_list = p->n_mask;
         ta.beta = prm->beta;
@@ -386,6 +419,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         sa.n = p->n;
         sa.U = p->U;
         sa.B = p->B;
+        sa.pitch = p->B + 1;
         sa.list = p->d_list;
         sa.n_list = p->n_mask;
         sa.moves = M;
@@ -423,8 +457,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             sa.task_counter = ws.counters + wdx;
             const size_t smem_bytes = (size_t)pl.warps * pl.warp_smem;
             cudaEventRecord(evs[2 * wdx], q);
-            err = pa.f16 ? launch_sweep_f16(pl.smem, pl.jmax, sa, pl.grid, pl.warps, smem_bytes, q)
-                                     : launch_sweep_f32(pl.smem, pl.jmax, sa, pl.grid, pl.warps, smem_bytes, q);
+            err = launch_sweep(pa.f16, pl.smem, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid, pl.warps, smem_bytes, q);
             if (err != cudaSuccess) return err;
             cudaEventRecord(evs[2 * wdx + 1], q);
             const bool last = wdx + 1 == n_windows;

@@ -34,6 +34,7 @@ struct SatArgs {
     long long row_stride;        // bytes between pixel rows
     int copy_bytes;              // bytes fetched per move (multiple of 16)
     int n, U, B;
+    int pitch;                   // residual row pitch (B + 1: a private pad cell per row)
     const int32_t* list;         // reconstruction-space pixels (NULL: identity)
     int n_list;
     int moves;                   // M moves per stage
@@ -67,7 +68,8 @@ struct SatArgs {
 };
 
 constexpr int kSatMaxWarps = 8;
-constexpr int kURing = 40;  // floats per uniform slot (>= 4 * ceil((kMaxK + 2) / 4))
+// Per-warp shared memory header: barriers, stage pixels, the draw ring.
+constexpr int kRingHeader = 128 + 2 * 8 * (32 + 4) * 4;
 
 __device__ __forceinline__ double stage_temperature(int schedule, double t0, double tn, int s, int n_sweeps) {
     const double N = (double)n_sweeps, n = (double)s;
@@ -76,53 +78,43 @@ __device__ __forceinline__ double stage_temperature(int schedule, double t0, dou
     return t0 - n * (t0 - tn) / N;
 }
 
-// Calls fn(j, u, entry) for the lane's records j < J of a stage buffer.
-template <bool F16, int JMAX, typename Fn>
-__device__ __forceinline__ void for_each_record(const unsigned char* stage, int lane, int J, Fn&& fn) {
+constexpr int kBatch = 8;       // moves per block of random draws
+constexpr int kDrawRing = 2 * kBatch;
+
+// Lane-owned decoded records of one move.  Entry 1 always sits on bin k + 1
+// (the builder stores consecutive bins), so only bin 0 is kept.
+template <int JMAX>
+struct Recs {
+    int k[JMAX];
+    float l0[JMAX], l1[JMAX];
+};
+
+template <bool F16, int JMAX>
+__device__ __forceinline__ void decode_stage(const unsigned char* stage, int lane, int J, Recs<JMAX>& r) {
     const uint4* q4 = reinterpret_cast<const uint4*>(stage);
     if constexpr (F16) {
 #pragma unroll
         for (int i = 0; i < JMAX / 2; ++i) {
             if (2 * i < J) {
-                const int q = lane + 32 * i;
-                const uint4 v = q4[q];
-                fn(2 * i, 2 * q, decode_f16(v.x, v.y));
-                fn(2 * i + 1, 2 * q + 1, decode_f16(v.z, v.w));
+                const uint4 v = q4[lane + 32 * i];
+                const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+                const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
+                r.k[2 * i] = (int)(v.x & 0xffffu);
+                r.l0[2 * i] = a.x;
+                r.l1[2 * i] = a.y;
+                r.k[2 * i + 1] = (int)(v.z & 0xffffu);
+                r.l0[2 * i + 1] = b.x;
+                r.l1[2 * i + 1] = b.y;
             }
         }
     } else {
 #pragma unroll
         for (int i = 0; i < JMAX; ++i) {
             if (i < J) {
-                const int q = lane + 32 * i;
-                fn(i, q, decode_f32(q4[q]));
-            }
-        }
-    }
-}
-
-// Same, over two stage buffers at once (same lane, same angle u).
-template <bool F16, int JMAX, typename Fn>
-__device__ __forceinline__ void for_each_record_pair(const unsigned char* s0, const unsigned char* s1, int lane,
-                                                     int J, Fn&& fn) {
-    const uint4* a4 = reinterpret_cast<const uint4*>(s0);
-    const uint4* b4 = reinterpret_cast<const uint4*>(s1);
-    if constexpr (F16) {
-#pragma unroll
-        for (int i = 0; i < JMAX / 2; ++i) {
-            if (2 * i < J) {
-                const int q = lane + 32 * i;
-                const uint4 va = a4[q], vb = b4[q];
-                fn(2 * i, decode_f16(va.x, va.y), decode_f16(vb.x, vb.y));
-                fn(2 * i + 1, decode_f16(va.z, va.w), decode_f16(vb.z, vb.w));
-            }
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < JMAX; ++i) {
-            if (i < J) {
-                const int q = lane + 32 * i;
-                fn(i, decode_f32(a4[q]), decode_f32(b4[q]));
+                const uint4 v = q4[lane + 32 * i];
+                r.k[i] = (int)v.x;
+                r.l0[i] = __uint_as_float(v.z);
+                r.l1[i] = __uint_as_float(v.w);
             }
         }
     }
@@ -131,13 +123,13 @@ __device__ __forceinline__ void for_each_record_pair(const unsigned char* s0, co
 struct WarpRing {
     uint64_t* bar;       // [kMaxStages]
     int* pix;            // [kMaxStages] pixel of the move held by each stage
-    float* uring;        // [2][kURing] uniforms of the current / next move
+    float* draws;        // [kDrawRing][draw_stride]: pixel, L = -ln N1, pad, pad, u_0..u_{K-1}
     unsigned char* stages;
 };
 
 // Waits (bounded) for the copies still in flight after a failure.
 static __device__ __noinline__ void drain_stages(const WarpRing& w, int D, int first_move, int last_move,
-                                          uint32_t& phase) {
+                                                 uint32_t& phase) {
     for (int mv = first_move; mv <= last_move; ++mv) {
         const int st = mv % D;
         mbar_wait_bounded(&w.bar[st], (phase >> st) & 1u);
@@ -145,52 +137,258 @@ static __device__ __noinline__ void drain_stages(const WarpRing& w, int D, int f
     }
 }
 
-// One temperature stage of one chain.  Returns false if a bounded wait gave up.
-template <bool F16, bool SMEM, int JMAX>
-__device__ __forceinline__ bool run_stage(const SatArgs& a, const WarpRing& w, int c, int s, float T, float* R,
-                                          float* img, uint2 key, uint32_t& phase, double& S, float& C2,
-                                          unsigned long long& n_acc, int lane) {
-    const int M = a.moves, D = a.D, K = a.K, B = a.B, J = a.J;
-    if (M <= 0 || a.n_list <= 0) return true;
-    const int nblk = (K + 2 + 3) / 4;
-    const uint32_t nl = (uint32_t)a.n_list;
-    const int32_t* list = a.list;
-    auto pixel_of = [&](uint32_t x) -> int {
-        const uint32_t i = pick_index(x, nl);
-        return list ? list[i] : (int)i;
-    };
-    auto issue = [&](int st, int p) {  // lane 31 only
-        w.pix[st] = p;
-        mbar_arrive_expect_tx(&w.bar[st], (uint32_t)a.copy_bytes);
-        bulk_copy_g2s(w.stages + (size_t)st * a.stage_bytes, a.table + (long long)p * a.row_stride,
-                      (uint32_t)a.copy_bytes, &w.bar[st]);
-        prefetch_l1(img + p);
-    };
+__device__ __forceinline__ void cp_async_4(void* smem_dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-    // Prologue: rows of moves 0..D-2 in flight, uniforms of move 0, pixel of move D-1.
-    const int pre = min(D - 1, M);
-    if (lane == 31) {
-        for (int j = 0; j < pre; ++j) {
-            const uint4 x = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)j, 0u, kStreamSat), key);
-            issue(j, pixel_of(x.x));
+// Random draws of moves [first, first + kBatch) of stage s: one warp-wide
+// Philox pass per 32 (move, block) units.  Draw d = 4*block + word: d = 0 the
+// pixel, d = 1 the acceptance number N1 (stored as L = -ln N1), d = 2 + e the
+// uniform of estimate e.  Pixels of a masked reconstruction space are copied
+// from the pixel list asynchronously.
+template <int KMAX>
+__device__ __forceinline__ void draw_batch(const SatArgs& a, const WarpRing& w, int s, int first, uint2 key,
+                                           int lane) {
+    constexpr int kStride = KMAX + 4;
+    const int nblk = (a.K + 2 + 3) / 4;
+    const int units = kBatch * nblk;
+    const uint32_t nl = (uint32_t)a.n_list;
+    for (int u0 = 0; u0 < units; u0 += 32) {
+        const int unit = u0 + lane;
+        const int mv = first + unit / nblk, blk = unit % nblk;
+        const uint4 x = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)mv, (uint32_t)blk, kStreamSat), key);
+        if (unit < units && mv < a.moves) {
+            float* rec = w.draws + (mv % kDrawRing) * kStride;
+            const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int d = 4 * blk + i;
+                if (d == 0) {
+                    const uint32_t idx = pick_index(wd[0], nl);
+                    if (a.list) cp_async_4(rec, a.list + idx);
+                    else reinterpret_cast<int*>(rec)[0] = (int)idx;
+                } else if (d == 1) {
+                    rec[1] = -logf(unit_uniform(wd[1]));
+                } else if (d - 2 < a.K) {
+                    rec[4 + d - 2] = unit_uniform(wd[i]);
+                }
+            }
         }
     }
-    int pending = 0;
-    {
-        const uint4 ctr = lane == 31 ? make_uint4((uint32_t)s, (uint32_t)(D - 1), 0u, kStreamSat)
-                                     : make_uint4((uint32_t)s, 0u, (uint32_t)lane, kStreamSat);
-        const uint4 x = philox4x32_10(ctr, key);
-        if (lane < nblk) {
-            float* u = w.uring + 4 * lane;
-            u[0] = unit_uniform(x.x);
-            u[1] = unit_uniform(x.y);
-            u[2] = unit_uniform(x.z);
-            u[3] = unit_uniform(x.w);
-        }
-        if (lane == 31 && D - 1 < M) pending = pixel_of(x.x);
+}
+
+// Issue of a pixel row into a stage by one lane of the warp (the predicate),
+// without a branch: barrier arrival with the expected bytes, then the copy.
+__device__ __forceinline__ void issue_row_pred(bool pred, uint64_t* bar, void* dst, const void* src,
+                                               uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %0, 0;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %4;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%2], [%3], %4, [%1];\n\t}" ::"r"(
+            (uint32_t)pred),
+        "r"(smem_u32(bar)), "r"(smem_u32(dst)), "l"(src), "r"(bytes)
+        : "memory");
+}
+
+// Residual values at a move's two entry cells per record.  Every cell index
+// is valid: an empty entry names a real cell of its row (and its length 0
+// keeps it out of every sum), a record past U names a lane-private dummy
+// cell after the residual.  So loads and stores need no predicate.
+template <int JMAX>
+__device__ __forceinline__ void gather(const float* R, const int (&rowbase)[JMAX], const Recs<JMAX>& r,
+                                       float (&v0)[JMAX], float (&v1)[JMAX]) {
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const float* q = R + rowbase[j] + r.k[j];
+        v0[j] = q[0];
+        v1[j] = q[1];
     }
+}
+
+struct MoveState {
+    int p;       // pixel of the move
+    float f;     // its value as loaded
+    bool fwd;    // the previous move wrote this pixel: use fwd_f instead
+    float fwd_f;
+};
+
+// One move (Steps 2-4 with BoME) whose records/values are (cur, rv), while
+// the next move's (nxt, nv) are gathered.  has_next = false for the last move.
+template <bool F16, int JMAX, int KMAX, bool HAS_NEXT>
+__device__ __forceinline__ bool move_step(const SatArgs& a, const WarpRing& w, int s, int m, int M, float T, float* R,
+                                          float* img, uint2 key, uint32_t& phase, float& S_hi, float& S_lo,
+                                          float& C, unsigned long long& n_acc, int lane, const int (&rowbase)[JMAX],
+                                          int& st_cur, int& issued, bool tracing, const Recs<JMAX>& cur,
+                                          const float (&rv0)[JMAX], const float (&rv1)[JMAX], Recs<JMAX>& nxt,
+                                          float (&nv0)[JMAX], float (&nv1)[JMAX], MoveState& ms) {
+    constexpr int kStride = KMAX + 4;
+    const int D = a.D;
+    const int st_next = st_cur + 1 == D ? 0 : st_cur + 1;
+    const int st_issue = st_cur == 0 ? D - 1 : st_cur - 1;
     __syncwarp();
-    int issued = pre - 1;  // last move whose row has been requested
+    // Moves [m-kBatch, m) are done: their draw slots take moves [m+kBatch, m+2*kBatch).
+    if ((m & (kBatch - 1)) == 0 && m > 0 && m + kBatch < M) draw_batch<KMAX>(a, w, s, m + kBatch, key, lane);
+    const int mi = m + D - 1;
+    if (mi < M) {
+        if (a.list && (mi & (kBatch - 1)) == 0) {
+            cp_async_wait_all();  // pixels of the batch that starts at mi
+            __syncwarp();
+        }
+        const int pi = reinterpret_cast<const int*>(w.draws + (mi % kDrawRing) * kStride)[0];
+        if (lane == 31) w.pix[st_issue] = pi;
+        issue_row_pred(lane == 31, &w.bar[st_issue], w.stages + (size_t)st_issue * a.stage_bytes,
+                       a.table + (long long)pi * a.row_stride, (uint32_t)a.copy_bytes);
+        if (lane == 31) prefetch_l1(img + pi);
+        issued = mi;
+    }
+    // Draws of this move (independent of the chain state).
+    const float* drec = w.draws + (m % kDrawRing) * kStride;
+    const float L = drec[1];
+    float uc[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; q += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(drec + 4 + q);
+        uc[q] = v.x;
+        if (q + 1 < KMAX) uc[q + 1] = v.y;
+        if (q + 2 < KMAX) uc[q + 2] = v.z;
+        if (q + 3 < KMAX) uc[q + 3] = v.w;
+    }
+    // Partial sums of this move.
+    float g0 = 0.0f, g1 = 0.0f, h0 = 0.0f, h1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        g0 = fmaf(rv0[j], cur.l0[j], g0);
+        g1 = fmaf(rv1[j], cur.l1[j], g1);
+        h0 = fmaf(cur.l0[j], cur.l0[j], h0);
+        h1 = fmaf(cur.l1[j], cur.l1[j], h1);
+    }
+    float g = g0 + g1, h = h0 + h1;
+    // Gather of the next move while this one is reduced and decided.
+    int p1 = 0;
+    float f1 = 0.0f;
+    if (HAS_NEXT) {
+        if (!mbar_wait_bounded(&w.bar[st_next], (phase >> st_next) & 1u)) {
+            raise_error(a.error, SATPILA_ERR_TIMEOUT);
+            drain_stages(w, D, m + 1, issued, phase);
+            return false;
+        }
+        phase ^= 1u << st_next;
+        p1 = w.pix[st_next];
+        f1 = img[p1];
+        decode_stage<F16, JMAX>(w.stages + (size_t)st_next * a.stage_bytes, lane, JMAX, nxt);
+        gather<JMAX>(R, rowbase, nxt, nv0, nv1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+    }
+    // Step 4 threshold: with L = -ln N1, N1 < exp(-dC/T) <=> dC < T L
+    // <=> x < T L (2C + T L) for x = dS / (B U) (dC = sqrt(C^2 + x) - C).
+    const float TL = T * L;
+    const float theta = TL * fmaf(2.0f, C, TL);
+    // BoME: every lane evaluates every estimate; smallest dS, lowest index on ties.
+    const float f = ms.fwd ? ms.fwd_f : ms.f;
+    const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
+    const float g2 = 2.0f * g;
+    float dS[KMAX], fc[KMAX];
+    int ci[KMAX];
+#pragma unroll
+    for (int e = 0; e < KMAX; ++e) {
+        fc[e] = fmaf(uc[e], span, lo);
+        const float df = fc[e] - f;
+        dS[e] = e < a.K ? df * fmaf(df, h, g2) : __int_as_float(0x7f800000);
+        ci[e] = e;
+    }
+#pragma unroll
+    for (int width = 1; width < KMAX; width *= 2) {
+#pragma unroll
+        for (int e = 0; e + width < KMAX; e += 2 * width) {
+            const bool take = dS[e + width] < dS[e];
+            dS[e] = take ? dS[e + width] : dS[e];
+            fc[e] = take ? fc[e + width] : fc[e];
+            ci[e] = take ? ci[e + width] : ci[e];
+        }
+    }
+    const float best_dS = dS[0], best_f = fc[0];
+    const float x = best_dS * a.inv_BU;
+    const bool accept = x <= 0.0f || x < theta;
+    const float df = accept ? best_f - f : 0.0f;
+    if (tracing && lane == 0) {
+        const float Cp = sqrtf(fmaxf(0.0f, fmaf(C, C, x)));
+        const float den = Cp + C;
+        const long long idx = (long long)s * M + m;
+        if (idx < a.trace_cap) {
+            sat_trace_rec r;
+            r.pixel = ms.p;
+            r.cstar = ci[0];
+            r.accepted = accept ? 1 : 0;
+            r.pad = 0;
+            r.dS = best_dS;
+            r.dC = den > 0.0f ? x / den : 0.0f;
+            r.fnew = accept ? best_f : f;
+            r.pad2 = 0.0f;
+            a.trace[idx] = r;
+        }
+    }
+    // Eq. (6) on the lane's own residual cells, and the same update on the
+    // already gathered values of the next move where the cells coincide.
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        float* q = R + rowbase[j] + cur.k[j];
+        q[0] = fmaf(df, cur.l0[j], rv0[j]);  // unchanged value when rejected or empty
+        q[1] = fmaf(df, cur.l1[j], rv1[j]);
+        if (HAS_NEXT) {
+            const int d = nxt.k[j] - cur.k[j];
+            const float s0 = d == 0 ? cur.l0[j] : (d == 1 ? cur.l1[j] : 0.0f);
+            const float s1 = d == 0 ? cur.l1[j] : (d == -1 ? cur.l0[j] : 0.0f);
+            nv0[j] = fmaf(df, s0, nv0[j]);
+            nv1[j] = fmaf(df, s1, nv1[j]);
+        }
+    }
+    img[ms.p] = accept ? best_f : f;
+    if (HAS_NEXT) {
+        ms.fwd = p1 == ms.p;  // the value written just above
+        ms.fwd_f = accept ? best_f : f;
+        ms.f = f1;
+        ms.p = p1;
+    }
+    // Kahan-compensated running sum of squared residuals.
+    const float y = (accept ? best_dS : 0.0f) - S_lo;
+    const float t = S_hi + y;
+    S_lo = (t - S_hi) - y;
+    S_hi = t;
+    const float C2 = fmaxf(0.0f, S_hi * a.inv_BU);
+    C = accept ? (C2 > 0.0f ? C2 * rsqrtf(C2) : 0.0f) : C;
+    n_acc += accept ? 1ull : 0ull;
+    st_cur = st_next;
+    return true;
+}
+
+// One temperature stage of one chain.  Returns false if a bounded wait gave up.
+template <bool F16, bool SMEM, int JMAX, int KMAX>
+__device__ __forceinline__ bool run_stage(const SatArgs& a, const WarpRing& w, int c, int s, float T, float* R,
+                                          float* img, uint2 key, uint32_t& phase, float& S_hi, float& S_lo,
+                                          unsigned long long& n_acc, int lane, const int (&rowbase)[JMAX]) {
+    constexpr int kStride = KMAX + 4;
+    const int M = a.moves, D = a.D;
+    if (M <= 0 || a.n_list <= 0) return true;
+
+    // Prologue: draws of the first two batches, rows of moves 0..D-2 in flight.
+    draw_batch<KMAX>(a, w, s, 0, key, lane);
+    draw_batch<KMAX>(a, w, s, kBatch, key, lane);
+    cp_async_wait_all();
+    __syncwarp();
+    const int pre = min(D - 1, M);
+    for (int j = 0; j < pre; ++j) {
+        const int pj = reinterpret_cast<const int*>(w.draws + (j % kDrawRing) * kStride)[0];
+        if (lane == 31) w.pix[j] = pj;
+        issue_row_pred(lane == 31, &w.bar[j], w.stages + (size_t)j * a.stage_bytes,
+                       a.table + (long long)pj * a.row_stride, (uint32_t)a.copy_bytes);
+    }
+    int issued = pre - 1;
     if (!mbar_wait_bounded(&w.bar[0], phase & 1u)) {
         raise_error(a.error, SATPILA_ERR_TIMEOUT);
         drain_stages(w, D, 0, issued, phase);
@@ -198,145 +396,43 @@ __device__ __forceinline__ bool run_stage(const SatArgs& a, const WarpRing& w, i
     }
     phase ^= 1u;
 
-    float rv0[JMAX], rv1[JMAX], nv0[JMAX], nv1[JMAX];
+    Recs<JMAX> ra, rb;
+    float a0[JMAX], a1[JMAX], b0[JMAX], b1[JMAX];
 #pragma unroll
-    for (int j = 0; j < JMAX; ++j) rv0[j] = rv1[j] = nv0[j] = nv1[j] = 0.0f;
-    int p = w.pix[0];
-    float f = img[p];
-    for_each_record<F16, JMAX>(w.stages, lane, J, [&](int j, int u, const Entry2& e) {
-        rv0[j] = e.l0 != 0.0f ? R[u * B + e.k0] : 0.0f;
-        rv1[j] = e.l1 != 0.0f ? R[u * B + e.k1] : 0.0f;
-    });
-
-    int st_cur = 0;
-    for (int m = 0; m < M; ++m) {
-        const int st_next = st_cur + 1 == D ? 0 : st_cur + 1;
-        const int st_issue = st_cur == 0 ? D - 1 : st_cur - 1;
-        __syncwarp();
-        // Row of move m+D-1 into the stage freed by move m-1.
-        if (lane == 31 && m + D - 1 < M) issue(st_issue, pending);
-        if (m + D - 1 < M) issued = m + D - 1;
-        {
-            // One Philox evaluation serves two purposes: lanes < nblk draw the
-            // uniforms of move m+1, lane 31 the pixel of move m+D.
-            const uint4 ctr = lane == 31 ? make_uint4((uint32_t)s, (uint32_t)(m + D), 0u, kStreamSat)
-                                         : make_uint4((uint32_t)s, (uint32_t)(m + 1), (uint32_t)lane, kStreamSat);
-            const uint4 x = philox4x32_10(ctr, key);
-            if (lane < nblk && m + 1 < M) {
-                float* u = w.uring + ((m + 1) & 1) * kURing + 4 * lane;
-                u[0] = unit_uniform(x.x);
-                u[1] = unit_uniform(x.y);
-                u[2] = unit_uniform(x.z);
-                u[3] = unit_uniform(x.w);
-            }
-            if (lane == 31 && m + D < M) pending = pixel_of(x.x);
-        }
-        __syncwarp();
-
-        const unsigned char* cur = w.stages + (size_t)st_cur * a.stage_bytes;
-        const unsigned char* nxt = w.stages + (size_t)st_next * a.stage_bytes;
-        // Partial sums of the current move.
-        float g = 0.0f, h = 0.0f;
-        for_each_record<F16, JMAX>(cur, lane, J, [&](int j, int, const Entry2& e) {
-            g = fmaf(rv0[j], e.l0, g);
-            g = fmaf(rv1[j], e.l1, g);
-            h = fmaf(e.l0, e.l0, h);
-            h = fmaf(e.l1, e.l1, h);
-        });
-        // Gather of the next move while this one is reduced and decided.
-        int p1 = -1;
-        float f1 = 0.0f;
-        if (m + 1 < M) {
-            if (!mbar_wait_bounded(&w.bar[st_next], (phase >> st_next) & 1u)) {
-                raise_error(a.error, SATPILA_ERR_TIMEOUT);
-                drain_stages(w, D, m + 1, issued, phase);
-                return false;
-            }
-            phase ^= 1u << st_next;
-            p1 = w.pix[st_next];
-            f1 = img[p1];
-            for_each_record<F16, JMAX>(nxt, lane, J, [&](int j, int u, const Entry2& e) {
-                nv0[j] = e.l0 != 0.0f ? R[u * B + e.k0] : 0.0f;
-                nv1[j] = e.l1 != 0.0f ? R[u * B + e.k1] : 0.0f;
-            });
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            g += __shfl_xor_sync(0xffffffffu, g, o);
-            h += __shfl_xor_sync(0xffffffffu, h, o);
-        }
-        // BoME over the K estimates (every lane evaluates all of them).
-        const float* ur = w.uring + (m & 1) * kURing;
-        const float lo = fmaxf(0.0f, f - a.beta), hi = fminf(a.beta, f + a.beta), span = hi - lo;
-        const float g2 = 2.0f * g;
-        float best_dS = __int_as_float(0x7f800000), best_df = 0.0f, best_f = f;
-        int best_c = 0;
-        for (int e = 0; e < K; ++e) {
-            const float fc = fmaf(ur[2 + e], span, lo);
-            const float df = fc - f;
-            const float dS = df * fmaf(df, h, g2);
-            if (dS < best_dS) {
-                best_dS = dS;
-                best_df = df;
-                best_f = fc;
-                best_c = e;
-            }
-        }
-        // Eq. (7) and Step 4.
-        const float x = best_dS * a.inv_BU;
-        const float C = sqrtf(C2);
-        const float Cp = sqrtf(fmaxf(0.0f, C2 + x));
-        const float den = Cp + C;
-        const float dC = den > 0.0f ? x / den : 0.0f;
-        const bool accept = dC <= 0.0f || (T > 0.0f && ur[1] < expf(-dC / T));
-        if (accept) {
-            for_each_record<F16, JMAX>(cur, lane, J, [&](int j, int u, const Entry2& e) {
-                if (e.l0 != 0.0f) R[u * B + e.k0] = fmaf(best_df, e.l0, rv0[j]);
-                if (e.l1 != 0.0f) R[u * B + e.k1] = fmaf(best_df, e.l1, rv1[j]);
-            });
-            if (m + 1 < M) {
-                for_each_record_pair<F16, JMAX>(cur, nxt, lane, J, [&](int j, const Entry2& ec, const Entry2& en) {
-                    if (en.l0 != 0.0f) {
-                        if (ec.l0 != 0.0f && ec.k0 == en.k0) nv0[j] = fmaf(best_df, ec.l0, nv0[j]);
-                        if (ec.l1 != 0.0f && ec.k1 == en.k0) nv0[j] = fmaf(best_df, ec.l1, nv0[j]);
-                    }
-                    if (en.l1 != 0.0f) {
-                        if (ec.l0 != 0.0f && ec.k0 == en.k1) nv1[j] = fmaf(best_df, ec.l0, nv1[j]);
-                        if (ec.l1 != 0.0f && ec.k1 == en.k1) nv1[j] = fmaf(best_df, ec.l1, nv1[j]);
-                    }
-                });
-            }
-            img[p] = best_f;
-            if (p1 == p) f1 = best_f;
-            S += (double)best_dS;
-            C2 = (float)(S * a.inv_BU_d);
-            ++n_acc;
-        }
-        if (a.trace && c == a.trace_chain && lane == 0) {
-            const long long idx = (long long)s * M + m;
-            if (idx < a.trace_cap) {
-                sat_trace_rec r;
-                r.pixel = p;
-                r.cstar = best_c;
-                r.accepted = accept ? 1 : 0;
-                r.pad = 0;
-                r.dS = best_dS;
-                r.dC = dC;
-                r.fnew = accept ? best_f : f;
-                r.pad2 = 0.0f;
-                a.trace[idx] = r;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-            rv0[j] = nv0[j];
-            rv1[j] = nv1[j];
-        }
-        f = f1;
-        p = p1;
-        st_cur = st_next;
+    for (int j = 0; j < JMAX; ++j) {
+        rb.k[j] = 0;
+        rb.l0[j] = rb.l1[j] = 0.0f;
+        b0[j] = b1[j] = 0.0f;
     }
-    return true;
+    decode_stage<F16, JMAX>(w.stages, lane, JMAX, ra);
+    gather<JMAX>(R, rowbase, ra, a0, a1);
+    MoveState ms;
+    ms.p = w.pix[0];
+    ms.f = img[ms.p];
+    ms.fwd = false;
+    ms.fwd_f = 0.0f;
+    float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
+    const bool tracing = a.trace && s >= 0 && a.trace_chain >= 0 && c == a.trace_chain;
+    int st_cur = 0;
+    int m = 0;
+    // Two moves per trip: the register sets alternate roles, no copies.
+    for (; m + 2 < M; m += 2) {
+        if (!move_step<F16, JMAX, KMAX, true>(a, w, s, m, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc, lane,
+                                              rowbase, st_cur, issued, tracing, ra, a0, a1, rb, b0, b1, ms))
+            return false;
+        if (!move_step<F16, JMAX, KMAX, true>(a, w, s, m + 1, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc,
+                                              lane, rowbase, st_cur, issued, tracing, rb, b0, b1, ra, a0, a1, ms))
+            return false;
+    }
+    if (m + 1 < M) {
+        if (!move_step<F16, JMAX, KMAX, true>(a, w, s, m, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc, lane,
+                                              rowbase, st_cur, issued, tracing, ra, a0, a1, rb, b0, b1, ms))
+            return false;
+        return move_step<F16, JMAX, KMAX, false>(a, w, s, m + 1, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc,
+                                                 lane, rowbase, st_cur, issued, tracing, rb, b0, b1, ra, a0, a1, ms);
+    }
+    return move_step<F16, JMAX, KMAX, false>(a, w, s, m, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc, lane,
+                                             rowbase, st_cur, issued, tracing, ra, a0, a1, rb, b0, b1, ms);
 }
 
 // Waits until another warp has finished the chain's earlier stages (at most
@@ -350,7 +446,7 @@ static __device__ __forceinline__ bool wait_progress(const int* flag, int target
     }
 }
 
-template <bool F16, bool SMEM, int JMAX>
+template <bool F16, bool SMEM, int JMAX, int KMAX>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -358,8 +454,8 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
     WarpRing w;
     w.bar = reinterpret_cast<uint64_t*>(wb);
     w.pix = reinterpret_cast<int*>(wb + 64);
-    w.uring = reinterpret_cast<float*>(wb + 128);
-    w.stages = wb + 512;
+    w.draws = reinterpret_cast<float*>(wb + 128);
+    w.stages = wb + kRingHeader;
     float* rs = reinterpret_cast<float*>(w.stages + (size_t)a.D * a.stage_bytes);
 
     // Stage tails beyond a row stay zero (length 0 = no contribution).
@@ -370,6 +466,14 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
     fence_proxy_async_smem();
     if (lane == 0) fence_barrier_init();
     __syncwarp();
+
+    // Residual row offsets of the lane's angles.
+    int rowbase[JMAX];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const int u = F16 ? 2 * (lane + 32 * (j / 2)) + (j & 1) : lane + 32 * j;
+        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * lane;  // past U: this lane's dummy cells
+    }
 
     uint32_t phase = 0;
     for (;;) {
@@ -398,8 +502,9 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
             for (long long e = lane; e < a.resid_floats / 4; e += 32) dst[e] = src[e];
             __syncwarp();
         }
-        double S = a.S[c];
-        float C2 = (float)(S * a.inv_BU_d);
+        const double S = a.S[c];
+        float S_hi = (float)S;
+        float S_lo = -(float)(S - (double)S_hi);  // Kahan carries the negated remainder
         unsigned long long n_acc = 0;
         const uint2 key = chain_key(a.seed + (unsigned long long)c);
         float* img = a.img + (long long)c * a.img_stride;
@@ -407,8 +512,11 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
         bool ok = true;
         for (int s = s0; s < s1 && ok; ++s) {
             const float T = (float)stage_temperature(a.schedule, T0, TN, s, a.n_sweeps_total);
-            ok = run_stage<F16, SMEM, JMAX>(a, w, c, s, T, R, img, key, phase, S, C2, n_acc, lane);
-            if (a.sweep_cost && lane == 0) a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(S * a.inv_BU_d);
+            ok = run_stage<F16, SMEM, JMAX, KMAX>(a, w, c, s, T, R, img, key, phase, S_hi, S_lo, n_acc, lane,
+                                                  rowbase);
+            if (a.sweep_cost && lane == 0)
+                a.sweep_cost[(long long)c * a.n_sweeps_total + s] =
+                    sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
         }
         __syncwarp();
         if (SMEM) {
@@ -417,7 +525,7 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
             for (long long e = lane; e < a.resid_floats / 4; e += 32) dst[e] = src[e];
         }
         if (lane == 0) {
-            a.S[c] = S;
+            a.S[c] = (double)S_hi - (double)S_lo;
             a.accepted[c] += n_acc;
         }
         __syncwarp();
@@ -434,6 +542,7 @@ struct T0Args {
     long long row_stride;
     int f16;
     int n, U, B;
+    int pitch;
     const int32_t* list;
     int n_list;
     float beta;
