@@ -158,6 +158,8 @@ typedef struct {
     int32_t residency;       /* SAT_RESIDENT_* */
     uint32_t flags;          /* SAT_FLAG_* */
     int32_t trace_chain;     /* chain whose moves are recorded, or -1 */
+    int32_t group_warps;     /* warps that share one chain's angles (1, 2, 4); 0: chosen by size */
+    int32_t pipeline_depth;  /* PILA rows in flight per chain, 3..8; 0: default (4) */
     sat_trace_rec* trace;    /* n_sweeps*M records for trace_chain (host or device), or NULL */
     double* sweep_cost;      /* [n_chains][n_sweeps] cost after each sweep (host or device), or NULL */
 } sat_params;

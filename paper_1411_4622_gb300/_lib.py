@@ -47,7 +47,8 @@ class SatParams(C.Structure):
                 ("moves_per_sweep", C.c_int32), ("t0", C.c_double), ("tn", C.c_double),
                 ("schedule", C.c_int32), ("t0_samples", C.c_int32), ("seed", C.c_uint64),
                 ("resync_every", C.c_int32), ("residency", C.c_int32), ("flags", C.c_uint32),
-                ("trace_chain", C.c_int32), ("trace", C.c_void_p), ("sweep_cost", C.c_void_p)]
+                ("trace_chain", C.c_int32), ("group_warps", C.c_int32), ("pipeline_depth", C.c_int32),
+                ("trace", C.c_void_p), ("sweep_cost", C.c_void_p)]
 
 
 class SatStats(C.Structure):

@@ -136,10 +136,12 @@ def pila_sirt_factor(p: Pila, stream=None) -> np.ndarray:
 
 def sat_params(*, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn=-1.0,
                schedule=SAT_SCHED_LINEAR, t0_samples=200, seed=0, resync_every=0,
-               residency=SAT_RESIDENT_AUTO, flags=0, trace_chain=-1, trace=None, sweep_cost=None):
+               residency=SAT_RESIDENT_AUTO, flags=0, trace_chain=-1, group_warps=0, pipeline_depth=0, trace=None,
+               sweep_cost=None):
     return L.SatParams(float(beta), int(bome_k), int(n_sweeps), int(moves_per_sweep), float(t0), float(tn),
                        int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(resync_every),
-                       int(residency), int(flags), int(trace_chain), _ptr(trace), _ptr(sweep_cost))
+                       int(residency), int(flags), int(trace_chain), int(group_warps), int(pipeline_depth), _ptr(trace),
+                       _ptr(sweep_cost))
 
 
 def sat_run(p: Pila, sino_meas, images, stream=None, **kw) -> list[dict]:

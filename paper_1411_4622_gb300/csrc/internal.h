@@ -23,6 +23,7 @@ struct satpila_pila {
     double* d_sin = nullptr;           // [U]
     double* d_w64 = nullptr;           // SIRT factor matrix [U][B], built on first use
     float* d_w32 = nullptr;
+    float* d_hsum = nullptr;           // [P] sum of squared stored lengths of each pixel
 };
 
 namespace satpila {

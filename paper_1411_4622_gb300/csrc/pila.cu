@@ -74,6 +74,23 @@ __global__ void pila_build_kernel(unsigned char* table, int f16, int row_records
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(entries, (unsigned long long)c);
 }
 
+// Per pixel, the sum of its stored lengths squared (sum l^2 of Eq. (7)'s
+// (df l)^2 term), accumulated in FP64 in angle order and rounded once.
+__global__ void pila_hsum_kernel(const unsigned char* table, int f16, int row_records, int U, long long P,
+                                 float* hsum) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double acc = 0.0;
+    for (int u = 0; u < U; ++u) {
+        const long long rec = p * row_records + u;
+        Entry2 e = f16 ? decode_f16(reinterpret_cast<const uint2*>(table)[rec].x,
+                                    reinterpret_cast<const uint2*>(table)[rec].y)
+                       : decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
+        acc += (double)e.l0 * e.l0 + (double)e.l1 * e.l1;
+    }
+    hsum[p] = (float)acc;
+}
+
 __global__ void pila_export_kernel(const unsigned char* table, int f16, int row_records, int U, long long P,
                                    int32_t* bins, float* lens) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,6 +164,7 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
         cudaMalloc(&p->d_list, std::max<size_t>(1, list.size()) * sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&p->d_mask, P) != cudaSuccess || cudaMalloc(&p->d_cos, p->U * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->d_sin, p->U * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&p->d_hsum, P * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&d_entries, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         if (d_entries) cudaFree(d_entries);
@@ -165,6 +183,11 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
         const long long blocks = (total + threads - 1) / threads;
         pila_build_kernel<<<(unsigned)blocks, threads, 0, s>>>(p->d_table, precision == PILA_F16, p->row_records,
                                                                 p->n, p->U, p->B, p->d_cos, p->d_sin, d_entries);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        pila_hsum_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(p->d_table, precision == PILA_F16,
+                                                                     p->row_records, p->U, P, p->d_hsum);
         e = cudaGetLastError();
     }
     unsigned long long entries = 0;
@@ -189,6 +212,7 @@ extern "C" int pila_free(satpila_pila* p) {
     cudaFree(p->d_sin);
     cudaFree(p->d_w64);
     cudaFree(p->d_w32);
+    cudaFree(p->d_hsum);
     delete p;
     return SATPILA_OK;
 }

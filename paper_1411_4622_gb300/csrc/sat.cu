@@ -184,57 +184,71 @@ struct Workspace {
 struct Plan {
     bool smem = false;
     int jmax = 4, J = 4, D = 4;
-    int warps = 1, grid = 1;
-    int stage_bytes = 0, warp_smem = 0;
+    int W = 1, groups = 1, warps = 1, grid = 1;
+    int stage_bytes = 0, group_smem = 0;
     long long resid_floats = 0;
     int spt = 1;  // stages per task
 };
 
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, Plan* pl) {
     const bool f16 = p->precision == PILA_F16;
-    const int J = f16 ? 2 * ((p->row_records + 63) / 64) : (p->U + 31) / 32;  // records per lane
-    int jmax = 0;
-    for (int c : {4, 8, 12, 16})
-        if (J <= c) {
-            jmax = c;
-            break;
-        }
-    if (!jmax) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: at most 512 angles are supported");
-    pl->J = jmax;  // lanes always walk jmax records; the ones past U are zero
-    pl->jmax = jmax;
-    pl->D = 4;
-    pl->stage_bytes = f16 ? 256 * jmax : 512 * jmax;
-    // rows of B + 1 cells (the last one private to the row's lane), then 2 dummy cells per lane
-    pl->resid_floats = (long long)align_up((size_t)p->U * (p->B + 1) + 64, 4);
     int dev = 0, maxopt = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t ring = kRingHeader + (size_t)pl->D * pl->stage_bytes;
-    const size_t smem_warp = align_up(ring + (size_t)pl->resid_floats * 4, 128);
-    const size_t glob_warp = align_up(ring, 128);
+    // Warps per chain: the fewest that leave each lane at most two records
+    // (four for very many angles).
+    auto records_per_lane = [&](int W) {
+        return f16 ? 2 * ((p->row_records + 64 * W - 1) / (64 * W)) : (p->U + 32 * W - 1) / (32 * W);
+    };
+    int W = prm->group_warps > 0 ? prm->group_warps : 1;
+    if (prm->group_warps <= 0)
+        while (W < kMaxGroupWarps && records_per_lane(W) > 2) W *= 2;
+    if (W != 1 && W != 2 && W != 4) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: group_warps must be 1, 2 or 4");
+    const int J = records_per_lane(W);
+    int jmax = 0;
+    for (int c : {2, 4, 8, 16})
+        if (J <= c) {
+            jmax = c;
+            break;
+        }
+    if (!jmax) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many angles for this many warps per chain");
+    pl->W = W;
+    pl->J = jmax;  // lanes always walk jmax records; the ones past U are zero
+    pl->jmax = jmax;
+    pl->D = prm->pipeline_depth > 0 ? prm->pipeline_depth : 4;
+    if (pl->D < 3 || pl->D > kMaxStages) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: pipeline_depth must be in [3, 8]");
+    pl->stage_bytes = 512 * W * (f16 ? jmax / 2 : jmax);  // 16-byte chunks of all lanes
+    // rows of B + 1 cells (the last one private to the row's lane), then
+    // 2 dummy cells per lane of a group
+    pl->resid_floats = (long long)align_up((size_t)p->U * (p->B + 1) + 64 * kMaxGroupWarps, 4);
+    const size_t ring = group_ring_bytes(W) + (size_t)pl->D * pl->stage_bytes;
+    const size_t smem_group = align_up(ring + (size_t)pl->resid_floats * 4, 128);
+    const size_t glob_group = align_up(ring, 128);
     bool smem = false;
     if (prm->residency == SAT_RESIDENT_SMEM) {
-        if (smem_warp > (size_t)maxopt)
+        if (smem_group > (size_t)maxopt)
             return fail(SATPILA_ERR_INVALID_ARG, "sat_run: residual does not fit in shared memory");
         smem = true;
     } else if (prm->residency == SAT_RESIDENT_AUTO) {
-        smem = smem_warp <= (size_t)maxopt;
+        smem = smem_group <= (size_t)maxopt;
     }
     pl->smem = smem;
-    pl->warp_smem = (int)(smem ? smem_warp : glob_warp);
-    // Shared-memory residuals: as many warps as fit one SM.  Global residuals:
-    // four warps per CTA so that chains spread over all SMs, one per scheduler.
-    int warps = smem ? std::min<int>(kSatMaxWarps, std::max<int>(1, maxopt / pl->warp_smem)) : 4;
-    warps = std::min(warps, std::max(1, n_chains));
-    pl->warps = warps;
-    const size_t smem_bytes = (size_t)warps * pl->warp_smem;
-    int per_sm = sweep_blocks_per_sm(f16, smem, jmax, kmax_for(prm->bome_k), warps, smem_bytes);
+    pl->group_smem = (int)(smem ? smem_group : glob_group);
+    // Shared-memory residuals: as many groups as fit one SM.  Global residuals:
+    // four warps per CTA so that chains spread over all SMs.
+    int groups = smem ? std::max<int>(1, std::min<int>(kSatMaxWarps / W, maxopt / pl->group_smem))
+                      : std::max(1, 4 / W);
+    groups = std::min(groups, std::max(1, n_chains));
+    pl->groups = groups;
+    pl->warps = groups * W;
+    const size_t smem_bytes = (size_t)groups * pl->group_smem;
+    int per_sm = sweep_blocks_per_sm(f16, smem, jmax, kmax_for(prm->bome_k), pl->warps, smem_bytes);
     if (per_sm < 1) per_sm = 1;
-    const long long slots = (long long)sms * per_sm * warps;
+    const long long slots = (long long)sms * per_sm * groups;
     pl->spt = n_chains <= slots ? window : 1;
     const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
-    const long long want = (std::min<long long>(tasks, slots) + warps - 1) / warps;
+    const long long want = (std::min<long long>(tasks, slots) + groups - 1) / groups;
     pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
     return SATPILA_OK;
 }
@@ -415,7 +429,8 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         SatArgs sa{};
         sa.table = p->d_table;
         sa.row_stride = p->row_bytes;
-        sa.copy_bytes = (int)p->row_bytes;
+        sa.row_chunks = (int)(p->row_bytes / 16);
+        sa.hsum = p->d_hsum;
         sa.n = p->n;
         sa.U = p->U;
         sa.B = p->B;
@@ -427,10 +442,10 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         sa.beta = prm->beta;
         sa.inv_BU = (float)(1.0 / (double)cells);
         sa.inv_BU_d = 1.0 / (double)cells;
-        sa.J = pl.J;
         sa.D = pl.D;
         sa.stage_bytes = pl.stage_bytes;
-        sa.warp_smem_bytes = pl.warp_smem;
+        sa.W = pl.W;
+        sa.group_smem_bytes = pl.group_smem;
         sa.resid_floats = pl.resid_floats;
         sa.n_chains = n_chains;
         sa.resid = ws.resid;
@@ -455,7 +470,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             sa.sweeps_per_task = pl.spt;
             sa.n_tasks = n_chains * ((sa.sweep_end - sa.sweep_begin + pl.spt - 1) / pl.spt);
             sa.task_counter = ws.counters + wdx;
-            const size_t smem_bytes = (size_t)pl.warps * pl.warp_smem;
+            const size_t smem_bytes = (size_t)pl.groups * pl.group_smem;
             cudaEventRecord(evs[2 * wdx], q);
             err = launch_sweep(pa.f16, pl.smem, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid, pl.warps, smem_bytes, q);
             if (err != cudaSuccess) return err;

@@ -1,28 +1,31 @@
 // The annealing move of Secs. II-A/II-B/III-B on sm_103a.
 //
-// One warp runs one chain; a chain is strictly sequential (move m+1 sees
-// move m's update).  Within a move the 32 lanes split the projection angles:
-// lane l owns a fixed set of angles for the whole run, so every residual cell
-// is only ever read and written by one thread and no atomics or barriers are
-// needed inside a chain.
+// A group of W warps runs one chain; a chain is strictly sequential (move
+// m+1 sees move m's update).  Within a move the 32*W lanes split the
+// projection angles: each lane owns a fixed set of angles for the whole run,
+// so every residual cell is only ever read and written by one thread and no
+// atomics are needed.
 //
 // Per move m (Step 2 -> Step 4):
 //   * pixel and estimates come from Philox4x32-10, key = seed + chain,
 //     counter (stage, move, block, 1): draw 0 picks the pixel, draw 1 is the
 //     acceptance number N1, draw 2+e the value of estimate e (Eq. (3) read as
 //     the uniform law on [max(0, f-beta), min(beta, f+beta)]);
-//   * the pixel's PILA row (Eq. (5)) is fetched by a 1-D bulk copy
-//     (cp.async.bulk + mbarrier) into a per-warp ring of D stages, issued
-//     D-1 moves ahead (pixel choice does not depend on the chain's state);
-//   * lanes gather the residual r = P_c - P_m at their entries' bins and form
-//     g = sum r*l and h = sum l^2 (warp-shuffle butterfly); every estimate's
-//     Eq. (7) sum is then dS = df * (2g + df*h), and the best one (BoME)
-//     is the smallest dS, lowest index on ties;
-//   * dC = (dS/(B*U)) / (C' + C) (Eq. (7) rearranged to avoid cancelling
-//     square roots); Metropolis test of Step 4 at the stage temperature;
+//   * each lane copies its own 16-byte chunks of the pixel's PILA row
+//     (Eq. (5)) into shared memory with cp.async, D-1 moves ahead (pixel
+//     choice does not depend on the chain's state);
+//   * the Eq. (7) sum of every estimate is dS = df * (2g + df*h) with
+//     g = sum r*l over the residual r = P_c - P_m and h = sum l^2 (a per-pixel
+//     constant of the table); the best estimate (BoME) is the smallest dS,
+//     lowest index on ties;
+//   * Step 4 compares x = dS/(B*U) with T L (2C + T L), L = -ln N1, which is
+//     N1 < exp(-(C' - C)/T) rearranged;
 //   * on acceptance each lane applies Eq. (6) to its own residual cells.
-// The residual of move m+1 is gathered while move m is being decided and is
-// patched in registers where move m's update touched the same cell.
+// The chain's only loop-carried dependence is kept to a few instructions:
+// move m+1's g is split as Gs + df(m) * OV, where Gs sums the residual as
+// gathered before move m's update and OV sums the products of the two moves'
+// lengths on shared cells; both are reduced across the group while move m is
+// still being decided.
 #pragma once
 #include "common.cuh"
 #include "internal.h"
@@ -32,7 +35,8 @@ namespace satpila {
 struct SatArgs {
     const unsigned char* table;  // PILA records [P][row_records]
     long long row_stride;        // bytes between pixel rows
-    int copy_bytes;              // bytes fetched per move (multiple of 16)
+    int row_chunks;              // 16-byte chunks per row
+    const float* hsum;           // [P] sum of squared stored lengths of each pixel
     int n, U, B;
     int pitch;                   // residual row pitch (B + 1: a private pad cell per row)
     const int32_t* list;         // reconstruction-space pixels (NULL: identity)
@@ -42,10 +46,10 @@ struct SatArgs {
     float beta;
     float inv_BU;
     double inv_BU_d;
-    int J;                       // records per lane in use (<= JMAX)
-    int D;                       // prefetch stages (2..kMaxStages)
+    int D;                       // PILA rows in flight (3..kMaxStages)
+    int W;                       // warps per chain (1, 2 or 4)
     int stage_bytes;             // bytes of one stage buffer
-    int warp_smem_bytes;         // shared memory per warp
+    int group_smem_bytes;        // shared memory per chain group
     long long resid_floats;      // per-chain residual stride (floats, multiple of 4)
     int n_chains;
     float* resid;                // [n_chains][resid_floats]
@@ -68,8 +72,14 @@ struct SatArgs {
 };
 
 constexpr int kSatMaxWarps = 8;
-// Per-warp shared memory header: barriers, stage pixels, the draw ring.
-constexpr int kRingHeader = 128 + 2 * 8 * (32 + 4) * 4;
+constexpr int kMaxGroupWarps = 4;
+constexpr int kBatch = 8;       // moves per block of random draws
+constexpr int kDrawRing = 3 * kBatch;  // the batch in use, the next one, and one being drawn
+constexpr int kDrawRingBytes = kDrawRing * (4 * ((kMaxK + 2 + 3) / 4) + 1) * 4;
+// Shared memory of a chain group: header, one draw ring per warp, then the
+// PILA-row stages and (when resident) the residual.
+constexpr int kGroupHeader = 256;
+__host__ __device__ constexpr int group_ring_bytes(int W) { return kGroupHeader + W * kDrawRingBytes; }
 
 __device__ __forceinline__ double stage_temperature(int schedule, double t0, double tn, int s, int n_sweeps) {
     const double N = (double)n_sweeps, n = (double)s;
@@ -77,9 +87,6 @@ __device__ __forceinline__ double stage_temperature(int schedule, double t0, dou
     if (schedule == SAT_SCHED_CUBIC) return t0 - n * n * n * (t0 - tn) / (N * N * N);
     return t0 - n * (t0 - tn) / N;
 }
-
-constexpr int kBatch = 8;       // moves per block of random draws
-constexpr int kDrawRing = 2 * kBatch;
 
 // Lane-owned decoded records of one move.  Entry 1 always sits on bin k + 1
 // (the builder stores consecutive bins), so only bin 0 is kept.
@@ -90,112 +97,149 @@ struct Recs {
 };
 
 template <bool F16, int JMAX>
-__device__ __forceinline__ void decode_stage(const unsigned char* stage, int lane, int J, Recs<JMAX>& r) {
+__host__ __device__ constexpr int chunks_per_lane() { return F16 ? JMAX / 2 : JMAX; }
+
+// Record index of slot j of group lane gl (= lane + 32 * warp-in-group).
+template <bool F16>
+__device__ __forceinline__ int record_of(int gl, int W, int j) {
+    return F16 ? 2 * (gl + 32 * W * (j / 2)) + (j & 1) : gl + 32 * W * j;
+}
+
+template <bool F16, int JMAX>
+__device__ __forceinline__ void decode_stage(const unsigned char* stage, int gl, int W, Recs<JMAX>& r) {
     const uint4* q4 = reinterpret_cast<const uint4*>(stage);
     if constexpr (F16) {
 #pragma unroll
         for (int i = 0; i < JMAX / 2; ++i) {
-            if (2 * i < J) {
-                const uint4 v = q4[lane + 32 * i];
-                const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-                const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
-                r.k[2 * i] = (int)(v.x & 0xffffu);
-                r.l0[2 * i] = a.x;
-                r.l1[2 * i] = a.y;
-                r.k[2 * i + 1] = (int)(v.z & 0xffffu);
-                r.l0[2 * i + 1] = b.x;
-                r.l1[2 * i + 1] = b.y;
-            }
+            const uint4 v = q4[gl + 32 * W * i];
+            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
+            r.k[2 * i] = (int)(v.x & 0xffffu);
+            r.l0[2 * i] = a.x;
+            r.l1[2 * i] = a.y;
+            r.k[2 * i + 1] = (int)(v.z & 0xffffu);
+            r.l0[2 * i + 1] = b.x;
+            r.l1[2 * i + 1] = b.y;
         }
     } else {
 #pragma unroll
         for (int i = 0; i < JMAX; ++i) {
-            if (i < J) {
-                const uint4 v = q4[lane + 32 * i];
-                r.k[i] = (int)v.x;
-                r.l0[i] = __uint_as_float(v.z);
-                r.l1[i] = __uint_as_float(v.w);
-            }
+            const uint4 v = q4[gl + 32 * W * i];
+            r.k[i] = (int)v.x;
+            r.l0[i] = __uint_as_float(v.z);
+            r.l1[i] = __uint_as_float(v.w);
         }
     }
 }
 
-struct WarpRing {
-    uint64_t* bar;       // [kMaxStages]
-    int* pix;            // [kMaxStages] pixel of the move held by each stage
-    float* draws;        // [kDrawRing][draw_stride]: pixel, L = -ln N1, pad, pad, u_0..u_{K-1}
+struct GroupShared {
+    uint64_t* bar;         // one barrier: the residual's bulk copy at task start
+    float* part;           // [2][kMaxGroupWarps][4] partial (Gs, OV) per move parity
+    volatile int* flags;   // [0] task, [2] progress-wait result
+    uint32_t* draws;       // this warp's ring [kDrawRing][4 * blocks]: raw Philox words
+    int* pix;              // this warp's ring [kDrawRing]: pixel of each move
     unsigned char* stages;
 };
 
-// Waits (bounded) for the copies still in flight after a failure.
-static __device__ __noinline__ void drain_stages(const WarpRing& w, int D, int first_move, int last_move,
-                                                 uint32_t& phase) {
-    for (int mv = first_move; mv <= last_move; ++mv) {
-        const int st = mv % D;
-        mbar_wait_bounded(&w.bar[st], (phase >> st) & 1u);
-        phase ^= 1u << st;
+// Named barrier of the chain group (ids 1.. ; id 0 is the CTA barrier).
+__device__ __forceinline__ void group_sync(int id, int W) {
+    if (W == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(32 * W) : "memory");
     }
 }
 
-__device__ __forceinline__ void cp_async_4(void* smem_dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async_16_pred(bool pred, void* smem_dst, const void* src) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, 0;\n\t"
+        "@p cp.async.cg.shared.global [%1], [%2], 16;\n\t}" ::"r"((uint32_t)pred),
+        "r"(smem_u32(smem_dst)), "l"(src)
+        : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most n of this thread's copy groups are still pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    }
+}
 
-// Random draws of moves [first, first + kBatch) of stage s: one warp-wide
-// Philox pass per 32 (move, block) units.  Draw d = 4*block + word: d = 0 the
-// pixel, d = 1 the acceptance number N1 (stored as L = -ln N1), d = 2 + e the
-// uniform of estimate e.  Pixels of a masked reconstruction space are copied
-// from the pixel list asynchronously.
+// The lane's chunks of a pixel's row into a stage (one copy group).
+template <bool F16, int JMAX>
+__device__ __forceinline__ void fetch_row(const SatArgs& a, unsigned char* stage, int p, int gl, int W) {
+    const unsigned char* row = a.table + (long long)p * a.row_stride;
+#pragma unroll
+    for (int i = 0; i < chunks_per_lane<F16, JMAX>(); ++i) {
+        const int q = gl + 32 * W * i;
+        cp_async_16_pred(q < a.row_chunks, stage + 16 * q, row + 16 * (q < a.row_chunks ? q : 0));
+    }
+    cp_async_commit();
+}
+
 template <int KMAX>
-__device__ __forceinline__ void draw_batch(const SatArgs& a, const WarpRing& w, int s, int first, uint2 key,
-                                           int lane) {
-    constexpr int kStride = KMAX + 4;
+__host__ __device__ constexpr int draw_words() { return 4 * ((KMAX + 2 + 3) / 4); }
+
+// Random draws of moves [first, first + kBatch) of stage s into this warp's
+// ring: one warp-wide Philox pass per 32 (move, block) units, raw words
+// stored as they come.  Draw d = 4*block + word: d = 0 the pixel, d = 1 the
+// acceptance number N1, d = 2 + e the uniform of estimate e.  A pixel of a
+// masked reconstruction space is looked up in the pixel list; `late` keeps
+// that lookup in a register (stored by settle_pixels a few moves later) so
+// the load latency stays off the move loop.
+struct PendingPixel {
+    int slot[3];  // ring slots, or -1 (a lane draws at most one pixel per pass, three passes)
+    int value[3];
+};
+
+template <int KMAX>
+__device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& G, int s, int first, uint2 key,
+                                           int lane, bool late, PendingPixel& pend) {
+    constexpr int kWords = draw_words<KMAX>();
     const int nblk = (a.K + 2 + 3) / 4;
-    const int units = kBatch * nblk;
+    const int units = kBatch * nblk;  // <= 72
     const uint32_t nl = (uint32_t)a.n_list;
-    for (int u0 = 0; u0 < units; u0 += 32) {
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        pend.slot[it] = -1;
+        const int u0 = 32 * it;
+        if (u0 >= units) continue;
         const int unit = u0 + lane;
         const int mv = first + unit / nblk, blk = unit % nblk;
         const uint4 x = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)mv, (uint32_t)blk, kStreamSat), key);
-        if (unit < units && mv < a.moves) {
-            float* rec = w.draws + (mv % kDrawRing) * kStride;
-            const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int d = 4 * blk + i;
-                if (d == 0) {
-                    const uint32_t idx = pick_index(wd[0], nl);
-                    if (a.list) cp_async_4(rec, a.list + idx);
-                    else reinterpret_cast<int*>(rec)[0] = (int)idx;
-                } else if (d == 1) {
-                    rec[1] = -logf(unit_uniform(wd[1]));
-                } else if (d - 2 < a.K) {
-                    rec[4 + d - 2] = unit_uniform(wd[i]);
-                }
+        const bool live = unit < units && mv < a.moves;
+        const int slot = mv % kDrawRing;
+        if (live) *reinterpret_cast<uint4*>(G.draws + slot * kWords + 4 * blk) = x;
+        if (live && blk == 0) {
+            const uint32_t idx = pick_index(x.x, nl);
+            const int p = a.list ? __ldg(a.list + idx) : (int)idx;
+            if (late) {
+                pend.slot[it] = slot;
+                pend.value[it] = p;
+            } else {
+                G.pix[slot] = p;
             }
         }
     }
 }
 
-// Issue of a pixel row into a stage by one lane of the warp (the predicate),
-// without a branch: barrier arrival with the expected bytes, then the copy.
-__device__ __forceinline__ void issue_row_pred(bool pred, uint64_t* bar, void* dst, const void* src,
-                                               uint32_t bytes) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %0, 0;\n\t"
-        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %4;\n\t"
-        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%2], [%3], %4, [%1];\n\t}" ::"r"(
-            (uint32_t)pred),
-        "r"(smem_u32(bar)), "r"(smem_u32(dst)), "l"(src), "r"(bytes)
-        : "memory");
+__device__ __forceinline__ void settle_pixels(const GroupShared& G, PendingPixel& pend) {
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        if (pend.slot[it] >= 0) G.pix[pend.slot[it]] = pend.value[it];
+        pend.slot[it] = -1;
+    }
 }
 
 // Residual values at a move's two entry cells per record.  Every cell index
-// is valid: an empty entry names a real cell of its row (and its length 0
-// keeps it out of every sum), a record past U names a lane-private dummy
-// cell after the residual.  So loads and stores need no predicate.
+// is valid: an empty entry names a cell of its own row (its length 0 keeps
+// it out of every sum), a record past U names a lane-private dummy cell
+// after the residual.  So loads and stores need no predicate.
 template <int JMAX>
 __device__ __forceinline__ void gather(const float* R, const int (&rowbase)[JMAX], const Recs<JMAX>& r,
                                        float (&v0)[JMAX], float (&v1)[JMAX]) {
@@ -207,99 +251,140 @@ __device__ __forceinline__ void gather(const float* R, const int (&rowbase)[JMAX
     }
 }
 
-struct MoveState {
-    int p;       // pixel of the move
-    float f;     // its value as loaded
-    bool fwd;    // the previous move wrote this pixel: use fwd_f instead
-    float fwd_f;
+struct StageCtx {
+    int s, M, D, W, wig, lane, gid, gl;
+    float T;
+    float* R;
+    float* img;
+    uint2 key;
+    bool tracing;
 };
 
-// One move (Steps 2-4 with BoME) whose records/values are (cur, rv), while
-// the next move's (nxt, nv) are gathered.  has_next = false for the last move.
-template <bool F16, int JMAX, int KMAX, bool HAS_NEXT>
-__device__ __forceinline__ bool move_step(const SatArgs& a, const WarpRing& w, int s, int m, int M, float T, float* R,
-                                          float* img, uint2 key, uint32_t& phase, float& S_hi, float& S_lo,
-                                          float& C, unsigned long long& n_acc, int lane, const int (&rowbase)[JMAX],
-                                          int& st_cur, int& issued, bool tracing, const Recs<JMAX>& cur,
-                                          const float (&rv0)[JMAX], const float (&rv1)[JMAX], Recs<JMAX>& nxt,
-                                          float (&nv0)[JMAX], float (&nv1)[JMAX], MoveState& ms) {
-    constexpr int kStride = KMAX + 4;
-    const int D = a.D;
-    const int st_next = st_cur + 1 == D ? 0 : st_cur + 1;
-    const int st_issue = st_cur == 0 ? D - 1 : st_cur - 1;
-    __syncwarp();
-    // Moves [m-kBatch, m) are done: their draw slots take moves [m+kBatch, m+2*kBatch).
-    if ((m & (kBatch - 1)) == 0 && m > 0 && m + kBatch < M) draw_batch<KMAX>(a, w, s, m + kBatch, key, lane);
-    const int mi = m + D - 1;
-    if (mi < M) {
-        if (a.list && (mi & (kBatch - 1)) == 0) {
-            cp_async_wait_all();  // pixels of the batch that starts at mi
-            __syncwarp();
-        }
-        const int pi = reinterpret_cast<const int*>(w.draws + (mi % kDrawRing) * kStride)[0];
-        if (lane == 31) w.pix[st_issue] = pi;
-        issue_row_pred(lane == 31, &w.bar[st_issue], w.stages + (size_t)st_issue * a.stage_bytes,
-                       a.table + (long long)pi * a.row_stride, (uint32_t)a.copy_bytes);
-        if (lane == 31) prefetch_l1(img + pi);
-        issued = mi;
-    }
-    // Draws of this move (independent of the chain state).
-    const float* drec = w.draws + (m % kDrawRing) * kStride;
-    const float L = drec[1];
-    float uc[KMAX];
-#pragma unroll
-    for (int q = 0; q < KMAX; q += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(drec + 4 + q);
-        uc[q] = v.x;
-        if (q + 1 < KMAX) uc[q + 1] = v.y;
-        if (q + 2 < KMAX) uc[q + 2] = v.z;
-        if (q + 3 < KMAX) uc[q + 3] = v.w;
-    }
-    // Partial sums of this move.
-    float g0 = 0.0f, g1 = 0.0f, h0 = 0.0f, h1 = 0.0f;
+// Registers of one move, prepared one move ahead.
+template <int JMAX>
+struct Ahead {
+    Recs<JMAX> r;               // its records
+    float v0[JMAX], v1[JMAX];   // residual at its cells, gathered before the previous move's update
+    float s0[JMAX], s1[JMAX];   // length of the previous move's entry on the same cell (0 if none)
+    float Gs, OV, h;            // sum v*l and sum s*l over the group; sum l^2 of the pixel
+    int p;                      // its pixel
+    float f;                    // its value as loaded (before the previous move's write)
+};
+
+struct ChainRegs {
+    float S_hi, S_lo;  // Kahan-compensated sum of squared residuals
+    float C;           // current cost
+    unsigned long long n_acc;
+    float df_prev;     // value change applied by the previous move (0 if rejected)
+    int p_prev;        // pixel of the previous move
+    float f_prev;      // its value after the previous move
+};
+
+// Loads of move mn's registers (records, stale residual, pixel value and
+// sum of squares); the sums follow in finish_prepare.
+template <bool F16, int JMAX>
+__device__ __forceinline__ void start_prepare(const SatArgs& a, const GroupShared& G, const StageCtx& x,
+                                              const int (&rowbase)[JMAX], const unsigned char* stage, int mn,
+                                              Ahead<JMAX>& n) {
+    n.p = G.pix[mn % kDrawRing];
+    n.f = __ldcg(x.img + n.p);  // L2: never a line another store of this chain left stale in L1
+    n.h = __ldg(a.hsum + n.p);
+    decode_stage<F16, JMAX>(stage, x.gl, x.W, n.r);
+    gather<JMAX>(x.R, rowbase, n.r, n.v0, n.v1);
+}
+
+// Partial sums of move n relative to the previous move's records `prev`,
+// reduced over the warp (the group's warps combine them afterwards).
+template <int JMAX>
+__device__ __forceinline__ void finish_prepare(const Recs<JMAX>* prev, Ahead<JMAX>& n) {
+    float gs0 = 0.0f, gs1 = 0.0f, ov = 0.0f;
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        g0 = fmaf(rv0[j], cur.l0[j], g0);
-        g1 = fmaf(rv1[j], cur.l1[j], g1);
-        h0 = fmaf(cur.l0[j], cur.l0[j], h0);
-        h1 = fmaf(cur.l1[j], cur.l1[j], h1);
-    }
-    float g = g0 + g1, h = h0 + h1;
-    // Gather of the next move while this one is reduced and decided.
-    int p1 = 0;
-    float f1 = 0.0f;
-    if (HAS_NEXT) {
-        if (!mbar_wait_bounded(&w.bar[st_next], (phase >> st_next) & 1u)) {
-            raise_error(a.error, SATPILA_ERR_TIMEOUT);
-            drain_stages(w, D, m + 1, issued, phase);
-            return false;
+        if (prev) {
+            const int d = n.r.k[j] - prev->k[j];
+            n.s0[j] = d == 0 ? prev->l0[j] : (d == 1 ? prev->l1[j] : 0.0f);
+            n.s1[j] = d == 0 ? prev->l1[j] : (d == -1 ? prev->l0[j] : 0.0f);
+        } else {
+            n.s0[j] = n.s1[j] = 0.0f;
         }
-        phase ^= 1u << st_next;
-        p1 = w.pix[st_next];
-        f1 = img[p1];
-        decode_stage<F16, JMAX>(w.stages + (size_t)st_next * a.stage_bytes, lane, JMAX, nxt);
-        gather<JMAX>(R, rowbase, nxt, nv0, nv1);
+        gs0 = fmaf(n.v0[j], n.r.l0[j], gs0);
+        gs1 = fmaf(n.v1[j], n.r.l1[j], gs1);
+        ov = fmaf(n.s0[j], n.r.l0[j], ov);
+        ov = fmaf(n.s1[j], n.r.l1[j], ov);
     }
+    float gs = gs0 + gs1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        g += __shfl_xor_sync(0xffffffffu, g, o);
-        h += __shfl_xor_sync(0xffffffffu, h, o);
+        gs += __shfl_xor_sync(0xffffffffu, gs, o);
+        ov += __shfl_xor_sync(0xffffffffu, ov, o);
     }
-    // Step 4 threshold: with L = -ln N1, N1 < exp(-dC/T) <=> dC < T L
-    // <=> x < T L (2C + T L) for x = dS / (B U) (dC = sqrt(C^2 + x) - C).
-    const float TL = T * L;
-    const float theta = TL * fmaf(2.0f, C, TL);
-    // BoME: every lane evaluates every estimate; smallest dS, lowest index on ties.
-    const float f = ms.fwd ? ms.fwd_f : ms.f;
+    n.Gs = gs;
+    n.OV = ov;
+}
+
+// Combines the warps' sums of a group (fixed order: identical in every warp).
+__device__ __forceinline__ void group_combine(const GroupShared& G, const StageCtx& x, int parity, float& gs,
+                                              float& ov) {
+    float* part = G.part + parity * (4 * kMaxGroupWarps);
+    if (x.lane == 0) {
+        part[4 * x.wig] = gs;
+        part[4 * x.wig + 1] = ov;
+    }
+    group_sync(x.gid, x.W);
+    gs = part[0];
+    ov = part[1];
+    for (int w = 1; w < x.W; ++w) {
+        gs += part[4 * w];
+        ov += part[4 * w + 1];
+    }
+}
+
+// Decides move m (Steps 2-4 with BoME) from its prepared registers `cur`,
+// prepares move m+1 into `nxt`, then applies Eq. (6) for move m.
+template <bool F16, int JMAX, int KMAX, bool HAS_NEXT>
+__device__ __forceinline__ void move_step(const SatArgs& a, const GroupShared& G, const StageCtx& x, int m,
+                                          ChainRegs& cr, const int (&rowbase)[JMAX], PendingPixel& pend,
+                                          Ahead<JMAX>& cur, Ahead<JMAX>& nxt) {
+    constexpr int kWords = draw_words<KMAX>();
+    const int D = x.D, M = x.M;
+    __syncwarp();
+    // Moves [m-kBatch, m) are done: their draw slots take moves [m+2*kBatch, m+3*kBatch).
+    // Their pixels are stored half a batch later, before any of them is used
+    // (the first row fetch of that batch is at least 2*kBatch - D + 1 moves away).
+    if ((m & (kBatch - 1)) == 0 && m + 2 * kBatch < M)
+        draw_batch<KMAX>(a, G, x.s, m + 2 * kBatch, x.key, x.lane, true, pend);
+    if ((m & (kBatch - 1)) == kBatch / 2) settle_pixels(G, pend);
+    if (HAS_NEXT) cp_async_wait_pending(D - 3);  // this lane's chunks of move m+1 have landed
+
+    // ---- loads for move m+1 and the draws of move m (independent of the decision) ----
+    const unsigned char* st_next = G.stages + (size_t)((m + 1) % D) * a.stage_bytes;
+    if (HAS_NEXT) start_prepare<F16, JMAX>(a, G, x, rowbase, st_next, m + 1, nxt);
+    const uint32_t* drw = G.draws + (m % kDrawRing) * kWords;
+    uint32_t raw[KMAX + 2];
+#pragma unroll
+    for (int q = 0; q < KMAX + 2; q += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(drw + q);
+        raw[q] = v.x;
+        if (q + 1 < KMAX + 2) raw[q + 1] = v.y;
+        if (q + 2 < KMAX + 2) raw[q + 2] = v.z;
+        if (q + 3 < KMAX + 2) raw[q + 3] = v.w;
+    }
+
+    // ---- decision of move m: g = Gs + df(m-1) * OV is the loop-carried step ----
+    const float L = -__logf(unit_uniform(raw[1]));
+    const float g = fmaf(cr.df_prev, cur.OV, cur.Gs);
+    const float f = cur.p == cr.p_prev ? cr.f_prev : cur.f;
+    const float TL = x.T * L;
+    const float theta = TL * fmaf(2.0f, cr.C, TL);
     const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
     const float g2 = 2.0f * g;
     float dS[KMAX], fc[KMAX];
     int ci[KMAX];
 #pragma unroll
     for (int e = 0; e < KMAX; ++e) {
-        fc[e] = fmaf(uc[e], span, lo);
+        fc[e] = fmaf(unit_uniform(raw[2 + e]), span, lo);
         const float df = fc[e] - f;
-        dS[e] = e < a.K ? df * fmaf(df, h, g2) : __int_as_float(0x7f800000);
+        dS[e] = e < a.K ? df * fmaf(df, cur.h, g2) : __int_as_float(0x7f800000);
         ci[e] = e;
     }
 #pragma unroll
@@ -313,130 +398,129 @@ __device__ __forceinline__ bool move_step(const SatArgs& a, const WarpRing& w, i
         }
     }
     const float best_dS = dS[0], best_f = fc[0];
-    const float x = best_dS * a.inv_BU;
-    const bool accept = x <= 0.0f || x < theta;
+    const float xs = best_dS * a.inv_BU;
+    const bool accept = xs <= 0.0f || xs < theta;
     const float df = accept ? best_f - f : 0.0f;
-    if (tracing && lane == 0) {
-        const float Cp = sqrtf(fmaxf(0.0f, fmaf(C, C, x)));
-        const float den = Cp + C;
-        const long long idx = (long long)s * M + m;
+
+    // ---- sums of move m+1 (shuffles overlap the decision above) ----
+    if (HAS_NEXT) {
+        finish_prepare<JMAX>(&cur.r, nxt);
+        if (x.W > 1) group_combine(G, x, m & 1, nxt.Gs, nxt.OV);
+    }
+
+    // ---- Eq. (6) for move m on the lane's own cells ----
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        float* q = x.R + rowbase[j] + cur.r.k[j];
+        const float v0 = fmaf(cr.df_prev, cur.s0[j], cur.v0[j]);  // the previous move's update
+        const float v1 = fmaf(cr.df_prev, cur.s1[j], cur.v1[j]);
+        q[0] = fmaf(df, cur.r.l0[j], v0);  // unchanged value when rejected or empty
+        q[1] = fmaf(df, cur.r.l1[j], v1);
+    }
+    const float fnew = accept ? best_f : f;
+    __stcg(x.img + cur.p, fnew);  // every warp of the group writes the same value
+    // Kahan-compensated running sum of squared residuals, and the cost.
+    const float y = (accept ? best_dS : 0.0f) - cr.S_lo;
+    const float t = cr.S_hi + y;
+    cr.S_lo = (t - cr.S_hi) - y;
+    cr.S_hi = t;
+    const float C2 = fmaxf(0.0f, cr.S_hi * a.inv_BU);
+    const float C_before = cr.C;
+    cr.C = accept ? (C2 > 0.0f ? C2 * rsqrtf(C2) : 0.0f) : cr.C;
+    cr.n_acc += accept ? 1ull : 0ull;
+    cr.df_prev = df;
+    cr.p_prev = cur.p;
+    cr.f_prev = fnew;
+
+    // Row of move m+D-1 into the stage that move m-1 used (empty group past the end).
+    const int mi = m + D - 1;
+    const int pi = mi < M ? G.pix[mi % kDrawRing] : 0;
+    if (mi < M) {
+        fetch_row<F16, JMAX>(a, G.stages + (size_t)(mi % D) * a.stage_bytes, pi, x.gl, x.W);
+    } else {
+        cp_async_commit();
+    }
+    if (mi < M && x.lane == 31) prefetch_l1(a.hsum + pi);
+
+    if (x.tracing && x.wig == 0 && x.lane == 0) {
+        const float Cp = sqrtf(fmaxf(0.0f, fmaf(C_before, C_before, xs)));
+        const float den = Cp + C_before;
+        const long long idx = (long long)x.s * M + m;
         if (idx < a.trace_cap) {
             sat_trace_rec r;
-            r.pixel = ms.p;
+            r.pixel = cur.p;
             r.cstar = ci[0];
             r.accepted = accept ? 1 : 0;
             r.pad = 0;
             r.dS = best_dS;
-            r.dC = den > 0.0f ? x / den : 0.0f;
-            r.fnew = accept ? best_f : f;
+            r.dC = den > 0.0f ? xs / den : 0.0f;
+            r.fnew = fnew;
             r.pad2 = 0.0f;
             a.trace[idx] = r;
         }
     }
-    // Eq. (6) on the lane's own residual cells, and the same update on the
-    // already gathered values of the next move where the cells coincide.
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        float* q = R + rowbase[j] + cur.k[j];
-        q[0] = fmaf(df, cur.l0[j], rv0[j]);  // unchanged value when rejected or empty
-        q[1] = fmaf(df, cur.l1[j], rv1[j]);
-        if (HAS_NEXT) {
-            const int d = nxt.k[j] - cur.k[j];
-            const float s0 = d == 0 ? cur.l0[j] : (d == 1 ? cur.l1[j] : 0.0f);
-            const float s1 = d == 0 ? cur.l1[j] : (d == -1 ? cur.l0[j] : 0.0f);
-            nv0[j] = fmaf(df, s0, nv0[j]);
-            nv1[j] = fmaf(df, s1, nv1[j]);
-        }
-    }
-    img[ms.p] = accept ? best_f : f;
-    if (HAS_NEXT) {
-        ms.fwd = p1 == ms.p;  // the value written just above
-        ms.fwd_f = accept ? best_f : f;
-        ms.f = f1;
-        ms.p = p1;
-    }
-    // Kahan-compensated running sum of squared residuals.
-    const float y = (accept ? best_dS : 0.0f) - S_lo;
-    const float t = S_hi + y;
-    S_lo = (t - S_hi) - y;
-    S_hi = t;
-    const float C2 = fmaxf(0.0f, S_hi * a.inv_BU);
-    C = accept ? (C2 > 0.0f ? C2 * rsqrtf(C2) : 0.0f) : C;
-    n_acc += accept ? 1ull : 0ull;
-    st_cur = st_next;
-    return true;
 }
 
-// One temperature stage of one chain.  Returns false if a bounded wait gave up.
-template <bool F16, bool SMEM, int JMAX, int KMAX>
-__device__ __forceinline__ bool run_stage(const SatArgs& a, const WarpRing& w, int c, int s, float T, float* R,
-                                          float* img, uint2 key, uint32_t& phase, float& S_hi, float& S_lo,
-                                          unsigned long long& n_acc, int lane, const int (&rowbase)[JMAX]) {
-    constexpr int kStride = KMAX + 4;
-    const int M = a.moves, D = a.D;
-    if (M <= 0 || a.n_list <= 0) return true;
+// One temperature stage of one chain.
+template <bool F16, int JMAX, int KMAX>
+__device__ __forceinline__ void run_stage(const SatArgs& a, const GroupShared& G, const StageCtx& x, float& S_hi,
+                                          float& S_lo, unsigned long long& n_acc, const int (&rowbase)[JMAX]) {
+    const int M = x.M, D = x.D;
+    if (M <= 0 || a.n_list <= 0) return;
 
     // Prologue: draws of the first two batches, rows of moves 0..D-2 in flight.
-    draw_batch<KMAX>(a, w, s, 0, key, lane);
-    draw_batch<KMAX>(a, w, s, kBatch, key, lane);
-    cp_async_wait_all();
+    PendingPixel pend;
+    draw_batch<KMAX>(a, G, x.s, 0, x.key, x.lane, false, pend);
+    draw_batch<KMAX>(a, G, x.s, kBatch, x.key, x.lane, false, pend);  // leaves pend empty
     __syncwarp();
-    const int pre = min(D - 1, M);
-    for (int j = 0; j < pre; ++j) {
-        const int pj = reinterpret_cast<const int*>(w.draws + (j % kDrawRing) * kStride)[0];
-        if (lane == 31) w.pix[j] = pj;
-        issue_row_pred(lane == 31, &w.bar[j], w.stages + (size_t)j * a.stage_bytes,
-                       a.table + (long long)pj * a.row_stride, (uint32_t)a.copy_bytes);
+    for (int j = 0; j < D - 1; ++j) {
+        if (j < M) fetch_row<F16, JMAX>(a, G.stages + (size_t)j * a.stage_bytes, G.pix[j % kDrawRing], x.gl, x.W);
+        else cp_async_commit();
     }
-    int issued = pre - 1;
-    if (!mbar_wait_bounded(&w.bar[0], phase & 1u)) {
-        raise_error(a.error, SATPILA_ERR_TIMEOUT);
-        drain_stages(w, D, 0, issued, phase);
-        return false;
-    }
-    phase ^= 1u;
+    cp_async_wait_pending(D - 2);  // move 0 has landed
 
-    Recs<JMAX> ra, rb;
-    float a0[JMAX], a1[JMAX], b0[JMAX], b1[JMAX];
+    Ahead<JMAX> A, B;
+    start_prepare<F16, JMAX>(a, G, x, rowbase, G.stages, 0, A);
+    finish_prepare<JMAX>(nullptr, A);
+    if (x.W > 1) {
+        group_combine(G, x, 1, A.Gs, A.OV);
+        group_sync(x.gid, x.W);  // the parity-1 slots are reused by move 1
+    }
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        rb.k[j] = 0;
-        rb.l0[j] = rb.l1[j] = 0.0f;
-        b0[j] = b1[j] = 0.0f;
+        B.r.k[j] = 0;
+        B.r.l0[j] = B.r.l1[j] = B.v0[j] = B.v1[j] = B.s0[j] = B.s1[j] = 0.0f;
     }
-    decode_stage<F16, JMAX>(w.stages, lane, JMAX, ra);
-    gather<JMAX>(R, rowbase, ra, a0, a1);
-    MoveState ms;
-    ms.p = w.pix[0];
-    ms.f = img[ms.p];
-    ms.fwd = false;
-    ms.fwd_f = 0.0f;
-    float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
-    const bool tracing = a.trace && s >= 0 && a.trace_chain >= 0 && c == a.trace_chain;
-    int st_cur = 0;
+    B.Gs = B.OV = B.h = B.f = 0.0f;
+    B.p = 0;
+    ChainRegs cr;
+    cr.S_hi = S_hi;
+    cr.S_lo = S_lo;
+    cr.C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
+    cr.n_acc = n_acc;
+    cr.df_prev = 0.0f;
+    cr.p_prev = -1;
+    cr.f_prev = 0.0f;
     int m = 0;
     // Two moves per trip: the register sets alternate roles, no copies.
     for (; m + 2 < M; m += 2) {
-        if (!move_step<F16, JMAX, KMAX, true>(a, w, s, m, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc, lane,
-                                              rowbase, st_cur, issued, tracing, ra, a0, a1, rb, b0, b1, ms))
-            return false;
-        if (!move_step<F16, JMAX, KMAX, true>(a, w, s, m + 1, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc,
-                                              lane, rowbase, st_cur, issued, tracing, rb, b0, b1, ra, a0, a1, ms))
-            return false;
+        move_step<F16, JMAX, KMAX, true>(a, G, x, m, cr, rowbase, pend, A, B);
+        move_step<F16, JMAX, KMAX, true>(a, G, x, m + 1, cr, rowbase, pend, B, A);
     }
     if (m + 1 < M) {
-        if (!move_step<F16, JMAX, KMAX, true>(a, w, s, m, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc, lane,
-                                              rowbase, st_cur, issued, tracing, ra, a0, a1, rb, b0, b1, ms))
-            return false;
-        return move_step<F16, JMAX, KMAX, false>(a, w, s, m + 1, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc,
-                                                 lane, rowbase, st_cur, issued, tracing, rb, b0, b1, ra, a0, a1, ms);
+        move_step<F16, JMAX, KMAX, true>(a, G, x, m, cr, rowbase, pend, A, B);
+        move_step<F16, JMAX, KMAX, false>(a, G, x, m + 1, cr, rowbase, pend, B, A);
+    } else if (m < M) {
+        move_step<F16, JMAX, KMAX, false>(a, G, x, m, cr, rowbase, pend, A, B);
     }
-    return move_step<F16, JMAX, KMAX, false>(a, w, s, m, M, T, R, img, key, phase, S_hi, S_lo, C, n_acc, lane,
-                                             rowbase, st_cur, issued, tracing, ra, a0, a1, rb, b0, b1, ms);
+    cp_async_wait_pending(0);  // nothing left in flight
+    S_hi = cr.S_hi;
+    S_lo = cr.S_lo;
+    n_acc = cr.n_acc;
 }
 
-// Waits until another warp has finished the chain's earlier stages (at most
-// 20 s of wall time).
+// Waits until another group has finished the chain's earlier stages (at
+// most 20 s of wall time).
 static __device__ __forceinline__ bool wait_progress(const int* flag, int target) {
     const unsigned long long t0 = global_ns();
     for (;;) {
@@ -446,92 +530,129 @@ static __device__ __forceinline__ bool wait_progress(const int* flag, int target
     }
 }
 
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 template <bool F16, bool SMEM, int JMAX, int KMAX>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wb = smem + (size_t)warp * a.warp_smem_bytes;
-    WarpRing w;
-    w.bar = reinterpret_cast<uint64_t*>(wb);
-    w.pix = reinterpret_cast<int*>(wb + 64);
-    w.draws = reinterpret_cast<float*>(wb + 128);
-    w.stages = wb + kRingHeader;
-    float* rs = reinterpret_cast<float*>(w.stages + (size_t)a.D * a.stage_bytes);
+    const int W = a.W;
+    const int grp = warp / W, wig = warp % W;
+    unsigned char* gb = smem + (size_t)grp * a.group_smem_bytes;
+    GroupShared G;
+    G.bar = reinterpret_cast<uint64_t*>(gb);
+    G.part = reinterpret_cast<float*>(gb + 64);  // 2 * 4 * 4 floats
+    G.flags = reinterpret_cast<volatile int*>(gb + 192);
+    G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * kDrawRingBytes);
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * kDrawRingBytes + kDrawRing * 4);
+    G.stages = gb + group_ring_bytes(W);
+    float* rs = reinterpret_cast<float*>(G.stages + (size_t)a.D * a.stage_bytes);
+    const int gid = 1 + grp;
+    const int gl = lane + 32 * wig;  // lane index within the group
 
-    // Stage tails beyond a row stay zero (length 0 = no contribution).
-    for (int e = lane; e < a.D * a.stage_bytes / 16; e += 32)
-        reinterpret_cast<uint4*>(w.stages)[e] = make_uint4(0u, 0u, 0u, 0u);
-    if (lane == 0)
-        for (int d = 0; d < a.D; ++d) mbar_init(&w.bar[d], 1);
+    // Stage chunks past a row stay zero (length 0 = no contribution).
+    for (int e = gl; e < a.D * a.stage_bytes / 16; e += 32 * W)
+        reinterpret_cast<uint4*>(G.stages)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (gl == 0) {
+        mbar_init(G.bar, 1);
+        for (int i = 0; i < 8; ++i) G.flags[i] = 0;
+    }
     fence_proxy_async_smem();
-    if (lane == 0) fence_barrier_init();
-    __syncwarp();
+    if (gl == 0) fence_barrier_init();
+    group_sync(gid, W);
 
-    // Residual row offsets of the lane's angles.
+    // Residual row offsets of the lane's angles; records past U use the
+    // lane's two dummy cells after the residual rows.
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        const int u = F16 ? 2 * (lane + 32 * (j / 2)) + (j & 1) : lane + 32 * j;
-        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * lane;  // past U: this lane's dummy cells
+        const int u = record_of<F16>(gl, W, j);
+        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * gl;
     }
 
     uint32_t phase = 0;
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.task_counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        if (gl == 0) G.flags[0] = atomicAdd(a.task_counter, 1);
+        group_sync(gid, W);
+        const int t = G.flags[0];
+        group_sync(gid, W);
         if (t >= a.n_tasks) break;
         const int c = t % a.n_chains;
         const int blk = t / a.n_chains;
         const int s0 = a.sweep_begin + blk * a.sweeps_per_task;
         const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
         if (blk > 0) {
-            int ok = 1;
-            if (lane == 0) ok = wait_progress(&a.progress[c], s0) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (gl == 0) G.flags[2] = wait_progress(&a.progress[c], s0) ? 1 : 0;
+            group_sync(gid, W);
+            const int ok = G.flags[2];
+            group_sync(gid, W);
             if (!ok) {
-                raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                if (gl == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
                 break;
             }
         }
         float* gres = a.resid + (long long)c * a.resid_floats;
         float* R = SMEM ? rs : gres;
         if (SMEM) {
-            const float4* src = reinterpret_cast<const float4*>(gres);
-            float4* dst = reinterpret_cast<float4*>(rs);
-            for (long long e = lane; e < a.resid_floats / 4; e += 32) dst[e] = src[e];
-            __syncwarp();
+            // Residual into shared memory with one bulk copy (TMA).
+            int ok = 1;
+            if (gl == 0) {
+                fence_proxy_async_global();  // written by generic stores of an earlier task
+                mbar_arrive_expect_tx(G.bar, (uint32_t)(a.resid_floats * 4));
+                bulk_copy_g2s(rs, gres, (uint32_t)(a.resid_floats * 4), G.bar);
+                ok = mbar_wait_bounded(G.bar, phase) ? 1 : 0;
+                G.flags[2] = ok;
+            }
+            group_sync(gid, W);
+            ok = G.flags[2];
+            group_sync(gid, W);
+            if (!ok) {
+                if (gl == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                break;
+            }
+            // every group lane observes the completed phase before reading
+            mbar_wait_bounded(G.bar, phase);
+            phase ^= 1u;
         }
         const double S = a.S[c];
         float S_hi = (float)S;
         float S_lo = -(float)(S - (double)S_hi);  // Kahan carries the negated remainder
         unsigned long long n_acc = 0;
-        const uint2 key = chain_key(a.seed + (unsigned long long)c);
-        float* img = a.img + (long long)c * a.img_stride;
+        StageCtx x;
+        x.M = a.moves;
+        x.D = a.D;
+        x.W = W;
+        x.wig = wig;
+        x.lane = lane;
+        x.gid = gid;
+        x.gl = gl;
+        x.R = R;
+        x.img = a.img + (long long)c * a.img_stride;
+        x.key = chain_key(a.seed + (unsigned long long)c);
+        x.tracing = a.trace != nullptr && c == a.trace_chain;
         const double T0 = a.T0[c], TN = a.TN[c];
-        bool ok = true;
-        for (int s = s0; s < s1 && ok; ++s) {
-            const float T = (float)stage_temperature(a.schedule, T0, TN, s, a.n_sweeps_total);
-            ok = run_stage<F16, SMEM, JMAX, KMAX>(a, w, c, s, T, R, img, key, phase, S_hi, S_lo, n_acc, lane,
-                                                  rowbase);
-            if (a.sweep_cost && lane == 0)
-                a.sweep_cost[(long long)c * a.n_sweeps_total + s] =
-                    sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
+        for (int s = s0; s < s1; ++s) {
+            x.s = s;
+            x.T = (float)stage_temperature(a.schedule, T0, TN, s, a.n_sweeps_total);
+            run_stage<F16, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
+            if (a.sweep_cost && gl == 0)
+                a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
         }
-        __syncwarp();
+        group_sync(gid, W);
         if (SMEM) {
             const float4* src = reinterpret_cast<const float4*>(rs);
             float4* dst = reinterpret_cast<float4*>(gres);
-            for (long long e = lane; e < a.resid_floats / 4; e += 32) dst[e] = src[e];
+            for (long long e = gl; e < a.resid_floats / 4; e += 32 * W) dst[e] = src[e];
         }
-        if (lane == 0) {
+        if (gl == 0) {
             a.S[c] = (double)S_hi - (double)S_lo;
             a.accepted[c] += n_acc;
         }
-        __syncwarp();
         __threadfence();
-        if (lane == 0) st_release(&a.progress[c], s1);
-        if (!ok) break;
+        group_sync(gid, W);
+        if (gl == 0) st_release(&a.progress[c], s1);
     }
 }
 

@@ -165,15 +165,16 @@ def _run_traced(api, p, pm, img0, S, M, **kw):
     return st[0], tr, img.cpu().numpy()[0]
 
 
-def test_sat_lockstep_plain64(api):
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_sat_lockstep_plain64(api, W):
     """The plain 64^2 workload (90 angles, K=1, T0=1e-2 -> 0, 20 stages):
-    every move compared with the oracle."""
+    every move compared with the oracle, for 1, 2 and 4 warps per chain."""
     cfg, n, U, B, ph, pm = _plain64()
     img0 = np.full((n, n), 0.5)
     p = api.pila_build(n, U, B, api.PILA_F32)
     S, M = cfg["n_sweeps"], n * n
     st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=1, t0=cfg["t0"], tn=cfg["tn"], seed=3000,
-                              resync_every=1)
+                              resync_every=1, group_warps=W)
     assert st["status"] == 0 and st["proposed"] == S * M
     _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=1, n_sweeps=S, seed=3000)
     assert rep["moves"] == S * M
@@ -184,8 +185,8 @@ def test_sat_lockstep_plain64(api):
     api.pila_free(p)
 
 
-@pytest.mark.parametrize("K,res", [(8, 0), (8, 2), (32, 2), (3, 0)])
-def test_sat_lockstep_bome_with_mask(api, K, res):
+@pytest.mark.parametrize("K,res,W", [(8, 0, 0), (8, 2, 1), (32, 2, 4), (3, 0, 2)])
+def test_sat_lockstep_bome_with_mask(api, K, res, W):
     """256^2-geometry slice (180 angles, 363 bins) with the disk reconstruction
     space, Gaussian noise, BoME, T0 by Eq. (8): two stages in lockstep."""
     n, U, B = 256, 180, 363
@@ -196,7 +197,7 @@ def test_sat_lockstep_bome_with_mask(api, K, res):
     p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
     S, M = 2, 6000
     st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=K, t0=-1.0, tn=-1.0, seed=3001, moves_per_sweep=M,
-                              residency=res)
+                              residency=res, group_warps=W)
     t0, found = oracle.sat_t0(pm, img0, seed=3001, mask=mask)
     assert found == st["t0_found"] == 200
     assert abs(st["t0"] - t0) <= 1e-4 * t0
@@ -215,7 +216,7 @@ def test_sat_batched_equals_single_and_residency_identical(api):
     sinos = np.stack([oracle.drt(synth.phantom(n, 6, 50 + i), U, B) for i in range(5)]).astype(np.float32)
     img0 = np.stack([synth.initial_image(n, 0.5, mask)] * 5).astype(np.float32)
     p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
-    kw = dict(bome_k=4, n_sweeps=6, t0=-1.0, tn=-1.0, resync_every=2)
+    kw = dict(bome_k=4, n_sweeps=6, t0=-1.0, tn=-1.0, resync_every=2, group_warps=2)
     outs = {}
     for res in (1, 2):
         imgs = dev(img0)
