@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=None, help="override stages (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
+    ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     return ap.parse_args()
 
 
@@ -217,7 +218,7 @@ def main():
     images = init.clone()
     seed0 = synth.slice_seeds(rank * slices)[2]
     run_kw = dict(bome_k=K, n_sweeps=S, t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0,
-                  residency=args.residency)
+                  residency=args.residency, group_warps=args.group_warps)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     info = {}

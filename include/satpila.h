@@ -132,6 +132,8 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
 
 #define SAT_FLAG_NO_GRAPH 1u  /* launch kernels directly instead of a cached CUDA graph */
 #define SAT_FLAG_AUTOTUNE 2u  /* time the launch candidates once per shape and keep the best */
+#define SAT_FLAG_HYBRID 4u    /* with more chains than shared-memory slots, also run chains on
+                                 global-memory warps beside them (same arithmetic) */
 
 typedef struct {
     int32_t pixel;     /* pixel index i*n + j */

@@ -18,7 +18,7 @@ ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS, ERR_BUSY, ERR_NOT_F
 PILA_F32, PILA_F16 = 0, 1
 SAT_SCHED_LINEAR, SAT_SCHED_GEOMETRIC, SAT_SCHED_CUBIC = 0, 1, 2
 SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
-SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE = 1, 2
+SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID = 1, 2, 4
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).

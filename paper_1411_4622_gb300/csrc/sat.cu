@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "sat_sweep.cuh"
+#include "sat_window.cuh"
 
 namespace satpila {
 
@@ -27,19 +28,24 @@ SweepFn sweep_kernel_f32_smem(int jmax, int kmax);
 SweepFn sweep_kernel_f32_glob(int jmax, int kmax);
 SweepFn sweep_kernel_f16_smem(int jmax, int kmax);
 SweepFn sweep_kernel_f16_glob(int jmax, int kmax);
+SweepFn window_kernel(bool f16, bool smem, int jmax, int kmax);
+SweepFn hybrid_kernel(bool f16, int jmax, int kmax);
 
 namespace {
 
-SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax) {
+// kind: 0 pipelined, 1 windowed, 2 hybrid
+SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax, int kind = 0) {
+    if (kind == 1) return window_kernel(f16, smem, jmax, kmax);
+    if (kind == 2) return hybrid_kernel(f16, jmax, kmax);
     if (f16) return smem ? sweep_kernel_f16_smem(jmax, kmax) : sweep_kernel_f16_glob(jmax, kmax);
     return smem ? sweep_kernel_f32_smem(jmax, kmax) : sweep_kernel_f32_glob(jmax, kmax);
 }
 
 int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : 32; }
 
-cudaError_t launch_sweep(bool f16, bool smem, int jmax, int kmax, const SatArgs& a, int grid, int warps,
-                         size_t smem_bytes, cudaStream_t s) {
-    SweepFn k = sweep_kernel(f16, smem, jmax, kmax);
+cudaError_t launch_sweep(bool f16, bool smem, int kind, int jmax, int kmax, const SatArgs& a, int grid,
+                         int warps, size_t smem_bytes, cudaStream_t s) {
+    SweepFn k = sweep_kernel(f16, smem, jmax, kmax, kind);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
@@ -47,8 +53,8 @@ cudaError_t launch_sweep(bool f16, bool smem, int jmax, int kmax, const SatArgs&
     return cudaGetLastError();
 }
 
-int sweep_blocks_per_sm(bool f16, bool smem, int jmax, int kmax, int warps, size_t smem_bytes) {
-    SweepFn k = sweep_kernel(f16, smem, jmax, kmax);
+int sweep_blocks_per_sm(bool f16, bool smem, int kind, int jmax, int kmax, int warps, size_t smem_bytes) {
+    SweepFn k = sweep_kernel(f16, smem, jmax, kmax, kind);
     if (!k) return 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     int nb = 0;
@@ -183,6 +189,8 @@ struct Workspace {
 
 struct Plan {
     bool smem = false;
+    int kind = 0;         // 0 pipelined, 1 windowed (shared-memory residual), 2 hybrid
+    int hybrid_smem_warps = 0, hybrid_glob_bytes = 0;
     int jmax = 4, J = 4, D = 4;
     int W = 1, groups = 1, warps = 1, grid = 1;
     int stage_bytes = 0, group_smem = 0;
@@ -201,6 +209,56 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     auto records_per_lane = [&](int W) {
         return f16 ? 2 * ((p->row_records + 64 * W - 1) / (64 * W)) : (p->U + 32 * W - 1) / (32 * W);
     };
+    // rows of B + 1 cells (the last one private to the row's lane), then
+    // 2 dummy cells per lane of a group
+    pl->resid_floats = (long long)align_up((size_t)p->U * (p->B + 1) + 64 * kMaxGroupWarps, 4);
+    // The windowed kernel: one warp per chain; residual in shared memory, in
+    // global memory, or both kinds of warp side by side (hybrid).
+    if (prm->group_warps <= 1 && records_per_lane(1) <= 4 && prm->pipeline_depth == 0) {
+        const int jw = records_per_lane(1) <= 2 ? 2 : 4;
+        const int stage = 512 * (f16 ? jw / 2 : jw);
+        const size_t ring1 = group_ring_bytes(1) + (size_t)2 * kWin * stage;
+        const size_t gsm = align_up(ring1 + (size_t)pl->resid_floats * 4, 128);  // shared-memory warp
+        const size_t glob = align_up(ring1, 128);                                   // global-memory warp
+        const int kmax = kmax_for(prm->bome_k);
+        pl->W = 1;
+        pl->J = pl->jmax = jw;
+        pl->D = 4;
+        pl->stage_bytes = stage;
+        auto finish = [&](int kind, bool smem, int warps, size_t smem_bytes, bool dynamic_tasks) {
+            pl->kind = kind;
+            pl->smem = smem;
+            pl->groups = warps;
+            pl->warps = warps;
+            int per_sm = sweep_blocks_per_sm(f16, smem, kind, jw, kmax, warps, smem_bytes);
+            if (per_sm < 1) per_sm = 1;
+            const long long slots = (long long)sms * per_sm * warps;
+            pl->spt = (!dynamic_tasks && n_chains <= slots) ? window : 1;
+            const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
+            const long long want = (std::min<long long>(tasks, slots) + warps - 1) / warps;
+            pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
+            return SATPILA_OK;
+        };
+        const int win_per_cta = (int)std::min<size_t>(kSatMaxWarps, maxopt / gsm);
+        if (prm->residency == SAT_RESIDENT_GLOBAL || (prm->residency == SAT_RESIDENT_AUTO && win_per_cta == 0)) {
+            pl->group_smem = (int)glob;
+            const int warps = std::min(4, std::max(1, n_chains));
+            return finish(1, false, warps, (size_t)warps * glob, false);
+        }
+        if (win_per_cta == 0) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: residual does not fit in shared memory");
+        const int ns = std::min(win_per_cta, 3), ng = 4 - ns;
+        if ((prm->flags & SAT_FLAG_HYBRID) && ng > 0 && n_chains > sms * win_per_cta &&
+            (size_t)ns * gsm + (size_t)ng * glob <= (size_t)maxopt) {
+            pl->group_smem = (int)gsm;
+            pl->hybrid_smem_warps = ns;
+            pl->hybrid_glob_bytes = (int)glob;
+            // stage-sized tasks, so that chains move between the two kinds of warp
+            return finish(2, true, ns + ng, (size_t)ns * gsm + (size_t)ng * glob, true);
+        }
+        pl->group_smem = (int)gsm;
+        const int warps = std::min(win_per_cta, std::max(1, n_chains));
+        return finish(1, true, warps, (size_t)warps * gsm, false);
+    }
     int W = prm->group_warps > 0 ? prm->group_warps : 1;
     if (prm->group_warps <= 0)
         while (W < kMaxGroupWarps && records_per_lane(W) > 2) W *= 2;
@@ -243,7 +301,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->groups = groups;
     pl->warps = groups * W;
     const size_t smem_bytes = (size_t)groups * pl->group_smem;
-    int per_sm = sweep_blocks_per_sm(f16, smem, jmax, kmax_for(prm->bome_k), pl->warps, smem_bytes);
+    int per_sm = sweep_blocks_per_sm(f16, smem, 0, jmax, kmax_for(prm->bome_k), pl->warps, smem_bytes);
     if (per_sm < 1) per_sm = 1;
     const long long slots = (long long)sms * per_sm * groups;
     pl->spt = n_chains <= slots ? window : 1;
@@ -446,6 +504,8 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         sa.stage_bytes = pl.stage_bytes;
         sa.W = pl.W;
         sa.group_smem_bytes = pl.group_smem;
+        sa.hybrid_smem_warps = pl.hybrid_smem_warps;
+        sa.hybrid_glob_bytes = pl.hybrid_glob_bytes;
         sa.resid_floats = pl.resid_floats;
         sa.n_chains = n_chains;
         sa.resid = ws.resid;
@@ -470,9 +530,12 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             sa.sweeps_per_task = pl.spt;
             sa.n_tasks = n_chains * ((sa.sweep_end - sa.sweep_begin + pl.spt - 1) / pl.spt);
             sa.task_counter = ws.counters + wdx;
-            const size_t smem_bytes = (size_t)pl.groups * pl.group_smem;
+            const size_t smem_bytes = pl.kind == 2 ? (size_t)pl.hybrid_smem_warps * pl.group_smem +
+                                                         (size_t)(pl.warps - pl.hybrid_smem_warps) * pl.hybrid_glob_bytes
+                                                   : (size_t)pl.groups * pl.group_smem;
             cudaEventRecord(evs[2 * wdx], q);
-            err = launch_sweep(pa.f16, pl.smem, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid, pl.warps, smem_bytes, q);
+            err = launch_sweep(pa.f16, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid, pl.warps,
+                               smem_bytes, q);
             if (err != cudaSuccess) return err;
             cudaEventRecord(evs[2 * wdx + 1], q);
             const bool last = wdx + 1 == n_windows;

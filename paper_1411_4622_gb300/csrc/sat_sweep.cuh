@@ -49,7 +49,9 @@ struct SatArgs {
     int D;                       // PILA rows in flight (3..kMaxStages)
     int W;                       // warps per chain (1, 2 or 4)
     int stage_bytes;             // bytes of one stage buffer
-    int group_smem_bytes;        // shared memory per chain group
+    int group_smem_bytes;        // shared memory per chain group (per shared-memory warp in the hybrid kernel)
+    int hybrid_smem_warps;       // hybrid kernel: warps with a shared-memory residual
+    int hybrid_glob_bytes;       // hybrid kernel: shared memory of each global-residual warp
     long long resid_floats;      // per-chain residual stride (floats, multiple of 4)
     int n_chains;
     float* resid;                // [n_chains][resid_floats]
@@ -534,13 +536,11 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Task loop of one chain group (W warps; grp numbers the group in its CTA,
+// gb is its shared memory).
 template <bool F16, bool SMEM, int JMAX, int KMAX>
-__global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int W = a.W;
-    const int grp = warp / W, wig = warp % W;
-    unsigned char* gb = smem + (size_t)grp * a.group_smem_bytes;
+__device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* gb, int grp, int W, int wig,
+                                               int lane) {
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
     G.part = reinterpret_cast<float*>(gb + 64);  // 2 * 4 * 4 floats
@@ -654,6 +654,15 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
         group_sync(gid, W);
         if (gl == 0) st_release(&a.progress[c], s1);
     }
+}
+
+template <bool F16, bool SMEM, int JMAX, int KMAX>
+__global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = a.W;
+    const int grp = warp / W;
+    pipeline_group<F16, SMEM, JMAX, KMAX>(a, smem + (size_t)grp * a.group_smem_bytes, grp, W, warp % W, lane);
 }
 
 // ---- Eq. (8): initial temperature ------------------------------------------

@@ -1,0 +1,412 @@
+// Windowed form of the annealing move for one warp per chain, with the
+// residual in shared memory or in global memory (identical arithmetic).
+//
+// Moves are still decided one after the other, each on the exact state left
+// by all earlier moves; what changes is how that state is read.  For a window
+// of kWin consecutive moves j (their pixels do not depend on the chain state)
+// the warp gathers every move's residual cells at the start of the window and
+// reduces, in one batch of independent shuffles,
+//   Gs_j = sum over j's entries of r * l_j          (residual at window start)
+//   OV_ij = sum over cells shared by i and j of l_i * l_j        (i < j).
+// Because Eq. (6) adds df_i * l_i on move i's cells, the sum that move j's
+// Eq. (7) needs is exactly  g_j = Gs_j + sum_{i<j} df_i * OV_ij.  Each
+// decision then costs a few FMAs plus the BoME selection.  Afterwards each
+// cell of move j is written with its gathered value plus the updates of the
+// moves i <= j that touched it (each lane owns its cells, so no
+// synchronisation; a cell several moves touch is rewritten in move order).
+#pragma once
+#include "sat_sweep.cuh"
+
+namespace satpila {
+
+constexpr int kWin = 4;
+constexpr int kPairs = kWin * (kWin - 1) / 2;
+
+// For slot s, the lengths that move i (records ki, a0, a1) puts on the two
+// cells of move j (bins kj, kj + 1); entry 1 of a record sits on bin k + 1.
+__device__ __forceinline__ void cell_share(int ki, float a0, float a1, int kj, float& s0, float& s1) {
+    const int d = kj - ki;
+    s0 = d == 0 ? a0 : (d == 1 ? a1 : 0.0f);
+    s1 = d == 0 ? a1 : (d == -1 ? a0 : 0.0f);
+}
+
+template <bool F16, bool SMEM, int JMAX, int KMAX>
+__device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupShared& G, const StageCtx& x,
+                                                 float& S_hi, float& S_lo, unsigned long long& n_acc,
+                                                 const int (&rowbase)[JMAX]) {
+    constexpr int kWords = draw_words<KMAX>();
+    const int M = x.M;
+    if (M <= 0 || a.n_list <= 0) return;
+    const int nwin = (M + kWin - 1) / kWin;
+    auto stage_of = [&](int w, int j) { return G.stages + (size_t)((w & 1) * kWin + j) * a.stage_bytes; };
+    auto fetch_window = [&](int w) {
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            const int mv = w * kWin + j;
+            if (mv < M) {
+                const unsigned char* row = a.table + (long long)G.pix[mv % kDrawRing] * a.row_stride;
+                unsigned char* st = stage_of(w, j);
+#pragma unroll
+                for (int i = 0; i < chunks_per_lane<F16, JMAX>(); ++i) {
+                    const int q = x.gl + 32 * i;
+                    cp_async_16_pred(q < a.row_chunks, st + 16 * q, row + 16 * (q < a.row_chunks ? q : 0));
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    PendingPixel pend;
+    draw_batch<KMAX>(a, G, x.s, 0, x.key, x.lane, false, pend);
+    draw_batch<KMAX>(a, G, x.s, kBatch, x.key, x.lane, false, pend);
+    __syncwarp();
+    fetch_window(0);
+    // Pixel values of the next window are loaded before this window's
+    // writes and forwarded from them where a pixel repeats.
+    int pn[kWin];
+    float fn[kWin];
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) {
+        pn[j] = j < M ? G.pix[j % kDrawRing] : -1;
+        fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
+    }
+    int pw_prev[kWin];
+    float fw_prev[kWin];
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) {
+        pw_prev[j] = -1;
+        fw_prev[j] = 0.0f;
+    }
+    float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
+
+    for (int w = 0; w < nwin; ++w) {
+        const int m0 = w * kWin;
+        __syncwarp();
+        if ((m0 & (kBatch - 1)) == 0 && m0 + 2 * kBatch < M)
+            draw_batch<KMAX>(a, G, x.s, m0 + 2 * kBatch, x.key, x.lane, true, pend);
+        if ((m0 & (kBatch - 1)) == kBatch / 2) settle_pixels(G, pend);
+        if (w + 1 < nwin) fetch_window(w + 1);
+        else cp_async_commit();
+        // this window's pixels and loaded values; the next window's loads
+        int pc[kWin];
+        float fc0[kWin], hc[kWin];
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            pc[j] = pn[j];
+            fc0[j] = fn[j];
+            hc[j] = pc[j] >= 0 ? __ldg(a.hsum + pc[j]) : 0.0f;
+            const int mv = m0 + kWin + j;
+            pn[j] = mv < M ? G.pix[mv % kDrawRing] : -1;
+            fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
+            if (mv + kWin < M && x.lane == j) prefetch_l1(a.hsum + G.pix[(mv + kWin) % kDrawRing]);
+        }
+        cp_async_wait_pending(1);  // this window's rows have landed
+
+        // ---- records, residual sums and pairwise overlaps of the window ----
+        int k[kWin][JMAX];
+        float l0[kWin][JMAX], l1[kWin][JMAX], v0[kWin][JMAX], v1[kWin][JMAX];
+        float sh0[kPairs][JMAX], sh1[kPairs][JMAX];  // cell_share of each pair (i < j)
+        float red[kWin + kPairs];
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            Recs<JMAX> r;
+            decode_stage<F16, JMAX>(stage_of(w, j), x.gl, 1, r);
+#pragma unroll
+            for (int s = 0; s < JMAX; ++s) {
+                k[j][s] = r.k[s];
+                l0[j][s] = r.l0[s];
+                l1[j][s] = r.l1[s];
+                const float* q = x.R + rowbase[s] + r.k[s];
+                if (SMEM) {
+                    v0[j][s] = q[0];
+                    v1[j][s] = q[1];
+                } else {
+                    v0[j][s] = __ldcg(q);
+                    v1[j][s] = __ldcg(q + 1);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            float g0 = 0.0f, g1 = 0.0f;
+#pragma unroll
+            for (int s = 0; s < JMAX; ++s) {
+                g0 = fmaf(v0[j][s], l0[j][s], g0);
+                g1 = fmaf(v1[j][s], l1[j][s], g1);
+            }
+            red[j] = g0 + g1;
+        }
+        {
+            int e = 0;
+#pragma unroll
+            for (int i = 0; i < kWin; ++i)
+#pragma unroll
+                for (int j = i + 1; j < kWin; ++j) {
+                    float ov = 0.0f;
+#pragma unroll
+                    for (int s = 0; s < JMAX; ++s) {
+                        cell_share(k[i][s], l0[i][s], l1[i][s], k[j][s], sh0[e][s], sh1[e][s]);
+                        ov = fmaf(sh0[e][s], l0[j][s], ov);
+                        ov = fmaf(sh1[e][s], l1[j][s], ov);
+                    }
+                    red[kWin + e] = ov;
+                    ++e;
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int e = 0; e < kWin + kPairs; ++e) red[e] += __shfl_xor_sync(0xffffffffu, red[e], o);
+
+        // ---- decisions, in move order ----
+        float df[kWin], fnew[kWin];
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            const int m = m0 + j;
+            const bool live = m < M;
+            float g = red[j];
+            {
+                int e = kWin;
+#pragma unroll
+                for (int i = 0; i < kWin; ++i)
+#pragma unroll
+                    for (int jj = i + 1; jj < kWin; ++jj) {
+                        if (jj == j) g = fmaf(df[i], red[e], g);
+                        ++e;
+                    }
+            }
+            // current value of the pixel: latest earlier write in this window,
+            // else in the previous window, else the loaded value
+            float f = fc0[j];
+#pragma unroll
+            for (int i = 0; i < kWin; ++i) f = pw_prev[i] == pc[j] ? fw_prev[i] : f;
+#pragma unroll
+            for (int i = 0; i < kWin; ++i)
+                if (i < j) f = pc[i] == pc[j] ? fnew[i] : f;
+            const uint32_t* drw = G.draws + (m % kDrawRing) * kWords;
+            const float L = -__logf(unit_uniform(drw[1]));
+            const float TL = x.T * L;
+            const float theta = TL * fmaf(2.0f, C, TL);
+            const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
+            const float g2 = 2.0f * g;
+            float dS[KMAX], fcand[KMAX];
+            int ci[KMAX];
+#pragma unroll
+            for (int e = 0; e < KMAX; ++e) {
+                fcand[e] = fmaf(unit_uniform(drw[2 + e]), span, lo);
+                const float d = fcand[e] - f;
+                dS[e] = e < a.K ? d * fmaf(d, hc[j], g2) : __int_as_float(0x7f800000);
+                ci[e] = e;
+            }
+#pragma unroll
+            for (int width = 1; width < KMAX; width *= 2) {
+#pragma unroll
+                for (int e = 0; e + width < KMAX; e += 2 * width) {
+                    const bool take = dS[e + width] < dS[e];
+                    dS[e] = take ? dS[e + width] : dS[e];
+                    fcand[e] = take ? fcand[e + width] : fcand[e];
+                    ci[e] = take ? ci[e + width] : ci[e];
+                }
+            }
+            const float xs = dS[0] * a.inv_BU;
+            const bool accept = live && (xs <= 0.0f || xs < theta);
+            df[j] = accept ? fcand[0] - f : 0.0f;
+            fnew[j] = accept ? fcand[0] : f;
+            if (x.tracing && live && x.lane == 0) {
+                const float Cp = sqrtf(fmaxf(0.0f, fmaf(C, C, xs)));
+                const float den = Cp + C;
+                const long long idx = (long long)x.s * M + m;
+                if (idx < a.trace_cap) {
+                    sat_trace_rec rr;
+                    rr.pixel = pc[j];
+                    rr.cstar = ci[0];
+                    rr.accepted = accept ? 1 : 0;
+                    rr.pad = 0;
+                    rr.dS = dS[0];
+                    rr.dC = den > 0.0f ? xs / den : 0.0f;
+                    rr.fnew = fnew[j];
+                    rr.pad2 = 0.0f;
+                    a.trace[idx] = rr;
+                }
+            }
+            const float y = (accept ? dS[0] : 0.0f) - S_lo;
+            const float t = S_hi + y;
+            S_lo = (t - S_hi) - y;
+            S_hi = t;
+            const float C2 = fmaxf(0.0f, S_hi * a.inv_BU);
+            C = accept ? (C2 > 0.0f ? C2 * rsqrtf(C2) : 0.0f) : C;
+            n_acc += accept ? 1ull : 0ull;
+        }
+
+        // ---- Eq. (6) for the window's moves, in order, on the lane's own cells:
+        // gathered value + updates of the earlier moves of the window on the
+        // same cell + this move's update (unchanged value where nothing moved) ----
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+#pragma unroll
+            for (int s = 0; s < JMAX; ++s) {
+                float c0 = v0[j][s], c1 = v1[j][s];
+                int e = 0;
+#pragma unroll
+                for (int i = 0; i < kWin; ++i)
+#pragma unroll
+                    for (int jj = i + 1; jj < kWin; ++jj) {
+                        if (jj == j) {
+                            c0 = fmaf(df[i], sh0[e][s], c0);
+                            c1 = fmaf(df[i], sh1[e][s], c1);
+                        }
+                        ++e;
+                    }
+                float* q = x.R + rowbase[s] + k[j][s];
+                if (SMEM) {
+                    q[0] = fmaf(df[j], l0[j][s], c0);
+                    q[1] = fmaf(df[j], l1[j][s], c1);
+                } else {
+                    __stcg(q, fmaf(df[j], l0[j][s], c0));
+                    __stcg(q + 1, fmaf(df[j], l1[j][s], c1));
+                }
+            }
+            if (pc[j] >= 0) __stcg(x.img + pc[j], fnew[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            pw_prev[j] = pc[j];
+            fw_prev[j] = fnew[j];
+        }
+    }
+    cp_async_wait_pending(0);
+}
+
+// Task loop of one warp with its residual in shared memory (gb, window_bytes
+// of shared memory; barrier id 1 + warp).
+template <bool F16, bool SMEM, int JMAX, int KMAX>
+__device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb, int warp, int lane) {
+    GroupShared G;
+    G.bar = reinterpret_cast<uint64_t*>(gb);
+    G.part = reinterpret_cast<float*>(gb + 64);
+    G.flags = reinterpret_cast<volatile int*>(gb + 192);
+    G.pix = reinterpret_cast<int*>(gb + kGroupHeader);
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + kDrawRing * 4);
+    G.stages = gb + group_ring_bytes(1);
+    float* rs = reinterpret_cast<float*>(G.stages + (size_t)2 * kWin * a.stage_bytes);
+
+    for (int e = lane; e < 2 * kWin * a.stage_bytes / 16; e += 32)
+        reinterpret_cast<uint4*>(G.stages)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (lane == 0) {
+        mbar_init(G.bar, 1);
+        for (int i = 0; i < 8; ++i) G.flags[i] = 0;
+    }
+    fence_proxy_async_smem();
+    if (lane == 0) fence_barrier_init();
+    __syncwarp();
+
+    int rowbase[JMAX];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const int u = record_of<F16>(lane, 1, j);
+        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * lane;
+    }
+
+    uint32_t phase = 0;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.task_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.n_tasks) break;
+        const int c = t % a.n_chains;
+        const int blk = t / a.n_chains;
+        const int s0 = a.sweep_begin + blk * a.sweeps_per_task;
+        const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
+        if (blk > 0) {
+            int ok = 1;
+            if (lane == 0) ok = wait_progress(&a.progress[c], s0) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                break;
+            }
+        }
+        float* gres = a.resid + (long long)c * a.resid_floats;
+        if (SMEM) {
+            // Residual into shared memory with one bulk copy (TMA).
+            int ok = 1;
+            if (lane == 0) {
+                fence_proxy_async_global();
+                mbar_arrive_expect_tx(G.bar, (uint32_t)(a.resid_floats * 4));
+                bulk_copy_g2s(rs, gres, (uint32_t)(a.resid_floats * 4), G.bar);
+            }
+            ok = mbar_wait_bounded(G.bar, phase) ? 1 : 0;
+            ok = __all_sync(0xffffffffu, ok);
+            phase ^= 1u;
+            if (!ok) {
+                if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                break;
+            }
+        }
+        const double S = a.S[c];
+        float S_hi = (float)S;
+        float S_lo = -(float)(S - (double)S_hi);
+        unsigned long long n_acc = 0;
+        StageCtx x;
+        x.M = a.moves;
+        x.D = a.D;
+        x.W = 1;
+        x.wig = 0;
+        x.lane = lane;
+        x.gid = 1 + warp;
+        x.gl = lane;
+        x.R = SMEM ? rs : gres;
+        x.img = a.img + (long long)c * a.img_stride;
+        x.key = chain_key(a.seed + (unsigned long long)c);
+        x.tracing = a.trace != nullptr && c == a.trace_chain;
+        const double T0 = a.T0[c], TN = a.TN[c];
+        for (int s = s0; s < s1; ++s) {
+            x.s = s;
+            x.T = (float)stage_temperature(a.schedule, T0, TN, s, a.n_sweeps_total);
+            run_stage_window<F16, SMEM, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
+            if (a.sweep_cost && lane == 0)
+                a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
+        }
+        __syncwarp();
+        if (SMEM) {
+            const float4* src = reinterpret_cast<const float4*>(rs);
+            float4* dst = reinterpret_cast<float4*>(gres);
+            for (long long e = lane; e < a.resid_floats / 4; e += 32) dst[e] = src[e];
+        }
+        if (lane == 0) {
+            a.S[c] = (double)S_hi - (double)S_lo;
+            a.accepted[c] += n_acc;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(&a.progress[c], s1);
+    }
+}
+
+template <bool F16, bool SMEM, int JMAX, int KMAX>
+__global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_kernel(const SatArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    window_warp<F16, SMEM, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
+}
+
+// Both kinds of warp in one CTA, pulling from the same task queue: the first
+// a.hybrid_smem_warps warps keep the residual in shared memory, the others
+// work on it in global memory.  Both run the same windowed arithmetic, so a
+// chain's result does not depend on which warps ran its stages; faster warps
+// simply take more tasks.
+template <bool F16, int JMAX, int KMAX>
+__global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const SatArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ns = a.hybrid_smem_warps;
+    if (warp < ns) {
+        window_warp<F16, true, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
+    } else {
+        const int g = warp - ns;
+        window_warp<F16, false, JMAX, KMAX>(a, smem + (size_t)ns * a.group_smem_bytes + (size_t)g * a.hybrid_glob_bytes,
+                                            warp, lane);
+    }
+}
+
+}  // namespace satpila

@@ -355,3 +355,46 @@ def test_resync_drift_bound_512(api):
     assert abs(st[0]["final_cost_incremental"] - st[0]["final_cost"]) <= 1e-4 * st[0]["final_cost"]
     assert st[0]["final_cost"] < st[0]["initial_cost"]
     api.pila_free(p)
+
+
+def test_window_kernel_identical_in_shared_and_global_memory(api):
+    """The windowed move runs the same arithmetic whichever memory holds the
+    residual, so both residencies give bit-identical chains."""
+    n, U = 40, 36
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    sinos = np.stack([oracle.drt(synth.phantom(n, 6, 70 + i), U, B) for i in range(3)]).astype(np.float32)
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * 3).astype(np.float32)
+    for prec in (0, 1):
+        p = api.pila_build(n, U, B, prec, mask=mask)
+        outs = []
+        for res in (1, 2):
+            imgs = dev(img0)
+            st = api.sat_run(p, dev(sinos), imgs, bome_k=4, n_sweeps=4, seed=5, residency=res, group_warps=1)
+            outs.append((imgs.cpu().numpy(), [s["accepted"] for s in st]))
+        assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+        api.pila_free(p)
+
+
+def test_hybrid_batch_matches_single_chains(api):
+    """More chains than shared-memory slots: the batch runs on shared-memory
+    and global-memory warps side by side, with chains moving between them
+    stage by stage; every chain must still equal its run alone."""
+    n, U = 128, 120
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    C = 330
+    base = [oracle.drt(synth.phantom(n, 8, 90 + i), U, B).astype(np.float32) for i in range(5)]
+    sinos = np.stack([base[i % 5] for i in range(C)])
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * C).astype(np.float32)
+    kw = dict(bome_k=4, n_sweeps=3, moves_per_sweep=400, t0=2e-3, tn=2e-5)
+    imgs = dev(img0)
+    st = api.sat_run(p, dev(sinos), imgs, seed=100, flags=api.SAT_FLAG_HYBRID, **kw)
+    out = imgs.cpu().numpy()
+    for c in (0, 7, 200, C - 1):
+        one = dev(img0[c:c + 1])
+        s1 = api.sat_run(p, dev(sinos[c:c + 1]), one, seed=100 + c, **kw)
+        assert np.array_equal(one.cpu().numpy()[0], out[c]), c
+        assert s1[0]["accepted"] == st[c]["accepted"]
+    api.pila_free(p)
