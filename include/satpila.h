@@ -221,6 +221,31 @@ typedef struct {
 int sirt_run(const satpila_pila* p, int32_t n_slices, const float* sino_meas, float* images,
              const sirt_params* prm, double* costs, void* stream);
 
+/* Size of the static device scratch that sirt_run_noalloc works in. */
+#define SATPILA_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * sirt_run without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * during the call, for instance code running while a stream is captured into
+ * a CUDA graph, processes confined to a memory budget fixed at start-up, or
+ * hosts whose own allocator owns the device.  Instead of allocating scratch,
+ * it works in one statically sized array of this library
+ * (SATPILA_NOALLOC_SCRATCH_BYTES; every GPU that loads the library keeps it
+ * until the process exits).  Same arguments and results as sirt_run, except:
+ *  - sino_meas, images and costs must be device pointers (nothing is staged);
+ *  - the call is asynchronous on `stream` and does not synchronize it;
+ *  - a problem whose scratch (n_slices * U * B floats, partial sums, and the
+ *    factor matrix when the PILA has not cached one) exceeds the array is
+ *    rejected with SATPILA_ERR_INVALID_ARG;
+ *  - the first call on a device looks up the array's device address once,
+ *    so make that first call before any stream capture begins;
+ *  - all calls share the array: calls whose work overlaps on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ */
+int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const float* sino_meas, float* images,
+                     const sirt_params* prm, double* costs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

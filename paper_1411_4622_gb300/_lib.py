@@ -23,7 +23,8 @@ SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["satpila_last_error", "satpila_version", "pila_build", "pila_free", "pila_info", "pila_export",
-           "pila_forward", "pila_sirt_factor", "sat_run", "sirt_run"]
+           "pila_forward", "pila_sirt_factor", "sat_run", "sirt_run", "sirt_run_noalloc"]
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class PilaGeom(C.Structure):
@@ -87,6 +88,7 @@ def load():
         lib.pila_sirt_factor.argtypes = [V, V, V]
         lib.sat_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SatParams), V, V]
         lib.sirt_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
+        lib.sirt_run_noalloc.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
         for name in EXPORTS:
             if name not in ("satpila_last_error", "satpila_version"):
                 getattr(lib, name).restype = C.c_int

@@ -167,3 +167,14 @@ def sirt_run(p: Pila, sino_meas, images, *, n_iter=1, mode=SIRT_SIMULTANEOUS, re
     prm = L.SirtParams(int(n_iter), int(mode), float(relax), 0)
     L.check(L.load().sirt_run(p.handle, n_sl, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
                               C.byref(prm), _ptr(costs, np.float64), _stream(stream)))
+
+
+def sirt_run_noalloc(p: Pila, sino_meas, images, *, n_iter=1, mode=SIRT_SIMULTANEOUS, relax=1.0, costs=None,
+                     stream=None) -> None:
+    """sirt_run for callers that cannot allocate device memory: device
+    tensors only, asynchronous on the stream, scratch in the library's static
+    device array (see include/satpila.h)."""
+    n_sl = int(images.shape[0]) if images.ndim == 3 else 1
+    prm = L.SirtParams(int(n_iter), int(mode), float(relax), 0)
+    L.check(L.load().sirt_run_noalloc(p.handle, n_sl, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
+                                      C.byref(prm), _ptr(costs, np.float64), _stream(stream)))

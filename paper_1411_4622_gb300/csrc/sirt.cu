@@ -12,6 +12,8 @@
 //   reconstruction space in raster order; each pixel's update is written into
 //   the residual through the PILA (Eq. (6)) before the next pixel is read.
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -220,5 +222,159 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(ws);
     if (e != cudaSuccess) return cuda_fail(e, "sirt_run");
+    return SATPILA_OK;
+}
+
+// ---- SIRT without any allocation -------------------------------------------
+//
+// For callers that must not allocate device memory during the call: code
+// that runs while a stream is being captured into a CUDA graph (where an
+// allocation would be invalid), processes that run inside a fixed memory
+// budget handed to them at start-up, and hosts whose own allocator owns all
+// device memory.  The scratch that sirt_run allocates per call lives instead
+// in one statically sized device array of this library, which every GPU that
+// loads the library keeps for the life of the process.
+
+namespace satpila {
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[SATPILA_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the static scratch on the current device.  The array's
+// name on the host is only a stand-in for the symbol, so the address comes
+// from the runtime, once per device (on that device's first call).
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sirt_run_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "sirt_run_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SATPILA_OK;
+}
+
+size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace satpila
+
+extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const float* sino_meas, float* images,
+                                const sirt_params* prm, double* costs, void* stream) {
+    if (!p || !prm || n_slices < 0) return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: bad argument");
+    if (prm->n_iter < 0 || (prm->mode != SIRT_SIMULTANEOUS && prm->mode != SIRT_SEQUENTIAL))
+        return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: bad n_iter or mode");
+    if (n_slices == 0 || prm->n_iter == 0) return SATPILA_OK;
+    if (!sino_meas || !images) return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: null data pointer");
+    if (!is_device_pointer(sino_meas) || !is_device_pointer(images) || (costs && !is_device_pointer(costs)))
+        return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: data must be in device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
+    const int n_iter = prm->n_iter;
+    int A = 0, G = 0;
+    if (projector_plan(p->U, p->B, &A, &G) != SATPILA_OK)
+        return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: too many bins");
+    // Scratch layout: correction or residual, partial sums, costs, and the
+    // factor matrix when the table has not cached one.
+    const bool own_w = p->d_w32 == nullptr;
+    const size_t o_corr = 0;
+    const size_t o_psq = o_corr + round256((size_t)n_slices * cells * 4);
+    const size_t o_cost = o_psq + round256((size_t)n_slices * G * 8);
+    const size_t o_w64 = o_cost + round256((size_t)n_slices * 8);
+    const size_t o_w32 = o_w64 + (own_w ? round256((size_t)cells * 8) : 0);
+    const size_t total = o_w32 + (own_w ? round256((size_t)cells * 4) : 0);
+    if (total > (size_t)SATPILA_NOALLOC_SCRATCH_BYTES)
+        return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: the problem needs " + std::to_string(total) +
+                                                 " bytes of scratch, more than the static " +
+                                                 std::to_string((size_t)SATPILA_NOALLOC_SCRATCH_BYTES));
+    void* base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc != SATPILA_OK) return rc;
+    char* b = (char*)base;
+    float* corr = (float*)(b + o_corr);
+    double* psq = (double*)(b + o_psq);
+    double* cost_now = (double*)(b + o_cost);
+    // The array keeps the previous call's contents: start from zero.
+    cudaError_t e = cudaMemsetAsync(base, 0, total, s);
+
+    ProjArgs pa{};
+    pa.table = p->d_table;
+    pa.f16 = p->precision == PILA_F16;
+    pa.row_records = p->row_records;
+    pa.n = p->n;
+    pa.U = p->U;
+    pa.B = p->B;
+    pa.angles_per_group = A;
+    pa.n_groups = G;
+    const float* w32 = p->d_w32;
+    if (e == cudaSuccess && own_w) {
+        ProjArgs fa = pa;
+        fa.mode = PROJ_FACTOR;
+        fa.mask = p->d_mask;
+        fa.out64 = (double*)(b + o_w64);
+        fa.out32 = (float*)(b + o_w32);
+        e = launch_projector(fa, 1, s);
+        w32 = fa.out32;
+    }
+    pa.img = images;
+    pa.img_stride = P;
+    pa.pm = sino_meas;
+    pa.pm_stride = cells;
+    pa.resid = corr;
+    pa.resid_stride = cells;
+    pa.w = w32;
+    pa.part_sq = psq;
+    ReduceArgs ra{};
+    ra.n_items = n_slices;
+    ra.n_groups = G;
+    ra.part_sq = psq;
+    ra.inv_cells = 1.0 / (double)cells;
+    ra.cost_out = cost_now;
+    ra.cost_stride = 1;
+    const float scale = prm->relax / (float)p->U;
+    auto record_cost = [&](int it) -> cudaError_t {
+        cudaError_t err = launch_reduce(ra, s);
+        if (err == cudaSuccess && costs) {
+            scatter_costs_kernel<<<(n_slices + 127) / 128, 128, 0, s>>>(cost_now, costs, n_slices, n_iter, it);
+            err = cudaGetLastError();
+        }
+        return err;
+    };
+    if (prm->mode == SIRT_SIMULTANEOUS) {
+        pa.mode = PROJ_SIRT;
+        for (int it = 0; it <= n_iter && e == cudaSuccess; ++it) {
+            e = launch_projector(pa, n_slices, s);
+            if (e == cudaSuccess && it > 0) e = record_cost(it - 1);
+            if (e == cudaSuccess && it < n_iter && p->n_mask > 0) {
+                const long long threads = (long long)p->n_mask * 32;
+                dim3 grid((unsigned)((threads + 255) / 256), n_slices);
+                sirt_backproject_kernel<<<grid, 256, 0, s>>>(p->d_table, pa.f16, p->row_records, p->U, p->B,
+                                                             p->d_list, p->n_mask, corr, cells, images, P, scale);
+                e = cudaGetLastError();
+            }
+        }
+    } else {
+        pa.mode = PROJ_RESYNC;
+        pa.drift = 0;
+        e = e == cudaSuccess ? launch_projector(pa, n_slices, s) : e;
+        for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+            const int threads = n_slices * 32;
+            sirt_sequential_kernel<<<(threads + 127) / 128, 128, 0, s>>>(p->d_table, pa.f16, p->row_records, p->U,
+                                                                         p->B, p->d_list, p->n_mask, w32, corr, cells,
+                                                                         images, P, scale, n_slices);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = launch_projector(pa, n_slices, s);
+            if (e == cudaSuccess) e = record_cost(it);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sirt_run_noalloc");
     return SATPILA_OK;
 }
