@@ -121,6 +121,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_hash():
+    """Hash of the CUDA sources; a stored DRAM-traffic figure only applies to them."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1411_4622_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per move of `kernel` from the committed ncu summary, or None
+    when the summary is missing or was taken on different sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}__{WORKLOAD}.md")
+    try:
+        kv = {}
+        for ln in open(path):
+            if ":" in ln and ln.startswith("- "):
+                k, v = ln[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_move"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -304,9 +334,12 @@ def main():
     E = info["entries"] / P
     bytes_per_move = info["row_records"] * info["record_bytes"] + 4 * E * (1 + acc) + 4 * (1 + acc)
     achieved = bytes_per_move * moves_per_step / (statistics.mean(sweep_ms) / 1e3) / 1e9
+    kernel = "sat_window_kernel"
+    tpm = stored_traffic(kernel)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_kind": peak_kind, "kernel": "sat_sweep_kernel",
-            "bytes_per_move": bytes_per_move, "sweep_ms": statistics.mean(sweep_ms)}
+            "traffic": (tpm * moves_per_step) if tpm is not None else None, "peak_kind": peak_kind,
+            "kernel": kernel, "bytes_per_move": bytes_per_move, "sweep_ms": statistics.mean(sweep_ms),
+            "launches_per_step": 1}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
