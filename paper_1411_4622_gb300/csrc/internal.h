@@ -24,6 +24,9 @@ struct satpila_pila {
     double* d_w64 = nullptr;           // SIRT factor matrix [U][B], built on first use
     float* d_w32 = nullptr;
     float* d_hsum = nullptr;           // [P] sum of squared stored lengths of each pixel
+    // Residual band: every cell an annealing move can touch (bins k and k + 1
+    // of each record of a reconstruction-space pixel) has band_lo <= bin <= band_hi.
+    int band_lo = 0, band_hi = 0;
 };
 
 namespace satpila {

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -91,6 +92,31 @@ __global__ void pila_hsum_kernel(const unsigned char* table, int f16, int row_re
     hsum[p] = (float)acc;
 }
 
+// Smallest and largest cell an annealing move can touch: over the records of
+// the reconstruction-space pixels, bin k0 and the cell k0 + 1 that the second
+// entry of a record addresses.
+__global__ void pila_band_kernel(const unsigned char* table, int f16, int row_records, int U, const int32_t* list,
+                                 long long n_list, int* lohi) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int lo = 0x7fffffff, hi = -1;
+    if (idx < n_list * U) {
+        const long long rec = (long long)list[idx / U] * row_records + idx % U;
+        Entry2 e = f16 ? decode_f16(reinterpret_cast<const uint2*>(table)[rec].x,
+                                    reinterpret_cast<const uint2*>(table)[rec].y)
+                       : decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
+        lo = e.k0;
+        hi = e.k0 + 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0 && hi >= 0) {
+        atomicMin(&lohi[0], lo);
+        atomicMax(&lohi[1], hi);
+    }
+}
+
 __global__ void pila_export_kernel(const unsigned char* table, int f16, int row_records, int U, long long P,
                                    int32_t* bins, float* lens) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,13 +185,13 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
         pila_free(p);
         return fail(code, msg);
     };
-    unsigned long long* d_entries = nullptr;
+    unsigned long long* d_entries = nullptr;  // entry count, then the band bounds
     if (cudaMalloc(&p->d_table, p->table_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_list, std::max<size_t>(1, list.size()) * sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&p->d_mask, P) != cudaSuccess || cudaMalloc(&p->d_cos, p->U * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->d_sin, p->U * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->d_hsum, P * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&d_entries, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&d_entries, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         if (d_entries) cudaFree(d_entries);
         return cleanup(SATPILA_ERR_OOM, "pila_build: device allocation failed");
@@ -176,7 +202,10 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_mask, mask.data(), P, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_cos, cs.data(), p->U * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_sin, sn.data(), p->U * sizeof(double), cudaMemcpyHostToDevice, s);
+    const int band_init[2] = {0x7fffffff, -1};
     if (e == cudaSuccess) e = cudaMemsetAsync(d_entries, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_entries + 1, band_init, sizeof(band_init), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const long long total = P * p->row_records;
         const int threads = 256;
@@ -190,15 +219,27 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
                                                                      p->row_records, p->U, P, p->d_hsum);
         e = cudaGetLastError();
     }
-    unsigned long long entries = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&entries, d_entries, sizeof(entries), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !list.empty()) {
+        const long long total = (long long)list.size() * p->U;
+        pila_band_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+            p->d_table, precision == PILA_F16, p->row_records, p->U, p->d_list, (long long)list.size(),
+            reinterpret_cast<int*>(d_entries + 1));
+        e = cudaGetLastError();
+    }
+    unsigned long long entries[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(entries, d_entries, sizeof(entries), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_entries);
     if (e != cudaSuccess) {
         const std::string msg = std::string("pila_build: ") + cudaGetErrorString(e);
         return cleanup(SATPILA_ERR_CUDA, msg);
     }
-    p->entries = (int64_t)entries;
+    p->entries = (int64_t)entries[0];
+    int band[2];
+    std::memcpy(band, &entries[1], sizeof(band));
+    if (list.empty() || band[1] < band[0]) band[0] = 0, band[1] = 1;
+    p->band_lo = std::max(0, band[0]);
+    p->band_hi = std::min(p->B, band[1]);
     *out = p;
     return SATPILA_OK;
 }

@@ -195,6 +195,10 @@ struct Plan {
     int W = 1, groups = 1, warps = 1, grid = 1;
     int stage_bytes = 0, group_smem = 0;
     long long resid_floats = 0;
+    int pitch = 0;               // residual row pitch in global memory (floats, multiple of 4)
+    int band_lo = 0;             // first bin of the shared-memory band (multiple of 4)
+    int band_pitch = 0;          // band row length in shared memory (floats, multiple of 4)
+    long long band_floats = 0;   // shared-memory residual of a windowed warp
     int spt = 1;  // stages per task
 };
 
@@ -209,16 +213,24 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     auto records_per_lane = [&](int W) {
         return f16 ? 2 * ((p->row_records + 64 * W - 1) / (64 * W)) : (p->U + 32 * W - 1) / (32 * W);
     };
-    // rows of B + 1 cells (the last one private to the row's lane), then
-    // 2 dummy cells per lane of a group
-    pl->resid_floats = (long long)align_up((size_t)p->U * (p->B + 1) + 64 * kMaxGroupWarps, 4);
+    // Rows of B + 1 cells (the last one private to the row's lane; rows padded
+    // to 16 bytes), then 2 dummy cells per lane of a group.
+    pl->pitch = (int)align_up((size_t)p->B + 1, 4);
+    pl->resid_floats = (long long)align_up((size_t)p->U * pl->pitch + 64 * kMaxGroupWarps, 4);
+    // A windowed warp keeps in shared memory only the band of bins that moves
+    // can touch (for a disk-shaped reconstruction space about n + 2 of the B
+    // bins), rows 16-byte aligned so that each row is one bulk copy, then 2
+    // dummy cells per lane.
+    pl->band_lo = p->band_lo & ~3;
+    pl->band_pitch = (int)align_up((size_t)(p->band_hi + 1 - pl->band_lo), 4);
+    pl->band_floats = (long long)p->U * pl->band_pitch + 64;
     // The windowed kernel: one warp per chain; residual in shared memory, in
     // global memory, or both kinds of warp side by side (hybrid).
     if (prm->group_warps <= 1 && records_per_lane(1) <= 4 && prm->pipeline_depth == 0) {
         const int jw = records_per_lane(1) <= 2 ? 2 : 4;
         const int stage = 512 * (f16 ? jw / 2 : jw);
         const size_t ring1 = group_ring_bytes(1) + (size_t)2 * kWin * stage;
-        const size_t gsm = align_up(ring1 + (size_t)pl->resid_floats * 4, 128);  // shared-memory warp
+        const size_t gsm = align_up(ring1 + (size_t)pl->band_floats * 4, 128);  // shared-memory warp
         const size_t glob = align_up(ring1, 128);                                   // global-memory warp
         const int kmax = kmax_for(prm->bome_k);
         pl->W = 1;
@@ -277,9 +289,6 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->D = prm->pipeline_depth > 0 ? prm->pipeline_depth : 4;
     if (pl->D < 3 || pl->D > kMaxStages) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: pipeline_depth must be in [3, 8]");
     pl->stage_bytes = 512 * W * (f16 ? jmax / 2 : jmax);  // 16-byte chunks of all lanes
-    // rows of B + 1 cells (the last one private to the row's lane), then
-    // 2 dummy cells per lane of a group
-    pl->resid_floats = (long long)align_up((size_t)p->U * (p->B + 1) + 64 * kMaxGroupWarps, 4);
     const size_t ring = group_ring_bytes(W) + (size_t)pl->D * pl->stage_bytes;
     const size_t smem_group = align_up(ring + (size_t)pl->resid_floats * 4, 128);
     const size_t glob_group = align_up(ring, 128);
@@ -437,7 +446,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         pa.pm_stride = cells;
         pa.resid = ws.resid;
         pa.resid_stride = pl.resid_floats;
-        pa.resid_pitch = p->B + 1;
+        pa.resid_pitch = pl.pitch;
         pa.part_sq = ws.part_sq;
         pa.part_drift = ws.part_drift;
         ReduceArgs ra{};
@@ -462,7 +471,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         ta.n = p->n;
         ta.U = p->U;
         ta.B = p->B;
-        ta.pitch = p->B + 1;
+        ta.pitch = pl.pitch;
         ta.list = p->d_list;
         ta.n_list = p->n_mask;
         ta.beta = prm->beta;
@@ -492,7 +501,10 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         sa.n = p->n;
         sa.U = p->U;
         sa.B = p->B;
-        sa.pitch = p->B + 1;
+        sa.pitch = pl.pitch;
+        sa.band_lo = pl.band_lo;
+        sa.band_pitch = pl.band_pitch;
+        sa.band_floats = pl.band_floats;
         sa.list = p->d_list;
         sa.n_list = p->n_mask;
         sa.moves = M;

@@ -38,7 +38,10 @@ struct SatArgs {
     int row_chunks;              // 16-byte chunks per row
     const float* hsum;           // [P] sum of squared stored lengths of each pixel
     int n, U, B;
-    int pitch;                   // residual row pitch (B + 1: a private pad cell per row)
+    int pitch;                   // residual row pitch (B + 1 rounded up to 4: a private pad cell per row)
+    int band_lo;                 // windowed kernel, shared-memory residual: first bin kept (multiple of 4)
+    int band_pitch;              //   bins kept per row (multiple of 4)
+    long long band_floats;       //   U * band_pitch cells, then 2 dummy cells per lane
     const int32_t* list;         // reconstruction-space pixels (NULL: identity)
     int n_list;
     int moves;                   // M moves per stage

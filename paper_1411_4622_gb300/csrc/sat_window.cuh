@@ -300,11 +300,22 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     if (lane == 0) fence_barrier_init();
     __syncwarp();
 
+    // Cell (u, k) of the residual: R[rowbase + k].  In shared memory only the
+    // band of bins [band_lo, band_lo + band_pitch) is kept, so a row starts
+    // band_lo cells before its first kept cell; every record of a
+    // reconstruction-space pixel addresses cells inside the band.  Lanes past
+    // the last angle address two dummy cells of their own.
+    const int rpitch = SMEM ? a.band_pitch : a.pitch;
+    const int rshift = SMEM ? a.band_lo : 0;
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int u = record_of<F16>(lane, 1, j);
-        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * lane;
+        rowbase[j] = u < a.U ? u * rpitch - rshift : a.U * rpitch + 2 * lane;
+    }
+    if (SMEM) {
+        rs[a.U * rpitch + 2 * lane] = 0.0f;
+        rs[a.U * rpitch + 2 * lane + 1] = 0.0f;
     }
 
     uint32_t phase = 0;
@@ -328,13 +339,19 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         }
         float* gres = a.resid + (long long)c * a.resid_floats;
         if (SMEM) {
-            // Residual into shared memory with one bulk copy (TMA).
+            // The band of every residual row into shared memory, one bulk copy
+            // (TMA) per row, all completing on one barrier phase.
             int ok = 1;
+            const uint32_t row_bytes = (uint32_t)a.band_pitch * 4u;
+            fence_proxy_async_smem();  // earlier generic accesses to the band before the async-proxy writes
+            fence_proxy_async_global();  // the chain's residual as the previous task left it
             if (lane == 0) {
-                fence_proxy_async_global();
-                mbar_arrive_expect_tx(G.bar, (uint32_t)(a.resid_floats * 4));
-                bulk_copy_g2s(rs, gres, (uint32_t)(a.resid_floats * 4), G.bar);
+                mbar_arrive_expect_tx(G.bar, row_bytes * (uint32_t)a.U);
             }
+            __syncwarp();
+            for (int u = lane; u < a.U; u += 32)
+                bulk_copy_g2s(rs + (long long)u * a.band_pitch, gres + (long long)u * a.pitch + a.band_lo, row_bytes,
+                              G.bar);
             ok = mbar_wait_bounded(G.bar, phase) ? 1 : 0;
             ok = __all_sync(0xffffffffu, ok);
             phase ^= 1u;
@@ -369,9 +386,12 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         }
         __syncwarp();
         if (SMEM) {
-            const float4* src = reinterpret_cast<const float4*>(rs);
-            float4* dst = reinterpret_cast<float4*>(gres);
-            for (long long e = lane; e < a.resid_floats / 4; e += 32) dst[e] = src[e];
+            const int q4 = a.band_pitch / 4;
+            for (int e = lane; e < a.U * q4; e += 32) {
+                const int u = e / q4, q = e - u * q4;
+                *reinterpret_cast<float4*>(gres + (long long)u * a.pitch + a.band_lo + 4 * q) =
+                    *reinterpret_cast<const float4*>(rs + (long long)u * a.band_pitch + 4 * q);
+            }
         }
         if (lane == 0) {
             a.S[c] = (double)S_hi - (double)S_lo;

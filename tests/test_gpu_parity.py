@@ -376,6 +376,39 @@ def test_window_kernel_identical_in_shared_and_global_memory(api):
         api.pila_free(p)
 
 
+def test_window_band_residual_off_centre_mask(api):
+    """A shared-memory windowed warp keeps only the band of bins that moves
+    can touch.  With an off-centre rectangular reconstruction space the band
+    is narrow and starts off a 16-byte boundary: the chain must still follow
+    the oracle move by move and equal its run with the residual in global
+    memory."""
+    n, U = 40, 36
+    B = synth.bins_for(n)
+    mask = np.zeros((n, n), np.uint8)
+    mask[5:21, 23:36] = 1
+    ph = synth.phantom(n, 6, 1003) * (0.5 + 0.5 * mask)
+    pm = oracle.drt(ph, U, B)
+    img0 = np.where(mask > 0, 0.5, 0.0)
+    M, S = int(mask.sum()) * 2, 3
+    for prec in (0, 1):
+        p = api.pila_build(n, U, B, prec, mask=mask)
+        outs = []
+        for res in (api.SAT_RESIDENT_SMEM, api.SAT_RESIDENT_GLOBAL):
+            st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=4, t0=1e-3, tn=1e-5, seed=3003,
+                                      moves_per_sweep=M, residency=res, group_warps=1)
+            assert st["status"] == 0
+            outs.append((img, st["accepted"], tr))
+        assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+        assert np.all(outs[0][0][mask == 0] == 0.0)
+        if prec == 0:
+            _, rep = oracle.sat_lockstep(pm, img0, outs[0][2], t0=1e-3, tn=1e-5, bome_k=4, n_sweeps=S, seed=3003,
+                                         moves_per_sweep=M, mask=mask)
+            assert rep["moves"] == S * M
+            assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+            assert rep["max_err_dS"] <= 1e-5, rep
+        api.pila_free(p)
+
+
 def test_hybrid_batch_matches_single_chains(api):
     """More chains than shared-memory slots: the batch runs on shared-memory
     and global-memory warps side by side, with chains moving between them
@@ -384,7 +417,7 @@ def test_hybrid_batch_matches_single_chains(api):
     B = synth.bins_for(n)
     mask = synth.disk_mask(n)
     p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
-    C = 330
+    C = 600
     base = [oracle.drt(synth.phantom(n, 8, 90 + i), U, B).astype(np.float32) for i in range(5)]
     sinos = np.stack([base[i % 5] for i in range(C)])
     img0 = np.stack([synth.initial_image(n, 0.5, mask)] * C).astype(np.float32)
