@@ -219,7 +219,14 @@ __device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& 
         const uint4 x = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)mv, (uint32_t)blk, kStreamSat), key);
         const bool live = unit < units && mv < a.moves;
         const int slot = mv % kDrawRing;
-        if (live) *reinterpret_cast<uint4*>(G.draws + slot * kWords + 4 * blk) = x;
+        // Stored ready for the move: word 0 raw (the pixel), word 1 as
+        // L = -ln N1 of Step 4, the others as the uniforms of the estimates.
+        const float w0 = unit_uniform(x.x), w1 = unit_uniform(x.y);
+        const float w2 = unit_uniform(x.z), w3 = unit_uniform(x.w);
+        const uint4 y = make_uint4(blk == 0 ? x.x : __float_as_uint(w0),
+                                   __float_as_uint(blk == 0 ? -__logf(w1) : w1), __float_as_uint(w2),
+                                   __float_as_uint(w3));
+        if (live) *reinterpret_cast<uint4*>(G.draws + slot * kWords + 4 * blk) = y;
         if (live && blk == 0) {
             const uint32_t idx = pick_index(x.x, nl);
             const int p = a.list ? __ldg(a.list + idx) : (int)idx;
@@ -376,7 +383,7 @@ __device__ __forceinline__ void move_step(const SatArgs& a, const GroupShared& G
     }
 
     // ---- decision of move m: g = Gs + df(m-1) * OV is the loop-carried step ----
-    const float L = -__logf(unit_uniform(raw[1]));
+    const float L = __uint_as_float(raw[1]);
     const float g = fmaf(cr.df_prev, cur.OV, cur.Gs);
     const float f = cur.p == cr.p_prev ? cr.f_prev : cur.f;
     const float TL = x.T * L;
@@ -387,7 +394,7 @@ __device__ __forceinline__ void move_step(const SatArgs& a, const GroupShared& G
     int ci[KMAX];
 #pragma unroll
     for (int e = 0; e < KMAX; ++e) {
-        fc[e] = fmaf(unit_uniform(raw[2 + e]), span, lo);
+        fc[e] = fmaf(__uint_as_float(raw[2 + e]), span, lo);
         const float df = fc[e] - f;
         dS[e] = e < a.K ? df * fmaf(df, cur.h, g2) : __int_as_float(0x7f800000);
         ci[e] = e;

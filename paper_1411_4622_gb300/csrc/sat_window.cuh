@@ -184,7 +184,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             for (int i = 0; i < kWin; ++i)
                 if (i < j) f = pc[i] == pc[j] ? fnew[i] : f;
             const uint32_t* drw = G.draws + (m % kDrawRing) * kWords;
-            const float L = -__logf(unit_uniform(drw[1]));
+            const float L = __uint_as_float(drw[1]);
             const float TL = x.T * L;
             const float theta = TL * fmaf(2.0f, C, TL);
             const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             int ci[KMAX];
 #pragma unroll
             for (int e = 0; e < KMAX; ++e) {
-                fcand[e] = fmaf(unit_uniform(drw[2 + e]), span, lo);
+                fcand[e] = fmaf(__uint_as_float(drw[2 + e]), span, lo);
                 const float d = fcand[e] - f;
                 dS[e] = e < a.K ? d * fmaf(d, hc[j], g2) : __int_as_float(0x7f800000);
                 ci[e] = e;
