@@ -409,8 +409,9 @@ def main():
                           "note": "every slice of a step completes with the step's one launch"},
            "e2e": e2e, "roofline": roof, "clocks": clk,
            # per step: PILA records, per-pixel sums, residual band, 2 resync
-           # projections, 2 reductions, Eq. (8), the sweep, one copy
-           "gpu_launches": args.steps * (1 + 1 + 1 + 2 + 2 + 1 + 1 + 1)}
+           # projections, 2 reductions, Eq. (8), the sweep between two timer
+           # stamps, one copy (the sat_run part as one CUDA graph)
+           "gpu_launches": args.steps * (1 + 1 + 1 + 2 + 2 + 1 + 3 + 1)}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(cfg)
     api.pila_free(pf)

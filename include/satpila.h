@@ -131,7 +131,8 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
 #define SAT_RESIDENT_GLOBAL 2 /* residual sinogram in global memory (L2) */
 
 #define SAT_FLAG_NO_GRAPH 1u  /* launch kernels directly instead of a cached CUDA graph */
-#define SAT_FLAG_AUTOTUNE 2u  /* time the launch candidates once per shape and keep the best */
+#define SAT_FLAG_AUTOTUNE 2u  /* time the launch candidates once per shape and keep the best:
+                                 warps per chain (angle tiling), chains per CTA and residency */
 #define SAT_FLAG_HYBRID 4u    /* with more chains than shared-memory slots, also run chains on
                                  global-memory warps beside them (same arithmetic) */
 
@@ -175,9 +176,24 @@ typedef struct {
     int64_t accepted, proposed;
     int32_t t0_found;         /* uphill samples found for Eq. (8) (0 if T0 was given) */
     int32_t status;           /* 0, or a SATPILA_ERR_* raised on the device */
-    double sweep_ms;          /* device time of the sweep kernels of this call (same for every chain),
-                                 from CUDA events on `stream` */
+    double sweep_ms;          /* device time of the sweep kernels of this call (same for every chain):
+                                 CUDA events on `stream` around each sweep launch (direct launches), or
+                                 the device's global timer read just before and after it (graphs) */
+    int32_t plan;             /* SAT_PLAN_* the launches used */
+    int32_t pad;
 } sat_stats;
+
+/* Launch layouts (sat_stats.plan).  They differ in how chains map onto the
+ * GPU, not in the moves: a layout with one warp per chain uses the windowed
+ * form of the move (exact in-window corrections), the pipelined layouts the
+ * per-move form; both follow Eq. (7) to FP32 rounding. */
+#define SAT_PLAN_RULES 0         /* chosen by size rules (no autotuning) */
+#define SAT_PLAN_WINDOW_SMEM 1   /* one warp per chain, residual band in shared memory */
+#define SAT_PLAN_WINDOW_GLOBAL 2 /* one warp per chain, residual in global memory */
+#define SAT_PLAN_WINDOW_HYBRID 3 /* both kinds of warp in one launch */
+#define SAT_PLAN_PIPE_1 4        /* pipelined, 1 warp per chain */
+#define SAT_PLAN_PIPE_2 5        /* pipelined, 2 warps per chain */
+#define SAT_PLAN_PIPE_4 6        /* pipelined, 4 warps per chain */
 
 /*
  * Anneal n_chains independent slices that share one PILA.  Chain c reads its
@@ -192,6 +208,12 @@ typedef struct {
  * 1); draw 0 picks the pixel, draw 1 is N1, draw 2 + e is estimate e.
  * stats (host, n_chains entries, may be NULL) are filled before return; the
  * call synchronizes `stream` at its end.
+ * Launches: unless SAT_FLAG_NO_GRAPH, a call whose buffers are all device
+ * memory is recorded into a CUDA graph (on a private stream) and launched on
+ * `stream`; the graph and its workspace are kept (a few entries, least
+ * recently used first out, dropped by pila_free) so that repeating the call
+ * with the same table, buffers and parameters replays it.  Calls with host
+ * buffers launch directly.
  * Errors: INVALID_ARG, OOM, CUDA; TIMEOUT/BOUNDS if a device-side check fired
  * (also reported per chain in stats.status).
  */

@@ -19,6 +19,8 @@ PILA_F32, PILA_F16 = 0, 1
 SAT_SCHED_LINEAR, SAT_SCHED_GEOMETRIC, SAT_SCHED_CUBIC = 0, 1, 2
 SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
 SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID = 1, 2, 4
+(SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
+ SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4) = range(7)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).
@@ -56,7 +58,8 @@ class SatStats(C.Structure):
     _fields_ = [("t0", C.c_double), ("tn", C.c_double), ("initial_cost", C.c_double),
                 ("final_cost", C.c_double), ("final_cost_incremental", C.c_double),
                 ("max_resync_drift", C.c_double), ("accepted", C.c_int64), ("proposed", C.c_int64),
-                ("t0_found", C.c_int32), ("status", C.c_int32), ("sweep_ms", C.c_double)]
+                ("t0_found", C.c_int32), ("status", C.c_int32), ("sweep_ms", C.c_double),
+                ("plan", C.c_int32), ("pad", C.c_int32)]
 
 
 class SirtParams(C.Structure):

@@ -89,6 +89,9 @@ struct ReduceArgs {
     double* drift_max;          // per item running max (may be NULL)
 };
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);
+// Sets the projector's launch attributes on the current device; call before
+// capturing launches of it into a graph.
+cudaError_t prepare_projector();
 
 // Builds the SIRT factor matrix of a PILA on first use.
 int ensure_factor(satpila_pila* p, cudaStream_t s);

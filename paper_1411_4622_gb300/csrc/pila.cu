@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "sat_host.h"
 
 namespace satpila {
 namespace {
@@ -246,6 +247,7 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
 
 extern "C" int pila_free(satpila_pila* p) {
     if (!p) return SATPILA_OK;
+    sat_cache_purge(p);
     cudaFree(p->d_table);
     cudaFree(p->d_list);
     cudaFree(p->d_mask);

@@ -14,6 +14,8 @@
 // The fraction bits are chosen per image from max|f| so nothing overflows.
 #include <cmath>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -179,14 +181,26 @@ int projector_plan(int U, int B, int* angles_per_group, int* n_groups) {
     return SATPILA_OK;
 }
 
+// The projector's shared-memory limit, set once per device (before any
+// stream capture that launches it).
+cudaError_t prepare_projector() {
+    static std::mutex mu;
+    static uint64_t done = 0;  // bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 64 && (done >> dev) & 1u) return cudaSuccess;
+    e = cudaFuncSetAttribute(projector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kProjSmemBudget);
+    if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+    return e;
+}
+
 cudaError_t launch_projector(const ProjArgs& a, int n_items, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     const int smem = projector_smem_bytes(a.angles_per_group, a.B);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(projector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kProjSmemBudget);
-        attr_set = true;
-    }
+    cudaError_t e = prepare_projector();
+    if (e != cudaSuccess) return e;
     dim3 grid(a.n_groups, n_items);
     projector_kernel<<<grid, kProjThreads, smem, s>>>(a);
     return cudaGetLastError();

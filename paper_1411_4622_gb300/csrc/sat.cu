@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "sat_host.h"
 #include "sat_sweep.cuh"
 #include "sat_window.cuh"
 
@@ -43,12 +44,11 @@ SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax, int kind = 0) {
 
 int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : 32; }
 
+// The kernel's shared-memory limit must have been set (prepare_launches).
 cudaError_t launch_sweep(bool f16, bool smem, int kind, int jmax, int kmax, const SatArgs& a, int grid,
                          int warps, size_t smem_bytes, cudaStream_t s) {
     SweepFn k = sweep_kernel(f16, smem, jmax, kmax, kind);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e != cudaSuccess) return e;
     k<<<grid, warps * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
@@ -73,20 +73,23 @@ __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
     __shared__ float dcs[32];
     __shared__ double total_s;
     __shared__ int found_s, done_s;
-    if (a.t0_fixed > 0.0) {
+    const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
+    const double t0_fixed = cc ? cc->t0 : a.t0_fixed, tn = cc ? cc->tn : a.tn;
+    const int Q = cc ? (cc->t0_samples > 0 ? cc->t0_samples : 200) : a.Q;
+    if (t0_fixed > 0.0) {
         if (tid == 0) {
-            a.T0[c] = a.t0_fixed;
-            a.TN[c] = a.tn < 0.0 ? a.t0_fixed / 1000.0 : a.tn;
+            a.T0[c] = t0_fixed;
+            a.TN[c] = tn < 0.0 ? t0_fixed / 1000.0 : tn;
             a.found[c] = 0;
         }
         return;
     }
-    const uint2 key = chain_key(a.seed + (unsigned long long)c);
+    const uint2 key = chain_key(cc ? cc->seed : a.seed + (unsigned long long)c);
     const float* R = a.resid + (long long)c * a.resid_floats;
     const float* img = a.img + (long long)c * a.img_stride;
     const float C2 = (float)(a.S[c] * a.inv_BU_d);
     const float C = sqrtf(C2);
-    const long long max_tries = 100LL * a.Q;
+    const long long max_tries = 100LL * Q;
     const uint32_t nl = (uint32_t)a.n_list;
     if (tid == 0) {
         total_s = 0.0;
@@ -139,14 +142,14 @@ __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
         }
         __syncthreads();
         if (tid == 0) {
-            for (int q = 0; q < 32 && found_s < a.Q; ++q) {
+            for (int q = 0; q < 32 && found_s < Q; ++q) {
                 if (base + q >= max_tries) break;
                 if (dcs[q] > 0.0f) {
                     total_s += (double)dcs[q];
                     ++found_s;
                 }
             }
-            if (found_s >= a.Q) done_s = 1;
+            if (found_s >= Q) done_s = 1;
         }
         __syncthreads();
         if (done_s) break;
@@ -155,54 +158,29 @@ __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
         // Eq. (8): T0 = -sum(C' - C) / (Q ln 0.9)
         const double t0 = found_s > 0 ? -total_s / ((double)found_s * log(0.9)) : 0.0;
         a.T0[c] = t0;
-        a.TN[c] = a.tn < 0.0 ? t0 / 1000.0 : a.tn;
+        a.TN[c] = tn < 0.0 ? t0 / 1000.0 : tn;
         a.found[c] = found_s;
     }
 }
+
+// Device global-timer stamp (ns), for timing launches inside a CUDA graph.
+__global__ void stamp_kernel(unsigned long long* out) { *out = global_ns(); }
 
 __global__ void copy_f64_kernel(double* dst, const double* src, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = src[i];
 }
 
+}  // namespace
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-struct Workspace {
-    void* base = nullptr;
-    size_t bytes = 0;
-    float* resid = nullptr;
-    double* S = nullptr;
-    double* T0 = nullptr;
-    double* TN = nullptr;
-    int* found = nullptr;
-    unsigned long long* accepted = nullptr;
-    int* progress = nullptr;
-    int* counters = nullptr;   // one task counter per sweep launch
-    int* error = nullptr;
-    double* part_sq = nullptr;
-    float* part_drift = nullptr;
-    double* drift_max = nullptr;
-    double* cost0 = nullptr;
-    double* costF = nullptr;
-    double* S_inc = nullptr;
-};
+size_t Plan::sweep_smem_bytes() const {
+    return kind == 2 ? (size_t)hybrid_smem_warps * group_smem + (size_t)(warps - hybrid_smem_warps) * hybrid_glob_bytes
+                     : (size_t)groups * group_smem;
+}
 
-struct Plan {
-    bool smem = false;
-    int kind = 0;         // 0 pipelined, 1 windowed (shared-memory residual), 2 hybrid
-    int hybrid_smem_warps = 0, hybrid_glob_bytes = 0;
-    int jmax = 4, J = 4, D = 4;
-    int W = 1, groups = 1, warps = 1, grid = 1;
-    int stage_bytes = 0, group_smem = 0;
-    long long resid_floats = 0;
-    int pitch = 0;               // residual row pitch in global memory (floats, multiple of 4)
-    int band_lo = 0;             // first bin of the shared-memory band (multiple of 4)
-    int band_pitch = 0;          // band row length in shared memory (floats, multiple of 4)
-    long long band_floats = 0;   // shared-memory residual of a windowed warp
-    int spt = 1;  // stages per task
-};
-
-int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, Plan* pl) {
+int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl) {
     const bool f16 = p->precision == PILA_F16;
     int dev = 0, maxopt = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -224,9 +202,24 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->band_lo = p->band_lo & ~3;
     pl->band_pitch = (int)align_up((size_t)(p->band_hi + 1 - pl->band_lo), 4);
     pl->band_floats = (long long)p->U * pl->band_pitch + 64;
+    if (projector_plan(p->U, p->B, &pl->proj_A, &pl->proj_G) != SATPILA_OK)
+        return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many bins");
+    pl->variant = variant;
     // The windowed kernel: one warp per chain; residual in shared memory, in
     // global memory, or both kinds of warp side by side (hybrid).
-    if (prm->group_warps <= 1 && records_per_lane(1) <= 4 && prm->pipeline_depth == 0) {
+    const bool window_ok = records_per_lane(1) <= 4;
+    const bool use_window = variant == PLAN_RULES
+                                ? prm->group_warps <= 1 && window_ok && prm->pipeline_depth == 0
+                                : variant == PLAN_WINDOW_SMEM || variant == PLAN_WINDOW_GLOBAL ||
+                                      variant == PLAN_WINDOW_HYBRID;
+    if (use_window && !window_ok)
+        return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many angles for the windowed kernel");
+    if (use_window) {
+        const int residency = variant == PLAN_WINDOW_SMEM     ? SAT_RESIDENT_SMEM
+                              : variant == PLAN_WINDOW_GLOBAL ? SAT_RESIDENT_GLOBAL
+                                                              : prm->residency;
+        const bool want_hybrid =
+            variant == PLAN_WINDOW_HYBRID || (variant == PLAN_RULES && (prm->flags & SAT_FLAG_HYBRID));
         const int jw = records_per_lane(1) <= 2 ? 2 : 4;
         const int stage = 512 * (f16 ? jw / 2 : jw);
         const size_t ring1 = group_ring_bytes(1) + (size_t)2 * kWin * stage;
@@ -252,14 +245,14 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
             return SATPILA_OK;
         };
         const int win_per_cta = (int)std::min<size_t>(kSatMaxWarps, maxopt / gsm);
-        if (prm->residency == SAT_RESIDENT_GLOBAL || (prm->residency == SAT_RESIDENT_AUTO && win_per_cta == 0)) {
+        if (residency == SAT_RESIDENT_GLOBAL || (residency == SAT_RESIDENT_AUTO && win_per_cta == 0)) {
             pl->group_smem = (int)glob;
             const int warps = std::min(4, std::max(1, n_chains));
             return finish(1, false, warps, (size_t)warps * glob, false);
         }
         if (win_per_cta == 0) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: residual does not fit in shared memory");
         const int ns = std::min(win_per_cta, 3), ng = 4 - ns;
-        if ((prm->flags & SAT_FLAG_HYBRID) && ng > 0 && n_chains > sms * win_per_cta &&
+        if (want_hybrid && ng > 0 && n_chains > sms * win_per_cta &&
             (size_t)ns * gsm + (size_t)ng * glob <= (size_t)maxopt) {
             pl->group_smem = (int)gsm;
             pl->hybrid_smem_warps = ns;
@@ -267,12 +260,17 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
             // stage-sized tasks, so that chains move between the two kinds of warp
             return finish(2, true, ns + ng, (size_t)ns * gsm + (size_t)ng * glob, true);
         }
+        if (variant == PLAN_WINDOW_HYBRID)
+            return fail(SATPILA_ERR_INVALID_ARG, "sat_run: no hybrid launch for this size");
         pl->group_smem = (int)gsm;
         const int warps = std::min(win_per_cta, std::max(1, n_chains));
         return finish(1, true, warps, (size_t)warps * gsm, false);
     }
-    int W = prm->group_warps > 0 ? prm->group_warps : 1;
-    if (prm->group_warps <= 0)
+    int W = variant == PLAN_PIPE_1   ? 1
+            : variant == PLAN_PIPE_2 ? 2
+            : variant == PLAN_PIPE_4 ? 4
+                                     : (prm->group_warps > 0 ? prm->group_warps : 1);
+    if (variant == PLAN_RULES && prm->group_warps <= 0)
         while (W < kMaxGroupWarps && records_per_lane(W) > 2) W *= 2;
     if (W != 1 && W != 2 && W != 4) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: group_warps must be 1, 2 or 4");
     const int J = records_per_lane(W);
@@ -320,6 +318,389 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     return SATPILA_OK;
 }
 
+
+namespace {
+
+struct BatchLayout {
+    size_t resid, S, T0, TN, found, acc, prog, err, psq, pdr, dmax, c0, cF, Sinc, bytes;
+};
+
+BatchLayout batch_layout(const Plan& pl, long long cap) {
+    BatchLayout L{};
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + std::max<size_t>(bytes, 1), 256);
+        return o;
+    };
+    const size_t n = (size_t)cap, G = (size_t)pl.proj_G;
+    L.resid = carve(n * (size_t)pl.resid_floats * sizeof(float));
+    L.S = carve(n * 8);
+    L.T0 = carve(n * 8);
+    L.TN = carve(n * 8);
+    L.found = carve(n * 4);
+    L.acc = carve(n * 8);
+    L.prog = carve(n * 4);
+    L.err = carve(4);
+    L.psq = carve(n * G * 8);
+    L.pdr = carve(n * G * 4);
+    L.dmax = carve(n * 8);
+    L.c0 = carve(n * 8);
+    L.cF = carve(n * 8);
+    L.Sinc = carve(n * 8);
+    L.bytes = off;
+    return L;
+}
+
+}  // namespace
+
+size_t batch_bytes(const Plan& pl, long long cap) { return batch_layout(pl, cap).bytes; }
+
+void batch_carve(void* base, const Plan& pl, long long cap, BatchDev* b) {
+    const BatchLayout L = batch_layout(pl, cap);
+    char* c = (char*)base;
+    b->resid = (float*)(c + L.resid);
+    b->S = (double*)(c + L.S);
+    b->T0 = (double*)(c + L.T0);
+    b->TN = (double*)(c + L.TN);
+    b->found = (int*)(c + L.found);
+    b->accepted = (unsigned long long*)(c + L.acc);
+    b->progress = (int*)(c + L.prog);
+    b->error = (int*)(c + L.err);
+    b->part_sq = (double*)(c + L.psq);
+    b->part_drift = (float*)(c + L.pdr);
+    b->drift_max = (double*)(c + L.dmax);
+    b->cost0 = (double*)(c + L.c0);
+    b->costF = (double*)(c + L.cF);
+    b->S_inc = (double*)(c + L.Sinc);
+}
+
+cudaError_t prepare_launches(const satpila_pila* p, const Plan& pl, int bome_k) {
+    cudaError_t e = prepare_projector();
+    if (e != cudaSuccess) return e;
+    SweepFn k = sweep_kernel(p->precision == PILA_F16, pl.smem, pl.jmax, kmax_for(bome_k), pl.kind);
+    if (!k) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.sweep_smem_bytes());
+}
+
+cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev& b, int c0, int nc, bool drift,
+                           double* cost_out, cudaStream_t q) {
+    if (nc <= 0) return cudaSuccess;
+    const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
+    const int G = pl.proj_G;
+    ProjArgs pa{};
+    pa.table = p->d_table;
+    pa.f16 = p->precision == PILA_F16;
+    pa.row_records = p->row_records;
+    pa.n = p->n;
+    pa.U = p->U;
+    pa.B = p->B;
+    pa.angles_per_group = pl.proj_A;
+    pa.n_groups = G;
+    pa.mode = PROJ_RESYNC;
+    pa.drift = drift ? 1 : 0;
+    pa.img = b.img + (long long)c0 * P;
+    pa.img_stride = P;
+    pa.pm = b.sino + (long long)c0 * cells;
+    pa.pm_stride = cells;
+    pa.resid = b.resid + (long long)c0 * pl.resid_floats;
+    pa.resid_stride = pl.resid_floats;
+    pa.resid_pitch = pl.pitch;
+    pa.part_sq = b.part_sq + (long long)c0 * G;
+    pa.part_drift = b.part_drift + (long long)c0 * G;
+    cudaError_t e = launch_projector(pa, nc, q);
+    if (e != cudaSuccess) return e;
+    ReduceArgs ra{};
+    ra.n_items = nc;
+    ra.n_groups = G;
+    ra.part_sq = pa.part_sq;
+    ra.part_drift = pa.part_drift;
+    ra.inv_cells = 1.0 / (double)cells;
+    ra.S_out = b.S + c0;
+    ra.cost_out = cost_out ? cost_out + c0 : nullptr;
+    ra.cost_stride = 1;
+    ra.drift_max = drift ? b.drift_max + c0 : nullptr;
+    return launch_reduce(ra, q);
+}
+
+cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm, int c0,
+                       int nc, cudaStream_t q) {
+    if (nc <= 0) return cudaSuccess;
+    const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
+    T0Args ta{};
+    ta.table = p->d_table;
+    ta.row_stride = p->row_bytes;
+    ta.f16 = p->precision == PILA_F16;
+    ta.n = p->n;
+    ta.U = p->U;
+    ta.B = p->B;
+    ta.pitch = pl.pitch;
+    ta.list = p->d_list;
+    ta.n_list = p->n_mask;
+    ta.beta = prm->beta;
+    ta.inv_BU = (float)(1.0 / (double)cells);
+    ta.inv_BU_d = 1.0 / (double)cells;
+    ta.resid = b.resid + (long long)c0 * pl.resid_floats;
+    ta.resid_floats = pl.resid_floats;
+    ta.img = b.img + (long long)c0 * P;
+    ta.img_stride = P;
+    ta.S = b.S + c0;
+    ta.seed = prm->seed + (unsigned long long)c0;
+    ta.Q = prm->t0_samples > 0 ? prm->t0_samples : 200;
+    ta.tn = prm->tn;
+    ta.t0_fixed = prm->t0;
+    ta.T0 = b.T0 + c0;
+    ta.TN = b.TN + c0;
+    ta.found = b.found + c0;
+    ta.ctl = b.ctl ? b.ctl + c0 : nullptr;
+    if (ta.f16) t0_kernel<true><<<nc, 256, 0, q>>>(ta);
+    else t0_kernel<false><<<nc, 256, 0, q>>>(ta);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm,
+                          int n_chains, int M, int s_total, int s_begin, int s_end, int* task_counter,
+                          cudaStream_t q) {
+    if (n_chains <= 0 || s_end <= s_begin) return cudaSuccess;
+    const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
+    SatArgs sa{};
+    sa.table = p->d_table;
+    sa.row_stride = p->row_bytes;
+    sa.row_chunks = (int)(p->row_bytes / 16);
+    sa.hsum = p->d_hsum;
+    sa.n = p->n;
+    sa.U = p->U;
+    sa.B = p->B;
+    sa.pitch = pl.pitch;
+    sa.band_lo = pl.band_lo;
+    sa.band_pitch = pl.band_pitch;
+    sa.band_floats = pl.band_floats;
+    sa.list = p->d_list;
+    sa.n_list = p->n_mask;
+    sa.moves = M;
+    sa.K = prm->bome_k;
+    sa.beta = prm->beta;
+    sa.inv_BU = (float)(1.0 / (double)cells);
+    sa.inv_BU_d = 1.0 / (double)cells;
+    sa.D = pl.D;
+    sa.stage_bytes = pl.stage_bytes;
+    sa.W = pl.W;
+    sa.group_smem_bytes = pl.group_smem;
+    sa.hybrid_smem_warps = pl.hybrid_smem_warps;
+    sa.hybrid_glob_bytes = pl.hybrid_glob_bytes;
+    sa.resid_floats = pl.resid_floats;
+    sa.n_chains = n_chains;
+    sa.resid = b.resid;
+    sa.img = b.img;
+    sa.img_stride = P;
+    sa.S = b.S;
+    sa.T0 = b.T0;
+    sa.TN = b.TN;
+    sa.seed = prm->seed;
+    sa.accepted = b.accepted;
+    sa.progress = b.progress;
+    sa.schedule = prm->schedule;
+    sa.n_sweeps_total = s_total;
+    sa.error = b.error;
+    sa.sweep_cost = b.sweep_cost;
+    sa.trace = b.trace;
+    sa.trace_chain = b.trace_chain;
+    sa.trace_cap = b.trace_cap;
+    sa.ctl = b.ctl;
+    sa.sweep_begin = s_begin;
+    sa.sweep_end = s_end;
+    sa.sweeps_per_task = pl.spt;
+    sa.n_tasks = n_chains * ((s_end - s_begin + pl.spt - 1) / pl.spt);
+    sa.task_counter = task_counter;
+    return launch_sweep(p->precision == PILA_F16, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid,
+                        pl.warps, pl.sweep_smem_bytes(), q);
+}
+
+cudaError_t enqueue_copy_f64(double* dst, const double* src, int n, cudaStream_t q) {
+    if (n <= 0) return cudaSuccess;
+    copy_f64_kernel<<<(n + 127) / 128, 128, 0, q>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// ---- the whole of one sat_run call, enqueued on a stream --------------------
+
+struct RunShape {
+    int n_chains, M, S_total, window, n_windows;
+};
+
+// Sweep launches are bracketed by events (direct launches) or, inside a
+// graph, by global-timer stamps written to `stamps` (2 per window).
+cudaError_t enqueue_run(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm,
+                        const RunShape& r, void* ws_base, size_t ws_bytes, int* counters,
+                        const std::vector<cudaEvent_t>& evs, unsigned long long* stamps, cudaStream_t q) {
+    cudaError_t err = cudaMemsetAsync(ws_base, 0, ws_bytes, q);
+    if (err != cudaSuccess) return err;
+    // 1. initial resync, 2. temperatures
+    if ((err = enqueue_resync(p, pl, b, 0, r.n_chains, false, b.cost0, q)) != cudaSuccess) return err;
+    if ((err = enqueue_t0(p, pl, b, prm, 0, r.n_chains, q)) != cudaSuccess) return err;
+    // 3. windows of stages, each followed by a resync that records the drift
+    for (int w = 0; w < r.n_windows; ++w) {
+        const int s0 = w * r.window, s1 = std::min(r.S_total, s0 + r.window);
+        auto mark = [&](int i) -> cudaError_t {
+            if (!stamps) return cudaEventRecord(evs[i], q);
+            stamp_kernel<<<1, 1, 0, q>>>(stamps + i);
+            return cudaGetLastError();
+        };
+        if ((err = mark(2 * w)) != cudaSuccess) return err;
+        err = enqueue_sweep(p, pl, b, prm, r.n_chains, r.M, r.S_total, s0, s1, counters + w, q);
+        if (err != cudaSuccess) return err;
+        if ((err = mark(2 * w + 1)) != cudaSuccess) return err;
+        const bool last = w + 1 == r.n_windows;
+        if (last && (err = enqueue_copy_f64(b.S_inc, b.S, r.n_chains, q)) != cudaSuccess) return err;
+        if ((err = enqueue_resync(p, pl, b, 0, r.n_chains, true, last ? b.costF : nullptr, q)) != cudaSuccess)
+            return err;
+    }
+    if (r.n_windows == 0) {
+        if ((err = enqueue_copy_f64(b.S_inc, b.S, r.n_chains, q)) != cudaSuccess) return err;
+        err = cudaMemcpyAsync(b.costF, b.cost0, (size_t)r.n_chains * 8, cudaMemcpyDeviceToDevice, q);
+    }
+    return err;
+}
+
+// ---- graph cache: repeated identical calls replay one CUDA graph ------------
+
+struct CachedRun {
+    int device = 0;
+    const satpila_pila* p = nullptr;
+    int n_chains = 0;
+    const void* sino = nullptr;
+    void* images = nullptr;
+    sat_params prm{};
+    int variant = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    BatchDev b;
+    Plan pl;
+    RunShape shape{};
+    std::vector<cudaEvent_t> evs;
+    cudaGraphExec_t exec = nullptr;
+    bool in_use = false;
+    unsigned long long last_use = 0;
+};
+
+constexpr size_t kGraphCacheEntries = 4;
+std::mutex g_cache_mu;
+std::list<CachedRun*> g_cache;
+unsigned long long g_cache_clock = 0;
+
+void destroy_cached(CachedRun* c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    for (auto& ev : c->evs) cudaEventDestroy(ev);
+    if (c->ws) cudaFree(c->ws);
+    delete c;
+}
+
+// A private stream per device for recording graphs (the caller's stream may
+// be the legacy default stream, which cannot be captured).
+cudaStream_t capture_stream(int dev) {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
+// ---- autotuner: the fastest plan variant for a problem shape ---------------
+
+struct TuneKey {
+    int device, n, U, B, precision, n_mask, K, chains_log2, M;
+    bool operator==(const TuneKey& o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, int>> g_tuned;
+
+// Times one short sweep launch of each feasible variant on a scratch copy of
+// the caller's images (the caller's data are not touched) and returns the
+// variant with the highest moves/s.  Variants differ only in how the work is
+// laid out on the GPU (warps per chain, residency, tasks), not in the moves.
+int autotune(const satpila_pila* p, int n_chains, const float* sino, const float* images, const sat_params* prm,
+             int M, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int lg = 0;
+    while ((1 << (lg + 1)) <= n_chains) ++lg;
+    const int Mp = std::min(M, 2048);
+    const TuneKey key{dev, p->n, p->U, p->B, p->precision, p->n_mask, prm->bome_k, lg, Mp};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto& kv : g_tuned)
+            if (kv.first == key) return kv.second;
+    }
+    const long long P = (long long)p->n * p->n;
+    int best = PLAN_RULES;
+    double best_rate = -1.0;
+    float* img = nullptr;
+    if (cudaMalloc(&img, (size_t)n_chains * P * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return PLAN_RULES;
+    }
+    sat_params tp = *prm;
+    tp.trace = nullptr;
+    tp.sweep_cost = nullptr;
+    tp.t0 = prm->t0 > 0.0 ? prm->t0 : 1e-3;  // a fixed temperature: the probe only times moves
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int v = PLAN_WINDOW_SMEM; v < PLAN_COUNT; ++v) {
+        Plan pl;
+        const std::string saved = satpila_last_error();
+        if (choose_plan(p, n_chains, 1, &tp, v, &pl) != SATPILA_OK) {
+            set_error(saved);
+            continue;
+        }
+        if (prepare_launches(p, pl, tp.bome_k) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const size_t bytes = batch_bytes(pl, n_chains) + 256;
+        void* ws = nullptr;
+        if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        BatchDev b;
+        batch_carve(ws, pl, n_chains, &b);
+        int* counter = (int*)((char*)ws + bytes - 256);
+        b.img = img;
+        b.sino = sino;
+        cudaError_t e = cudaMemsetAsync(ws, 0, bytes, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(img, images, (size_t)n_chains * P * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = enqueue_resync(p, pl, b, 0, n_chains, false, nullptr, s);
+        if (e == cudaSuccess) e = enqueue_t0(p, pl, b, &tp, 0, n_chains, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = enqueue_sweep(p, pl, b, &tp, n_chains, Mp, 1, 0, 1, counter, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        int err_code = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err_code, b.error, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float ms = 0.0f;
+        if (e == cudaSuccess && err_code == 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f) {
+            const double rate = (double)n_chains * Mp / ms;
+            if (rate > best_rate) {
+                best_rate = rate;
+                best = v;
+            }
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        cudaFree(ws);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(img);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned.push_back({key, best});
+    return best;
+}
+
 // Device staging for a caller buffer that may live on the host.
 struct Staged {
     void* dev = nullptr;
@@ -338,7 +719,21 @@ int stage_in(const void* src, size_t bytes, bool copy, cudaStream_t s, Staged* o
     return SATPILA_OK;
 }
 
+
 }  // namespace
+
+void sat_cache_purge(const satpila_pila* p) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    for (auto it = g_cache.begin(); it != g_cache.end();) {
+        if ((*it)->p == p && !(*it)->in_use) {
+            destroy_cached(*it);
+            it = g_cache.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 }  // namespace satpila
 
 using namespace satpila;
@@ -360,217 +755,125 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
     cudaStream_t s = (cudaStream_t)stream;
     const long long P = (long long)p->n * p->n;
     const long long cells = (long long)p->U * p->B;
-    const int S_total = prm->n_sweeps;
-    const int M = prm->moves_per_sweep > 0 ? prm->moves_per_sweep : p->n_mask;
-    const int window = prm->resync_every > 0 ? std::min(prm->resync_every, std::max(1, S_total)) : std::max(1, S_total);
-    const int n_windows = S_total > 0 ? (S_total + window - 1) / window : 0;
-
-    Plan pl;
-    int rc = choose_plan(p, n_chains, window, prm, &pl);
-    if (rc != SATPILA_OK) return rc;
-    int A = 0, G = 0;
-    if (projector_plan(p->U, p->B, &A, &G) != SATPILA_OK)
-        return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many bins");
+    RunShape shape{};
+    shape.n_chains = n_chains;
+    shape.S_total = prm->n_sweeps;
+    shape.M = prm->moves_per_sweep > 0 ? prm->moves_per_sweep : p->n_mask;
+    shape.window = prm->resync_every > 0 ? std::min(prm->resync_every, std::max(1, shape.S_total))
+                                         : std::max(1, shape.S_total);
+    shape.n_windows = shape.S_total > 0 ? (shape.S_total + shape.window - 1) / shape.window : 0;
+    const int M = shape.M, S_total = shape.S_total, n_windows = shape.n_windows;
 
     // Caller buffers (host buffers are staged).
     Staged d_sino, d_img, d_trace, d_cost;
     const size_t trace_recs = prm->trace ? (size_t)S_total * M : 0;
+    auto free_staged = [&]() {
+        for (Staged* st : {&d_sino, &d_img, &d_trace, &d_cost})
+            if (st->owned) cudaFree(st->dev);
+    };
+    int rc;
     if ((rc = stage_in(sino_meas, (size_t)n_chains * cells * sizeof(float), true, s, &d_sino)) ||
         (rc = stage_in(images, (size_t)n_chains * P * sizeof(float), true, s, &d_img)) ||
         (rc = stage_in(prm->trace, trace_recs * sizeof(sat_trace_rec), false, s, &d_trace)) ||
         (rc = stage_in(prm->sweep_cost, (size_t)n_chains * S_total * sizeof(double), false, s, &d_cost))) {
-        for (Staged* st : {&d_sino, &d_img, &d_trace, &d_cost})
-            if (st->owned) cudaFree(st->dev);
+        free_staged();
         return rc;
     }
+    const bool staged = d_sino.owned || d_img.owned || d_trace.owned || d_cost.owned;
 
-    // Workspace.
-    Workspace ws;
-    const size_t nc = (size_t)n_chains;
-    size_t off = 0;
-    auto carve = [&](size_t bytes) {
-        const size_t o = off;
-        off = align_up(off + bytes, 256);
-        return o;
-    };
-    const size_t o_resid = carve(nc * pl.resid_floats * sizeof(float));
-    const size_t o_S = carve(nc * 8), o_T0 = carve(nc * 8), o_TN = carve(nc * 8), o_found = carve(nc * 4);
-    const size_t o_acc = carve(nc * 8), o_prog = carve(nc * 4), o_cnt = carve((size_t)(n_windows + 1) * 4);
-    const size_t o_err = carve(4), o_psq = carve(nc * G * 8), o_pdr = carve(nc * G * 4);
-    const size_t o_dmax = carve(nc * 8), o_c0 = carve(nc * 8), o_cF = carve(nc * 8), o_Sinc = carve(nc * 8);
-    ws.bytes = off;
-    cudaError_t e = cudaMalloc(&ws.base, ws.bytes);
-    if (e != cudaSuccess) {
-        for (Staged* st : {&d_sino, &d_img, &d_trace, &d_cost})
-            if (st->owned) cudaFree(st->dev);
-        return cuda_fail(e, "sat_run: workspace");
+    // Launch plan, chosen by rules or by the autotuner.
+    int variant = PLAN_RULES;
+    if ((prm->flags & SAT_FLAG_AUTOTUNE) && S_total > 0 && p->n_mask > 0)
+        variant = autotune(p, n_chains, (const float*)d_sino.dev, (const float*)d_img.dev, prm, M, s);
+    Plan pl;
+    if ((rc = choose_plan(p, n_chains, shape.window, prm, variant, &pl)) != SATPILA_OK) {
+        free_staged();
+        return rc;
     }
-    char* b = (char*)ws.base;
-    ws.resid = (float*)(b + o_resid);
-    ws.S = (double*)(b + o_S);
-    ws.T0 = (double*)(b + o_T0);
-    ws.TN = (double*)(b + o_TN);
-    ws.found = (int*)(b + o_found);
-    ws.accepted = (unsigned long long*)(b + o_acc);
-    ws.progress = (int*)(b + o_prog);
-    ws.counters = (int*)(b + o_cnt);
-    ws.error = (int*)(b + o_err);
-    ws.part_sq = (double*)(b + o_psq);
-    ws.part_drift = (float*)(b + o_pdr);
-    ws.drift_max = (double*)(b + o_dmax);
-    ws.cost0 = (double*)(b + o_c0);
-    ws.costF = (double*)(b + o_cF);
-    ws.S_inc = (double*)(b + o_Sinc);
+    cudaError_t e = prepare_launches(p, pl, prm->bome_k);
+    if (e != cudaSuccess) {
+        free_staged();
+        return cuda_fail(e, "sat_run: launch attributes");
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
 
-    std::vector<cudaEvent_t> evs(2 * (size_t)n_windows);
-    for (auto& ev : evs) cudaEventCreate(&ev);
-    const float* sino_d = (const float*)d_sino.dev;
-    float* img_d = (float*)d_img.dev;
-
-    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
-        cudaError_t err = cudaMemsetAsync(ws.base, 0, ws.bytes, q);
-        if (err != cudaSuccess) return err;
-        ProjArgs pa{};
-        pa.table = p->d_table;
-        pa.f16 = p->precision == PILA_F16;
-        pa.row_records = p->row_records;
-        pa.n = p->n;
-        pa.U = p->U;
-        pa.B = p->B;
-        pa.angles_per_group = A;
-        pa.n_groups = G;
-        pa.mode = PROJ_RESYNC;
-        pa.img = img_d;
-        pa.img_stride = P;
-        pa.pm = sino_d;
-        pa.pm_stride = cells;
-        pa.resid = ws.resid;
-        pa.resid_stride = pl.resid_floats;
-        pa.resid_pitch = pl.pitch;
-        pa.part_sq = ws.part_sq;
-        pa.part_drift = ws.part_drift;
-        ReduceArgs ra{};
-        ra.n_items = n_chains;
-        ra.n_groups = G;
-        ra.part_sq = ws.part_sq;
-        ra.part_drift = ws.part_drift;
-        ra.inv_cells = 1.0 / (double)cells;
-        ra.S_out = ws.S;
-        ra.cost_stride = 1;
-        // 1. initial resync
-        pa.drift = 0;
-        if ((err = launch_projector(pa, n_chains, q)) != cudaSuccess) return err;
-        ra.cost_out = ws.cost0;
-        ra.drift_max = nullptr;
-        if ((err = launch_reduce(ra, q)) != cudaSuccess) return err;
-        // 2. temperatures
-        T0Args ta{};
-        ta.table = p->d_table;
-        ta.row_stride = p->row_bytes;
-        ta.f16 = p->precision == PILA_F16;
-        ta.n = p->n;
-        ta.U = p->U;
-        ta.B = p->B;
-        ta.pitch = pl.pitch;
-        ta.list = p->d_list;
-        ta.n_list = p->n_mask;
-        ta.beta = prm->beta;
-        ta.inv_BU = (float)(1.0 / (double)cells);
-        ta.inv_BU_d = 1.0 / (double)cells;
-        ta.resid = ws.resid;
-        ta.resid_floats = pl.resid_floats;
-        ta.img = img_d;
-        ta.img_stride = P;
-        ta.S = ws.S;
-        ta.seed = prm->seed;
-        ta.Q = prm->t0_samples > 0 ? prm->t0_samples : 200;
-        ta.tn = prm->tn;
-        ta.t0_fixed = prm->t0;
-        ta.T0 = ws.T0;
-        ta.TN = ws.TN;
-        ta.found = ws.found;
-        if (ta.f16) t0_kernel<true><<<n_chains, 256, 0, q>>>(ta);
-        else t0_kernel<false><<<n_chains, 256, 0, q>>>(ta);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        // 3. windows of stages
-        SatArgs sa{};
-        sa.table = p->d_table;
-        sa.row_stride = p->row_bytes;
-        sa.row_chunks = (int)(p->row_bytes / 16);
-        sa.hsum = p->d_hsum;
-        sa.n = p->n;
-        sa.U = p->U;
-        sa.B = p->B;
-        sa.pitch = pl.pitch;
-        sa.band_lo = pl.band_lo;
-        sa.band_pitch = pl.band_pitch;
-        sa.band_floats = pl.band_floats;
-        sa.list = p->d_list;
-        sa.n_list = p->n_mask;
-        sa.moves = M;
-        sa.K = prm->bome_k;
-        sa.beta = prm->beta;
-        sa.inv_BU = (float)(1.0 / (double)cells);
-        sa.inv_BU_d = 1.0 / (double)cells;
-        sa.D = pl.D;
-        sa.stage_bytes = pl.stage_bytes;
-        sa.W = pl.W;
-        sa.group_smem_bytes = pl.group_smem;
-        sa.hybrid_smem_warps = pl.hybrid_smem_warps;
-        sa.hybrid_glob_bytes = pl.hybrid_glob_bytes;
-        sa.resid_floats = pl.resid_floats;
-        sa.n_chains = n_chains;
-        sa.resid = ws.resid;
-        sa.img = img_d;
-        sa.img_stride = P;
-        sa.S = ws.S;
-        sa.T0 = ws.T0;
-        sa.TN = ws.TN;
-        sa.seed = prm->seed;
-        sa.accepted = ws.accepted;
-        sa.progress = ws.progress;
-        sa.schedule = prm->schedule;
-        sa.n_sweeps_total = S_total;
-        sa.error = ws.error;
-        sa.sweep_cost = (double*)d_cost.dev;
-        sa.trace = (sat_trace_rec*)d_trace.dev;
-        sa.trace_chain = prm->trace_chain;
-        sa.trace_cap = (long long)trace_recs;
-        for (int wdx = 0; wdx < n_windows; ++wdx) {
-            sa.sweep_begin = wdx * window;
-            sa.sweep_end = std::min(S_total, sa.sweep_begin + window);
-            sa.sweeps_per_task = pl.spt;
-            sa.n_tasks = n_chains * ((sa.sweep_end - sa.sweep_begin + pl.spt - 1) / pl.spt);
-            sa.task_counter = ws.counters + wdx;
-            const size_t smem_bytes = pl.kind == 2 ? (size_t)pl.hybrid_smem_warps * pl.group_smem +
-                                                         (size_t)(pl.warps - pl.hybrid_smem_warps) * pl.hybrid_glob_bytes
-                                                   : (size_t)pl.groups * pl.group_smem;
-            cudaEventRecord(evs[2 * wdx], q);
-            err = launch_sweep(pa.f16, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid, pl.warps,
-                               smem_bytes, q);
-            if (err != cudaSuccess) return err;
-            cudaEventRecord(evs[2 * wdx + 1], q);
-            const bool last = wdx + 1 == n_windows;
-            if (last) {
-                copy_f64_kernel<<<(n_chains + 127) / 128, 128, 0, q>>>(ws.S_inc, ws.S, n_chains);
-                if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // A cached graph for this exact call (device buffers only), else a new
+    // workspace; with SAT_FLAG_NO_GRAPH the launches are issued one by one.
+    const bool use_graph = !(prm->flags & SAT_FLAG_NO_GRAPH) && !staged;
+    CachedRun* run = nullptr;
+    bool cached = false;
+    if (use_graph) {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        for (CachedRun* c : g_cache)
+            if (!c->in_use && c->device == dev && c->p == p && c->n_chains == n_chains && c->sino == d_sino.dev &&
+                c->images == d_img.dev && c->variant == variant &&
+                std::memcmp(&c->prm, prm, sizeof(sat_params)) == 0) {
+                run = c;
+                run->in_use = true;
+                run->last_use = ++g_cache_clock;
+                cached = true;
+                break;
             }
-            pa.drift = 1;
-            if ((err = launch_projector(pa, n_chains, q)) != cudaSuccess) return err;
-            ra.cost_out = last ? ws.costF : nullptr;
-            ra.drift_max = ws.drift_max;
-            if ((err = launch_reduce(ra, q)) != cudaSuccess) return err;
+    }
+    if (!run) {
+        run = new CachedRun();
+        run->device = dev;
+        run->p = p;
+        run->n_chains = n_chains;
+        run->sino = d_sino.dev;
+        run->images = d_img.dev;
+        run->prm = *prm;
+        run->variant = variant;
+        run->pl = pl;
+        run->shape = shape;
+        run->ws_bytes = batch_bytes(pl, n_chains) + align_up((size_t)(n_windows + 1) * 4, 256) +
+                        align_up((size_t)(2 * n_windows + 1) * 8, 256);
+        e = cudaMalloc(&run->ws, run->ws_bytes);
+        if (e != cudaSuccess) {
+            delete run;
+            free_staged();
+            return cuda_fail(e, "sat_run: workspace");
         }
-        if (n_windows == 0) {
-            copy_f64_kernel<<<(n_chains + 127) / 128, 128, 0, q>>>(ws.S_inc, ws.S, n_chains);
-            if ((err = cudaGetLastError()) != cudaSuccess) return err;
-            err = cudaMemcpyAsync(ws.costF, ws.cost0, nc * 8, cudaMemcpyDeviceToDevice, q);
-        }
-        return err;
-    };
+        batch_carve(run->ws, pl, n_chains, &run->b);
+        run->b.img = (float*)d_img.dev;
+        run->b.sino = (const float*)d_sino.dev;
+        run->b.sweep_cost = (double*)d_cost.dev;
+        run->b.trace = (sat_trace_rec*)d_trace.dev;
+        run->b.trace_cap = (long long)trace_recs;
+        run->b.trace_chain = prm->trace_chain;
+        run->evs.resize(2 * (size_t)n_windows);
+        for (auto& ev : run->evs) cudaEventCreate(&ev);
+        run->in_use = true;
+    }
+    int* counters = (int*)((char*)run->ws + batch_bytes(pl, n_chains));
+    unsigned long long* stamps =
+        (unsigned long long*)((char*)counters + align_up((size_t)(n_windows + 1) * 4, 256));
 
-    e = enqueue(s);
+    if (use_graph && !run->exec) {
+        // Record every launch of the call once into a graph.
+        cudaStream_t cs = capture_stream(dev);
+        cudaGraph_t graph = nullptr;
+        e = cs ? cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) : cudaErrorInvalidResourceHandle;
+        if (e == cudaSuccess) {
+            const cudaError_t e1 =
+                enqueue_run(p, pl, run->b, prm, shape, run->ws, run->ws_bytes, counters, run->evs, stamps, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&run->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            run->exec = nullptr;  // fall back to direct launches
+        }
+    }
+    if (run->exec) e = cudaGraphLaunch(run->exec, s);
+    else e = enqueue_run(p, pl, run->b, prm, shape, run->ws, run->ws_bytes, counters, run->evs, nullptr, s);
+
     // Results.
+    const BatchDev& b = run->b;
+    const size_t nc = (size_t)n_chains;
     std::vector<double> T0(nc), TN(nc), c0(nc), cF(nc), Sinc(nc), dmax(nc);
     std::vector<int> found(nc);
     std::vector<unsigned long long> acc(nc);
@@ -580,13 +883,16 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             void* dst;
             const void* src;
             size_t bytes;
-        } cps[] = {{T0.data(), ws.T0, nc * 8},       {TN.data(), ws.TN, nc * 8},     {c0.data(), ws.cost0, nc * 8},
-                   {cF.data(), ws.costF, nc * 8},    {Sinc.data(), ws.S_inc, nc * 8}, {dmax.data(), ws.drift_max, nc * 8},
-                   {found.data(), ws.found, nc * 4}, {acc.data(), ws.accepted, nc * 8}};
+        } cps[] = {{T0.data(), b.T0, nc * 8},       {TN.data(), b.TN, nc * 8},       {c0.data(), b.cost0, nc * 8},
+                   {cF.data(), b.costF, nc * 8},    {Sinc.data(), b.S_inc, nc * 8},  {dmax.data(), b.drift_max, nc * 8},
+                   {found.data(), b.found, nc * 4}, {acc.data(), b.accepted, nc * 8}};
         for (auto& c : cps)
             if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, s);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_code, ws.error, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_code, b.error, 4, cudaMemcpyDeviceToHost, s);
+    std::vector<unsigned long long> ts(2 * (size_t)n_windows);
+    if (e == cudaSuccess && run->exec && n_windows > 0)
+        e = cudaMemcpyAsync(ts.data(), stamps, ts.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && d_img.owned)
         e = cudaMemcpyAsync(images, d_img.dev, nc * P * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && d_trace.owned)
@@ -595,14 +901,34 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
         e = cudaMemcpyAsync(prm->sweep_cost, d_cost.dev, nc * S_total * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     double sweep_ms = 0.0;
-    for (int wdx = 0; e == cudaSuccess && wdx < n_windows; ++wdx) {
+    for (int w = 0; e == cudaSuccess && w < n_windows; ++w) {
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, evs[2 * wdx], evs[2 * wdx + 1]) == cudaSuccess) sweep_ms += ms;
+        if (run->exec) sweep_ms += 1e-6 * (double)(ts[2 * w + 1] - ts[2 * w]);
+        else if (cudaEventElapsedTime(&ms, run->evs[2 * w], run->evs[2 * w + 1]) == cudaSuccess) sweep_ms += ms;
+        else cudaGetLastError();
     }
-    for (auto& ev : evs) cudaEventDestroy(ev);
-    cudaFree(ws.base);
-    for (Staged* st : {&d_sino, &d_img, &d_trace, &d_cost})
-        if (st->owned) cudaFree(st->dev);
+    // Keep the graph and its workspace for a repeat of this call.
+    if (use_graph && run->exec && e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        run->in_use = false;
+        run->last_use = ++g_cache_clock;
+        if (!cached) g_cache.push_back(run);
+        while (g_cache.size() > kGraphCacheEntries) {
+            auto victim = g_cache.end();
+            for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
+                if (!(*it)->in_use && (victim == g_cache.end() || (*it)->last_use < (*victim)->last_use)) victim = it;
+            if (victim == g_cache.end()) break;
+            destroy_cached(*victim);
+            g_cache.erase(victim);
+        }
+    } else {
+        if (cached) {
+            std::lock_guard<std::mutex> lock(g_cache_mu);
+            g_cache.remove(run);
+        }
+        destroy_cached(run);
+    }
+    free_staged();
     if (e != cudaSuccess) return cuda_fail(e, "sat_run");
     if (stats) {
         const double inv_cells = 1.0 / (double)cells;
@@ -620,6 +946,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             st.t0_found = found[c];
             st.status = err_code;
             st.sweep_ms = sweep_ms;
+            st.plan = variant;
         }
     }
     if (err_code != 0) return fail(err_code, "sat_run: a device-side check failed");

@@ -32,6 +32,18 @@
 
 namespace satpila {
 
+// Per-chain control of a batch whose chains are at different points of their
+// own schedules (the serving engine); sat_run passes none and uses the
+// batch-wide values.
+struct ChainCtl {
+    unsigned long long seed;  // Philox key of the chain
+    double t0, tn;            // as in sat_params (t0 <= 0: Eq. (8); tn < 0: T0 / 1000)
+    int stage0;               // stages the chain ran before this launch
+    int n_sweeps;             // length of the chain's schedule
+    int schedule;             // SAT_SCHED_*
+    int t0_samples;           // Q of Eq. (8)
+};
+
 struct SatArgs {
     const unsigned char* table;  // PILA records [P][row_records]
     long long row_stride;        // bytes between pixel rows
@@ -74,6 +86,7 @@ struct SatArgs {
     sat_trace_rec* trace;
     int trace_chain;
     long long trace_cap;
+    const ChainCtl* ctl;         // [n_chains] or NULL
 };
 
 constexpr int kSatMaxWarps = 8;
@@ -640,12 +653,15 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
         x.gl = gl;
         x.R = R;
         x.img = a.img + (long long)c * a.img_stride;
-        x.key = chain_key(a.seed + (unsigned long long)c);
+        const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
+        const int s_base = cc ? cc->stage0 : 0, s_total = cc ? cc->n_sweeps : a.n_sweeps_total;
+        const int sched = cc ? cc->schedule : a.schedule;
+        x.key = chain_key(cc ? cc->seed : a.seed + (unsigned long long)c);
         x.tracing = a.trace != nullptr && c == a.trace_chain;
         const double T0 = a.T0[c], TN = a.TN[c];
-        for (int s = s0; s < s1; ++s) {
-            x.s = s;
-            x.T = (float)stage_temperature(a.schedule, T0, TN, s, a.n_sweeps_total);
+        for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
+            x.s = s_base + s;
+            x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
             run_stage<F16, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
             if (a.sweep_cost && gl == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
@@ -700,6 +716,7 @@ struct T0Args {
     double* T0;
     double* TN;
     int* found;
+    const ChainCtl* ctl;  // [chains] or NULL
 };
 
 }  // namespace satpila

@@ -374,12 +374,15 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         x.gl = lane;
         x.R = SMEM ? rs : gres;
         x.img = a.img + (long long)c * a.img_stride;
-        x.key = chain_key(a.seed + (unsigned long long)c);
+        const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
+        const int s_base = cc ? cc->stage0 : 0, s_total = cc ? cc->n_sweeps : a.n_sweeps_total;
+        const int sched = cc ? cc->schedule : a.schedule;
+        x.key = chain_key(cc ? cc->seed : a.seed + (unsigned long long)c);
         x.tracing = a.trace != nullptr && c == a.trace_chain;
         const double T0 = a.T0[c], TN = a.TN[c];
-        for (int s = s0; s < s1; ++s) {
-            x.s = s;
-            x.T = (float)stage_temperature(a.schedule, T0, TN, s, a.n_sweeps_total);
+        for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
+            x.s = s_base + s;
+            x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
             run_stage_window<F16, SMEM, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
             if (a.sweep_cost && lane == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);

@@ -66,4 +66,4 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.PilaInfo) == 48
     assert C.sizeof(_lib.SatParams) == 88
     assert C.sizeof(_lib.PilaGeom) == 32
-    assert C.sizeof(_lib.SatStats) == 80
+    assert C.sizeof(_lib.SatStats) == 88
