@@ -221,6 +221,83 @@ int sat_run(const satpila_pila* p, int32_t n_chains, const float* sino_meas, flo
             const sat_params* prm, sat_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of annealing requests (no counterpart in the  */
+/* paper, which reconstructs one slice at a time; each request runs Steps 1-4 */
+/* of Sec. II-A exactly as sat_run does for one chain).                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct satpila_server satpila_server;
+
+typedef struct {
+    int32_t device;          /* CUDA device the server runs on */
+    int32_t max_active;      /* chains on the device at once; 0: 4096 */
+    int32_t stages_per_tick; /* stages every active chain advances per batched launch; each tick ends
+                                with the FP64-grade resync, so a request behaves as sat_run with
+                                resync_every = stages_per_tick; 0: 5 */
+    int32_t queue_limit;     /* waiting requests beyond which submit returns SATPILA_ERR_BUSY; 0: 65536 */
+    uint64_t mem_budget;     /* device bytes for tables and chain state; 0: 120 GiB; capped at the
+                                device's free memory less 2 GiB */
+} sat_server_cfg;
+
+typedef struct {
+    int32_t n, n_angles, n_bins; /* geometry, as pila_geom */
+    int32_t precision;           /* PILA_F32 or PILA_F16 */
+    const double* angles_rad;    /* [n_angles] or NULL (u * pi / U) */
+    const uint8_t* mask;         /* [n][n] reconstruction space or NULL (all pixels) */
+    const float* sino;           /* [n_angles][n_bins] measured sinogram P_m */
+    const float* image;          /* [n][n] start image, or NULL: 0.5 on the reconstruction space, 0 elsewhere */
+    sat_params prm;              /* as for sat_run; prm.seed is this chain's Philox key; trace,
+                                    sweep_cost, resync_every and flags are not used */
+} sat_request;
+
+typedef struct {
+    sat_stats stats;             /* as sat_run's (sweep_ms: the chain's last tick) */
+    double submit_ms, admit_ms, done_ms; /* server clock, ms since sat_server_create */
+} sat_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int32_t active, queued, geometries, classes;
+    uint64_t bytes_in_use, bytes_peak, mem_budget;
+    int64_t ticks, moves;
+} sat_server_stats;
+
+/*
+ * Start a server: one engine thread that owns the device work.  Requests
+ * sharing geometry, bome_k, beta and moves per stage anneal together in one
+ * persistent sweep launch per tick (each chain at its own stage of its own
+ * schedule); different such classes run on their own streams.  Between ticks
+ * finished chains are copied out and waiting requests are admitted, in
+ * arrival order, while chain slots and the memory budget allow (PILA tables
+ * are cached per geometry and unused ones dropped when memory is needed).
+ * A chain's result is the same alone and in any mix.
+ * Errors: INVALID_ARG (no such device), OOM.
+ */
+int sat_server_create(const sat_server_cfg* cfg, satpila_server** out);
+
+/* Queue one request; its buffers (host or device) are copied before return.
+ * Errors: BUSY (queue full), INVALID_ARG (bad request, or one that can never
+ * fit the budget), or the error that stopped the server. */
+int sat_server_submit(satpila_server* s, const sat_request* r, uint64_t* ticket);
+
+/* Collect a finished request: image_out ([n][n], host or device, may be NULL)
+ * and res (may be NULL).  PENDING while it is queued or running; NOT_FOUND for
+ * an unknown or already collected ticket; a device-side error code if the
+ * request failed. */
+int sat_server_poll(satpila_server* s, uint64_t ticket, float* image_out, sat_result* res);
+
+/* As sat_server_poll, waiting up to timeout_ms (< 0: no limit); PENDING on
+ * timeout. */
+int sat_server_wait(satpila_server* s, uint64_t ticket, int32_t timeout_ms, float* image_out, sat_result* res);
+
+/* Counters of the server. */
+int sat_server_info(satpila_server* s, sat_server_stats* out);
+
+/* Stop after the current tick, free every device buffer and table; results
+ * not collected are lost. */
+int sat_server_destroy(satpila_server* s);
+
+/* ------------------------------------------------------------------------ */
 /* SIRT with PILA: Eqs. (10)-(11), Sec. III-D.                                */
 /* ------------------------------------------------------------------------ */
 

@@ -25,7 +25,8 @@ SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["satpila_last_error", "satpila_version", "pila_build", "pila_free", "pila_info", "pila_export",
-           "pila_forward", "pila_sirt_factor", "sat_run", "sirt_run", "sirt_run_noalloc"]
+           "pila_forward", "pila_sirt_factor", "sat_run", "sat_server_create", "sat_server_submit", "sat_server_poll",
+           "sat_server_wait", "sat_server_info", "sat_server_destroy", "sirt_run", "sirt_run_noalloc"]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -62,6 +63,28 @@ class SatStats(C.Structure):
                 ("plan", C.c_int32), ("pad", C.c_int32)]
 
 
+class SatServerCfg(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_active", C.c_int32), ("stages_per_tick", C.c_int32),
+                ("queue_limit", C.c_int32), ("mem_budget", C.c_uint64)]
+
+
+class SatRequest(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_angles", C.c_int32), ("n_bins", C.c_int32), ("precision", C.c_int32),
+                ("angles_rad", C.c_void_p), ("mask", C.c_void_p), ("sino", C.c_void_p), ("image", C.c_void_p),
+                ("prm", SatParams)]
+
+
+class SatResult(C.Structure):
+    _fields_ = [("stats", SatStats), ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double)]
+
+
+class SatServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("active", C.c_int32), ("queued", C.c_int32), ("geometries", C.c_int32), ("classes", C.c_int32),
+                ("bytes_in_use", C.c_uint64), ("bytes_peak", C.c_uint64), ("mem_budget", C.c_uint64),
+                ("ticks", C.c_int64), ("moves", C.c_int64)]
+
+
 class SirtParams(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("mode", C.c_int32), ("relax", C.c_float), ("pad", C.c_int32)]
 
@@ -90,6 +113,12 @@ def load():
         lib.pila_forward.argtypes = [V, C.c_int32, V, V, V]
         lib.pila_sirt_factor.argtypes = [V, V, V]
         lib.sat_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SatParams), V, V]
+        lib.sat_server_create.argtypes = [C.POINTER(SatServerCfg), C.POINTER(V)]
+        lib.sat_server_submit.argtypes = [V, C.POINTER(SatRequest), C.POINTER(C.c_uint64)]
+        lib.sat_server_poll.argtypes = [V, C.c_uint64, V, C.POINTER(SatResult)]
+        lib.sat_server_wait.argtypes = [V, C.c_uint64, C.c_int32, V, C.POINTER(SatResult)]
+        lib.sat_server_info.argtypes = [V, C.POINTER(SatServerStats)]
+        lib.sat_server_destroy.argtypes = [V]
         lib.sirt_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
         lib.sirt_run_noalloc.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
         for name in EXPORTS:

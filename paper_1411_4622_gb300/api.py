@@ -16,6 +16,7 @@ from ._lib import (PILA_F16, PILA_F32, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID, SAT_F
                    SAT_RESIDENT_AUTO,
                    SAT_RESIDENT_GLOBAL, SAT_RESIDENT_SMEM, SAT_SCHED_CUBIC, SAT_SCHED_GEOMETRIC,
                    SAT_SCHED_LINEAR, SIRT_SEQUENTIAL, SIRT_SIMULTANEOUS, SatpilaError)
+from ._lib import ERR_BUSY, ERR_INVALID_ARG, ERR_NOT_FOUND, ERR_PENDING  # noqa: F401
 
 TRACE_DTYPE = np.dtype([("pixel", "<i4"), ("cstar", "<i4"), ("accepted", "<i4"), ("pad", "<i4"),
                         ("dS", "<f4"), ("dC", "<f4"), ("fnew", "<f4"), ("pad2", "<f4")])
@@ -158,6 +159,87 @@ def sat_run(p: Pila, sino_meas, images, stream=None, **kw) -> list[dict]:
     L.check(L.load().sat_run(p.handle, n_chains, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
                              C.byref(prm), C.cast(stats, C.c_void_p), _stream(stream)))
     return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
+
+
+class Server:
+    """Continuous-batching annealing server (sat_server_* of include/satpila.h).
+
+    submit() copies the request's arrays and returns a ticket; poll()/wait()
+    return (image [n, n] float32, result dict) once the request is done."""
+
+    def __init__(self, device=0, max_active=0, stages_per_tick=0, queue_limit=0, mem_budget=0):
+        cfg = L.SatServerCfg(int(device), int(max_active), int(stages_per_tick), int(queue_limit), int(mem_budget))
+        h = C.c_void_p()
+        L.check(L.load().sat_server_create(C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self.sizes = {}
+
+    def submit(self, sino, *, n, precision=PILA_F32, mask=None, image=None, angles=None, **kw) -> int:
+        sino = np.ascontiguousarray(sino, dtype=np.float32)
+        U, B = sino.shape
+        keep = []
+
+        def arr(x, dtype):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=dtype)
+            keep.append(a)
+            return a.ctypes.data_as(C.c_void_p)
+
+        req = L.SatRequest(int(n), int(U), int(B), int(precision), arr(angles, np.float64), arr(mask, np.uint8),
+                           arr(sino, np.float32), arr(image, np.float32), sat_params(**kw))
+        t = C.c_uint64()
+        L.check(L.load().sat_server_submit(self.handle, C.byref(req), C.byref(t)))
+        self.sizes[t.value] = int(n)
+        return t.value
+
+    def _collect(self, ticket, rc, img, res):
+        if rc == L.ERR_PENDING:
+            return None
+        L.check(rc)
+        self.sizes.pop(ticket, None)
+        st = {f: getattr(res.stats, f) for f, _ in L.SatStats._fields_}
+        st.update(submit_ms=res.submit_ms, admit_ms=res.admit_ms, done_ms=res.done_ms)
+        return img, st
+
+    def poll(self, ticket):
+        """(image, result) if done, else None."""
+        n = self.sizes.get(ticket, 1)
+        img = np.zeros((n, n), dtype=np.float32)
+        res = L.SatResult()
+        rc = L.load().sat_server_poll(self.handle, C.c_uint64(ticket), img.ctypes.data_as(C.c_void_p), C.byref(res))
+        return self._collect(ticket, rc, img, res)
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(image, result) once done; None if timeout_ms passes first."""
+        n = self.sizes.get(ticket, 1)
+        img = np.zeros((n, n), dtype=np.float32)
+        res = L.SatResult()
+        rc = L.load().sat_server_wait(self.handle, C.c_uint64(ticket), int(timeout_ms),
+                                      img.ctypes.data_as(C.c_void_p), C.byref(res))
+        return self._collect(ticket, rc, img, res)
+
+    def info(self) -> dict:
+        st = L.SatServerStats()
+        L.check(L.load().sat_server_info(self.handle, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in L.SatServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            L.load().sat_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sirt_run(p: Pila, sino_meas, images, *, n_iter=1, mode=SIRT_SIMULTANEOUS, relax=1.0, costs=None,
