@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     ap.add_argument("--flags", type=int, default=0, help="SAT_FLAG_* bits for the batched run")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve"],
+                    help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     return ap.parse_args()
 
 
@@ -122,30 +125,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
-    """Hash of the CUDA sources; a stored DRAM-traffic figure only applies to them."""
+KERNEL_SOURCES = {
+    "sat_window_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window.cu"],
+    "sat_sweep_kernel": ["common.cuh", "sat_sweep.cuh", "sat_f16_glob.cu", "sat_f16_smem.cu", "sat_f32_glob.cu",
+                         "sat_f32_smem.cu"],
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the device sources of `kernel`; a stored DRAM-traffic figure
+    only applies to them."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1411_4622_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel):
+def stored_traffic(kernel, workload=WORKLOAD):
     """DRAM bytes per move of `kernel` from the committed ncu summary, or None
     when the summary is missing or was taken on different sources."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}__{WORKLOAD}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
     try:
         kv = {}
         for ln in open(path):
             if ":" in ln and ln.startswith("- "):
                 k, v = ln[2:].split(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
-        if kv.get("source_sha") != kernel_source_hash():
+        if kv.get("source_sha") != kernel_source_hash(kernel):
             return None
         return float(kv["dram_bytes_per_move"])
     except (OSError, KeyError, ValueError):
@@ -268,8 +278,205 @@ def run_reference(args, cfg):
     print(json.dumps(out))
 
 
+def timed_steps(args, step, stream, dist, local):
+    """W warm-up steps, then K timed steps (L2 flushed between them, outside
+    the events); returns (per-step ms, per-step stats, clocks)."""
+    import torch
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, stats = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return step_ms, stats, clocks.stop()
+
+
+def run_precision(args):
+    """The 512^2 configuration as a gather-throughput workload: C chains of
+    512x512 slices (8 distinct phantoms with 40 ellipses, Poisson noise at
+    1e5 photons, each chain its own seed), 360 angles, 725 bins, FP16 PILA,
+    K = 8, the whole 200-stage linear schedule from Eq. (8) with 1/100 of a
+    sweep per stage (the moves of every temperature, 2,058 per stage);
+    residual in global memory.  One step: PILA build, resync, Eq. (8), the
+    200 stages, final resync."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    cfg = dict(synth.WORKLOADS["precision512"])
+    n, U, B, K, S = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"]
+    C = args.slices or 304
+    mask = synth.disk_mask(n)
+    M = int(mask.sum()) // 100
+    distinct = min(8, C)
+    ph = np.stack([synth.phantom(n, cfg["ellipses"], synth.slice_seeds(i)[0]) * mask for i in range(distinct)])
+    pf = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    clean = api.pila_forward(pf, torch.tensor(ph, dtype=torch.float32, device="cuda")).cpu().numpy()
+    api.pila_free(pf)
+    noisy = np.stack([synth.poisson_noise(clean[i], cfg["noise"][1], synth.slice_seeds(i)[1])
+                      for i in range(distinct)]).astype(np.float32)
+    idx = np.arange(C) % distinct
+    sino = torch.tensor(noisy[idx], device="cuda").contiguous()
+    init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * C), dtype=torch.float32, device="cuda")
+    images = init.clone()
+    stream = torch.cuda.current_stream()
+    run_kw = dict(bome_k=K, n_sweeps=S, moves_per_sweep=M, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2],
+                  residency=args.residency, group_warps=args.group_warps, flags=args.flags)
+    info = {}
+
+    def step():
+        images.copy_(init)
+        p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+        st = api.sat_run(p, sino, images, **run_kw)
+        if not info:
+            info.update(api.pila_info(p))
+        api.pila_free(p)
+        return st
+
+    step_ms, stats, clk = timed_steps(args, step, stream, None, 0)
+    ms = statistics.mean(step_ms)
+    moves = C * S * M
+    st = stats[-1]
+    acc = sum(x["accepted"] for x in st) / max(1, sum(x["proposed"] for x in st))
+    sweep_ms = statistics.mean(x[0]["sweep_ms"] for x in stats)
+    peak, peak_kind = peaks()
+    E = info["entries"] / (n * n)
+    row_bytes = info["row_records"] * info["record_bytes"]
+    # one 32-byte sector per angle, two when a record's entries straddle a
+    # sector boundary (k0 = 7 mod 8: 1/8 of the records with two entries)
+    sectors = U * (1.0 + (E / U - 1.0) / 8.0)
+    sector_bytes = row_bytes + 32.0 * sectors * (1.0 + acc) + 8.0 * (1.0 + acc)
+    useful_bytes = row_bytes + 4.0 * E * (1.0 + acc) + 4.0 * (1.0 + acc)
+    rate = moves / (sweep_ms / 1e3)
+    achieved = sector_bytes * rate / 1e9
+    tpm = stored_traffic("sat_sweep_kernel", "precision512")
+    out = {"metric": "SAT pixel-moves/s, 512x512 slices (gather throughput)", "value": moves / (ms / 1e3),
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "precision512", "chains": C, "distinct_slices": distinct, "n": n, "angles": U,
+                      "bins": B, "bome_k": K, "stages": S, "moves_per_stage": M, "pila": "f16",
+                      "l2": "flushed between timed steps (256 MB write)"},
+           "acceptance": acc, "sweep_moves_per_s": rate,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": tpm * moves if tpm is not None else None,
+                        "traffic_frac": tpm * rate / 1e9 / peak if tpm is not None else None,
+                        "peak_kind": peak_kind, "kernel": "sat_sweep_kernel", "bytes_per_move": sector_bytes,
+                        "bytes_per_move_useful": useful_bytes, "frac_useful": useful_bytes * rate / 1e9 / peak,
+                        "accounting": "PILA row + one 32-byte sector per touched residual cell group, read and "
+                                      "(times acceptance) written", "sweep_ms": sweep_ms},
+           "clocks": clk, "gpu_launches": args.steps * (1 + 1 + 1 + 2 + 2 + 1 + 3 + 1)}
+    print(json.dumps(out))
+
+
+def run_serve(args):
+    """The serving workload: a Poisson stream of requests, sizes uniform over
+    {64, 128, 256, 512}^2, angles uniform in [N/2, N], 2 floor(N/sqrt 2) + 1
+    bins, Gaussian (1% of max) or Poisson (1e5) noise with probability 1/2,
+    K uniform over {1, 4, 8}, 50 stages each, FP16 PILA, disk reconstruction
+    space, under a 120 GB device budget.  The arrival rate is 80% of the
+    capacity measured on a closed burst of up to 400 requests of the mix.  Reported: moves/s
+    over the stream and per-request latency (submit to result) p50/p99."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(7)
+    nreq = args.requests
+    sizes = rng.choice([64, 128, 256, 512], size=nreq)
+    angles = np.array([rng.integers(s // 2, s + 1) for s in sizes])
+    noise = rng.integers(0, 2, size=nreq)
+    ks = rng.choice([1, 4, 8], size=nreq)
+    pool = 8  # distinct phantoms per size
+    phid = rng.integers(0, pool, size=nreq)
+    masks = {s: synth.disk_mask(s) for s in (64, 128, 256, 512)}
+    phantoms = {s: np.stack([synth.phantom(s, 20, 5000 + 100 * i + s) * masks[s] for i in range(pool)])
+                for s in (64, 128, 256, 512)}
+    # sinograms: one FP32 table per (size, angles), all phantoms of that size
+    sinos = {}
+    for s, u in sorted(set(zip(sizes.tolist(), angles.tolist()))):
+        pf = api.pila_build(s, u, synth.bins_for(s), api.PILA_F32, mask=masks[s])
+        sinos[(s, u)] = api.pila_forward(pf, torch.tensor(phantoms[s], dtype=torch.float32,
+                                                          device="cuda")).cpu().numpy()
+        api.pila_free(pf)
+    reqs = []
+    for i in range(nreq):
+        s, u = int(sizes[i]), int(angles[i])
+        clean = sinos[(s, u)][phid[i]]
+        sn = (synth.gaussian_noise(clean, 0.01, 9000 + i) if noise[i] == 0
+              else synth.poisson_noise(clean, 1e5, 9000 + i)).astype(np.float32)
+        reqs.append(dict(sino=sn, n=s, precision=api.PILA_F16, mask=masks[s], bome_k=int(ks[i]), n_sweeps=50,
+                         seed=20000 + i, t0=-1.0, tn=-1.0))
+    moves_of = [50 * int(masks[r["n"]].sum()) for r in reqs]
+    with api.Server(stages_per_tick=5, mem_budget=120 << 30) as srv:
+        # capacity: a closed burst of the first requests
+        burst = min(400, nreq)
+        t = time.perf_counter()
+        tk = [srv.submit(**reqs[i]) for i in range(burst)]
+        for x in tk:
+            srv.wait(x)
+        cap = sum(moves_of[:burst]) / (time.perf_counter() - t)
+        rate = 0.8 * cap / float(np.mean(moves_of))  # requests per second
+        gaps = rng.exponential(1.0 / rate, size=nreq)
+        clocks = ClockSampler(0)
+        clocks.start()
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for i in range(nreq):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                time.sleep(min(0.001, max(0.0, due - time.perf_counter())))
+            tickets.append(srv.submit(**reqs[i]))
+        lat, done_moves, failed = [], 0, 0
+        for x in tickets:
+            img, st = srv.wait(x)
+            lat.append(st["done_ms"] - st["submit_ms"])
+            done_moves += st["proposed"]
+            failed += int(st["status"] != 0)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        info = srv.info()
+    out = {"metric": "SAT pixel-moves/s, served request stream; request p50/p99 ms", "value": done_moves / wall,
+           "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serve", "requests": nreq, "sizes": [64, 128, 256, 512], "stages": 50,
+                      "k": [1, 4, 8], "pila": "f16", "budget_gb": 120, "arrival": "poisson",
+                      "rate_per_s": rate, "capacity_moves_per_s": cap},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "failed": failed, "server": {k: info[k] for k in ("ticks", "bytes_peak", "geometries", "classes")},
+           "clocks": clk}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.workload == "precision512":
+        return run_precision(args)
+    if args.workload == "serve":
+        return run_serve(args)
     cfg = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,7 +512,6 @@ def main():
     run_kw = dict(bome_k=K, n_sweeps=S, t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0,
                   residency=args.residency, group_warps=args.group_warps, flags=args.flags)
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     info = {}
 
     def step():
@@ -317,28 +523,9 @@ def main():
         api.pila_free(p)
         return st
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    step_ms, sweep_ms = [], []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        sweep_ms.append(st[0]["sweep_ms"])
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
+    step_ms, stats, clk = timed_steps(args, step, stream, dist, local)
+    st = stats[-1]
+    sweep_ms = [x[0]["sweep_ms"] for x in stats]
     ms = shard.max_over_ranks(statistics.mean(step_ms), dist, device="cuda")
     M = int(mask.sum())
     moves_per_step = slices * S * M

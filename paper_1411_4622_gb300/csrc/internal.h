@@ -27,9 +27,17 @@ struct satpila_pila {
     // Residual band: every cell an annealing move can touch (bins k and k + 1
     // of each record of a reconstruction-space pixel) has band_lo <= bin <= band_hi.
     int band_lo = 0, band_hi = 0;
+    // Tables built for the serving engine come from a stream-ordered memory
+    // pool (no device-wide synchronisation on allocation or release).
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t alloc_stream = nullptr;
 };
 
 namespace satpila {
+
+// pila_build with its allocations taken from `pool` in the order of stream s
+// (pool == NULL: ordinary allocations, as pila_build).
+int pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s, cudaMemPool_t pool, satpila_pila** out);
 
 // Thread-local last-error message.
 void set_error(const std::string& msg);

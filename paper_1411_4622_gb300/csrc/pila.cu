@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -140,6 +141,11 @@ __global__ void pila_export_kernel(const unsigned char* table, int f16, int row_
 using namespace satpila;
 
 extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, satpila_pila** out) {
+    return satpila::pila_build_in(g, precision, (cudaStream_t)stream, nullptr, out);
+}
+
+int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t stream, cudaMemPool_t pool,
+                           satpila_pila** out) {
     if (!g || !out) return fail(SATPILA_ERR_INVALID_ARG, "pila_build: null argument");
     *out = nullptr;
     if (g->n < 1 || g->n_angles < 1 || g->n_bins < 1)
@@ -150,9 +156,11 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
         return fail(SATPILA_ERR_INVALID_ARG, "pila_build: PILA_F16 needs n_bins <= 32767");
     if ((long long)g->n * g->n > (1LL << 30))
         return fail(SATPILA_ERR_INVALID_ARG, "pila_build: image too large");
-    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t s = stream;
     auto* p = new satpila_pila();
     cudaGetDevice(&p->device);
+    p->pool = pool;
+    p->alloc_stream = pool ? s : nullptr;
     p->n = g->n;
     p->U = g->n_angles;
     p->B = g->n_bins;
@@ -186,15 +194,19 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
         pila_free(p);
         return fail(code, msg);
     };
+    auto dalloc = [&](auto** ptr, size_t bytes) {
+        void* v = nullptr;
+        const cudaError_t e = pool ? cudaMallocFromPoolAsync(&v, bytes, pool, s) : cudaMalloc(&v, bytes);
+        *ptr = static_cast<std::remove_pointer_t<decltype(ptr)>>(v);
+        return e == cudaSuccess;
+    };
     unsigned long long* d_entries = nullptr;  // entry count, then the band bounds
-    if (cudaMalloc(&p->d_table, p->table_bytes) != cudaSuccess ||
-        cudaMalloc(&p->d_list, std::max<size_t>(1, list.size()) * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&p->d_mask, P) != cudaSuccess || cudaMalloc(&p->d_cos, p->U * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&p->d_sin, p->U * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&p->d_hsum, P * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&d_entries, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (!dalloc(&p->d_table, p->table_bytes) || !dalloc(&p->d_list, std::max<size_t>(1, list.size()) * 4) ||
+        !dalloc(&p->d_mask, P) || !dalloc(&p->d_cos, p->U * sizeof(double)) ||
+        !dalloc(&p->d_sin, p->U * sizeof(double)) || !dalloc(&p->d_hsum, P * sizeof(float)) ||
+        !dalloc(&d_entries, 2 * sizeof(unsigned long long))) {
         cudaGetLastError();
-        if (d_entries) cudaFree(d_entries);
+        if (d_entries) pool ? cudaFreeAsync(d_entries, s) : cudaFree(d_entries);
         return cleanup(SATPILA_ERR_OOM, "pila_build: device allocation failed");
     }
     cudaError_t e = cudaSuccess;
@@ -230,7 +242,8 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
     unsigned long long entries[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(entries, d_entries, sizeof(entries), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_entries);
+    if (pool) cudaFreeAsync(d_entries, s);
+    else cudaFree(d_entries);
     if (e != cudaSuccess) {
         const std::string msg = std::string("pila_build: ") + cudaGetErrorString(e);
         return cleanup(SATPILA_ERR_CUDA, msg);
@@ -248,14 +261,14 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
 extern "C" int pila_free(satpila_pila* p) {
     if (!p) return SATPILA_OK;
     sat_cache_purge(p);
-    cudaFree(p->d_table);
-    cudaFree(p->d_list);
-    cudaFree(p->d_mask);
-    cudaFree(p->d_cos);
-    cudaFree(p->d_sin);
-    cudaFree(p->d_w64);
-    cudaFree(p->d_w32);
-    cudaFree(p->d_hsum);
+    void* bufs[] = {p->d_table, p->d_list, p->d_mask, p->d_cos, p->d_sin, p->d_hsum};
+    for (void* b : bufs) {
+        if (!b) continue;
+        if (p->pool) cudaFreeAsync(b, p->alloc_stream);
+        else cudaFree(b);
+    }
+    if (p->d_w64) cudaFree(p->d_w64);  // SIRT factor: ordinary allocations
+    if (p->d_w32) cudaFree(p->d_w32);
     delete p;
     return SATPILA_OK;
 }

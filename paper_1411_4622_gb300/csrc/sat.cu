@@ -53,10 +53,25 @@ cudaError_t launch_sweep(bool f16, bool smem, int kind, int jmax, int kmax, cons
     return cudaGetLastError();
 }
 
+// The shared-memory limit of a sweep kernel is set to the device maximum
+// once: the attribute belongs to the function, so a per-launch value would
+// be lowered under other callers (other sat_run calls, serving classes)
+// launching the same function with more.
+cudaError_t allow_max_smem(SweepFn k) {
+    int dev = 0, maxopt = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt);
+    return e;
+}
+
 int sweep_blocks_per_sm(bool f16, bool smem, int kind, int jmax, int kmax, int warps, size_t smem_bytes) {
     SweepFn k = sweep_kernel(f16, smem, jmax, kmax, kind);
     if (!k) return 0;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (allow_max_smem(k) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem_bytes) != cudaSuccess) return 0;
     return nb;
@@ -380,7 +395,7 @@ cudaError_t prepare_launches(const satpila_pila* p, const Plan& pl, int bome_k) 
     if (e != cudaSuccess) return e;
     SweepFn k = sweep_kernel(p->precision == PILA_F16, pl.smem, pl.jmax, kmax_for(bome_k), pl.kind);
     if (!k) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.sweep_smem_bytes());
+    return allow_max_smem(k);
 }
 
 cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev& b, int c0, int nc, bool drift,

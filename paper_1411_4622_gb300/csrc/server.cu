@@ -39,6 +39,16 @@ namespace {
 
 __global__ void tick_stamp_kernel(unsigned long long* out) { *out = global_ns(); }
 
+// S before the resync that follows a window, for the chains that ran stages
+// in it (so a chain's incremental cost is the one at its last stage).
+__global__ void s_inc_kernel(double* S_inc, const double* S, const ChainCtl* ctl, int n, int s_begin) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n && ctl[c].stage0 + s_begin < ctl[c].n_sweeps) S_inc[c] = S[c];
+}
+
+constexpr int kMaxWindowsPerTick = 32;
+constexpr double kTickTargetMs = 40.0;
+
 double now_ms(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -73,6 +83,42 @@ struct Geometry {
     size_t bytes = 0;
     int users = 0;  // classes holding it
     double last_use = 0.0;
+    std::vector<cudaEvent_t> released;  // end of the work of classes that used it
+};
+
+// Page-locked host blocks, reused by size class and released only when the
+// server stops (so no host allocation call stalls the device's work).
+struct PinnedPool {
+    std::map<size_t, std::vector<void*>> free_blocks;
+    std::vector<void*> all;
+    static size_t bucket(size_t b) {
+        size_t s = 256;
+        while (s < b) s <<= 1;
+        return s;
+    }
+    void* get(size_t bytes) {
+        auto& v = free_blocks[bucket(bytes)];
+        if (!v.empty()) {
+            void* q = v.back();
+            v.pop_back();
+            return q;
+        }
+        void* q = nullptr;
+        if (cudaMallocHost(&q, bucket(bytes)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        all.push_back(q);
+        return q;
+    }
+    void put(void* q, size_t bytes) {
+        if (q) free_blocks[bucket(bytes)].push_back(q);
+    }
+    void release() {
+        for (void* q : all) cudaFreeHost(q);
+        all.clear();
+        free_blocks.clear();
+    }
 };
 
 // One chain of a class (host mirror of slot state).
@@ -102,6 +148,8 @@ struct Class {
     int* h_err = nullptr;
     unsigned long long* h_stamps = nullptr;
     float* h_img = nullptr;    // [cap][P] images of finishing chains
+    size_t hb_ctl = 0, hb_scal = 0, hb_img = 0;  // their sizes (pinned-pool blocks)
+    std::vector<std::pair<void*, size_t>> staging;  // request inputs being copied in
     std::vector<Slot> slots;   // [n] active chains
     int n_ready = 0;           // chains whose setup has been enqueued
     cudaStream_t stream = nullptr;
@@ -109,7 +157,9 @@ struct Class {
     bool in_flight = false;
     std::vector<int> finishing;  // slots that complete with the tick in flight
     cudaGraphExec_t exec = nullptr;
-    int exec_n = -1;
+    int exec_n = -1, exec_windows = 0;
+    int windows = 1;       // resync windows per tick (grows until a tick is ~kTickTargetMs)
+    int tick_windows = 1;  // windows of the tick in flight
     double tick_ms = 0.0;
 };
 
@@ -136,6 +186,9 @@ struct satpila_server {
     std::list<std::unique_ptr<Class>> classes;
     size_t bytes_in_use = 0;
     cudaStream_t build_stream = nullptr;
+    cudaMemPool_t pool = nullptr;  // stream-ordered device memory of tables and classes
+    std::string where;             // the step a failed CUDA call belonged to
+    PinnedPool pinned;
     std::thread worker;
 
     void run();
@@ -169,7 +222,11 @@ Geometry* satpila_server::geometry_for(const Request& r, size_t budget_left) {
         if (!victim) return nullptr;
         bytes_in_use -= victim->bytes;
         budget_left += victim->bytes;
-        pila_free(victim->p);
+        for (cudaEvent_t ev : victim->released) {
+            cudaStreamWaitEvent(build_stream, ev, 0);  // its classes' last kernels come first
+            cudaEventDestroy(ev);
+        }
+        pila_free(victim->p);  // stream-ordered release on build_stream
         geoms.remove_if([&](const std::unique_ptr<Geometry>& g) { return g.get() == victim; });
     }
     pila_geom pg{};
@@ -179,7 +236,7 @@ Geometry* satpila_server::geometry_for(const Request& r, size_t budget_left) {
     pg.angles_rad = r.angles.empty() ? nullptr : r.angles.data();
     pg.mask = r.mask.empty() ? nullptr : r.mask.data();
     satpila_pila* p = nullptr;
-    if (pila_build(&pg, r.precision, build_stream, &p) != SATPILA_OK) return nullptr;
+    if (pila_build_in(&pg, r.precision, build_stream, pool, &p) != SATPILA_OK) return nullptr;
     auto g = std::make_unique<Geometry>();
     g->key = std::move(key);
     g->p = p;
@@ -233,27 +290,20 @@ int satpila_server::grow(Class* c, int need) {
     const size_t bytes = off_st + 256;
     if (bytes_in_use - c->dev_bytes + bytes > budget()) return SATPILA_ERR_OOM;
     void* dev = nullptr;
-    if (cudaMalloc(&dev, bytes) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&dev, bytes, pool, c->stream) != cudaSuccess) {
         cudaGetLastError();
         return SATPILA_ERR_OOM;
     }
-    ChainCtl* h_ctl = nullptr;
-    double* h_scal = nullptr;
-    float* h_img = nullptr;
-    int* h_err = nullptr;
-    unsigned long long* h_st = nullptr;
-    if (cudaMallocHost(&h_ctl, (size_t)cap * sizeof(ChainCtl)) != cudaSuccess ||
-        cudaMallocHost(&h_scal, (size_t)8 * cap * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&h_img, (size_t)cap * P * sizeof(float)) != cudaSuccess ||
-        cudaMallocHost(&h_err, sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(&h_st, 2 * sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(dev);
-        cudaFreeHost(h_ctl);
-        cudaFreeHost(h_scal);
-        cudaFreeHost(h_img);
-        cudaFreeHost(h_err);
-        cudaFreeHost(h_st);
+    const size_t hb_ctl = (size_t)cap * sizeof(ChainCtl), hb_scal = (size_t)8 * cap * sizeof(double) + 64;
+    const size_t hb_img = (size_t)cap * P * sizeof(float);
+    auto* h_ctl = (ChainCtl*)pinned.get(hb_ctl);
+    auto* h_scal = (double*)pinned.get(hb_scal);
+    auto* h_img = (float*)pinned.get(hb_img);
+    if (!h_ctl || !h_scal || !h_img) {
+        pinned.put(h_ctl, hb_ctl);
+        pinned.put(h_scal, hb_scal);
+        pinned.put(h_img, hb_img);
+        cudaFreeAsync(dev, c->stream);
         return SATPILA_ERR_OOM;
     }
     BatchDev nb;
@@ -266,7 +316,7 @@ int satpila_server::grow(Class* c, int need) {
     cudaError_t e = cudaMemsetAsync(dev, 0, bytes, c->stream);
     const int n = c->n_ready;
     if (n > 0 && e == cudaSuccess) {
-        // move the live chains' state into the new arrays
+        // move the live chains' state into the new arrays (stream-ordered)
         const BatchDev& ob = c->b;
         const int G = c->pl.proj_G;
         struct {
@@ -292,22 +342,19 @@ int satpila_server::grow(Class* c, int need) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(cp.d, cp.s, cp.bytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) std::memcpy(h_ctl, c->h_ctl, (size_t)n * sizeof(ChainCtl));
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        cudaFree(dev);
-        cudaFreeHost(h_ctl);
-        cudaFreeHost(h_scal);
-        cudaFreeHost(h_img);
-        cudaFreeHost(h_err);
-        cudaFreeHost(h_st);
+        pinned.put(h_ctl, hb_ctl);
+        pinned.put(h_scal, hb_scal);
+        pinned.put(h_img, hb_img);
+        cudaFreeAsync(dev, c->stream);
         return cuda_fail(e, "sat_server: growing a class");
     }
-    if (c->dev) cudaFree(c->dev);
-    cudaFreeHost(c->h_ctl);
-    cudaFreeHost(c->h_scal);
-    cudaFreeHost(c->h_img);
-    cudaFreeHost(c->h_err);
-    cudaFreeHost(c->h_stamps);
+    // the old arrays go back to the pool after the copies (stream order);
+    // no copy into the old host blocks is pending between ticks
+    if (c->dev) cudaFreeAsync(c->dev, c->stream);
+    pinned.put(c->h_ctl, c->hb_ctl);
+    pinned.put(c->h_scal, c->hb_scal);
+    pinned.put(c->h_img, c->hb_img);
     bytes_in_use = bytes_in_use - c->dev_bytes + bytes;
     c->dev = dev;
     c->dev_bytes = bytes;
@@ -319,8 +366,11 @@ int satpila_server::grow(Class* c, int need) {
     c->h_ctl = h_ctl;
     c->h_scal = h_scal;
     c->h_img = h_img;
-    c->h_err = h_err;
-    c->h_stamps = h_st;
+    c->h_err = reinterpret_cast<int*>(h_scal + 8 * (size_t)cap);
+    c->h_stamps = reinterpret_cast<unsigned long long*>(h_scal + 8 * (size_t)cap) + 2;
+    c->hb_ctl = hb_ctl;
+    c->hb_scal = hb_scal;
+    c->hb_img = hb_img;
     if (c->exec) {
         cudaGraphExecDestroy(c->exec);
         c->exec = nullptr;
@@ -331,15 +381,22 @@ int satpila_server::grow(Class* c, int need) {
 
 void satpila_server::release_class(Class* c) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->dev) cudaFree(c->dev);
-    cudaFreeHost(c->h_ctl);
-    cudaFreeHost(c->h_scal);
-    cudaFreeHost(c->h_img);
-    cudaFreeHost(c->h_err);
-    cudaFreeHost(c->h_stamps);
+    if (c->dev) cudaFreeAsync(c->dev, c->stream);
+    cudaEvent_t done_ev = nullptr;
+    if (cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(done_ev, c->stream) == cudaSuccess)
+        c->g->released.push_back(done_ev);
+    else if (done_ev)
+        cudaEventDestroy(done_ev);
+    cudaGetLastError();
+    // between ticks no copy into these host blocks is pending
+    pinned.put(c->h_ctl, c->hb_ctl);
+    pinned.put(c->h_scal, c->hb_scal);
+    pinned.put(c->h_img, c->hb_img);
+    for (auto& b : c->staging) pinned.put(b.first, b.second);
+    c->staging.clear();
     if (c->ev) cudaEventDestroy(c->ev);
-    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->stream) cudaStreamDestroy(c->stream);  // returns at once; queued work still completes
     bytes_in_use -= c->dev_bytes;
     c->g->users--;
     c->g->last_use = now_ms(t0);
@@ -357,10 +414,16 @@ cudaError_t satpila_server::setup_chains(Class* c, int first, int count,
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         const Request& r = *reqs[i];
         const int s = first + i;
-        e = cudaMemcpyAsync((void*)(c->b.sino + (size_t)s * cells), r.sino.data(), cells * 4, cudaMemcpyHostToDevice,
-                            c->stream);
+        // inputs through a page-locked block, released after the next tick
+        const size_t bytes = (cells + P) * 4;
+        auto* st = (float*)pinned.get(bytes);
+        if (!st) return cudaErrorMemoryAllocation;
+        c->staging.push_back({st, bytes});
+        std::memcpy(st, r.sino.data(), cells * 4);
+        std::memcpy(st + cells, r.image.data(), P * 4);
+        e = cudaMemcpyAsync((void*)(c->b.sino + (size_t)s * cells), st, cells * 4, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c->b.img + (size_t)s * P, r.image.data(), P * 4, cudaMemcpyHostToDevice, c->stream);
+            e = cudaMemcpyAsync(c->b.img + (size_t)s * P, st + cells, P * 4, cudaMemcpyHostToDevice, c->stream);
     }
     const int G = c->pl.proj_G;
     auto zero = [&](void* ptr, size_t each) {
@@ -375,9 +438,12 @@ cudaError_t satpila_server::setup_chains(Class* c, int first, int count,
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = enqueue_resync(p, c->pl, c->b, first, count, false, c->b.cost0, c->stream);
     if (e == cudaSuccess) e = enqueue_t0(p, c->pl, c->b, &c->prm, first, count, c->stream);
-    // the resync of the first tick overwrites costF; until then it is cost0
+    // until a window runs, the final and the incremental cost are the initial ones
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->b.costF + first, c->b.cost0 + first, (size_t)count * 8, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->b.S_inc + first, c->b.S + first, (size_t)count * 8, cudaMemcpyDeviceToDevice,
                             c->stream);
     return e;
 }
@@ -386,41 +452,59 @@ cudaError_t satpila_server::launch_tick(Class* c) {
     const satpila_pila* p = c->g->p;
     const int n = (int)c->slots.size();
     const int w = cfg.stages_per_tick;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        where = "an earlier call";
+        return e;
+    }
     if (c->plan_n != n) {
         Plan pl;
-        if (choose_plan(p, n, w, &c->prm, PLAN_RULES, &pl) != SATPILA_OK) return cudaErrorInvalidValue;
-        if ((e = prepare_launches(p, pl, c->K)) != cudaSuccess) return e;
+        if (choose_plan(p, n, w, &c->prm, PLAN_RULES, &pl) != SATPILA_OK) {
+            where = std::string("plan: ") + satpila_last_error();
+            return cudaErrorInvalidValue;
+        }
+        if ((e = prepare_launches(p, pl, c->K)) != cudaSuccess) {
+            where = "launch attributes";
+            return e;
+        }
         c->pl = pl;  // array layout (resid_floats, proj_G) does not depend on n
         c->plan_n = n;
     }
-    // stage offsets of this tick
+    // A tick is `T` windows of w stages, each followed by the resync (so the
+    // resync cadence, and with it every result, does not depend on T).
+    const int T = c->windows;
+    c->tick_windows = T;
     int max_total = 0;
     c->finishing.clear();
     for (int i = 0; i < n; ++i) {
         c->h_ctl[i] = c->slots[i].ctl;
         max_total = std::max(max_total, c->slots[i].ctl.n_sweeps);
-        if (c->slots[i].ctl.stage0 + w >= c->slots[i].ctl.n_sweeps) c->finishing.push_back(i);
+        if (c->slots[i].ctl.stage0 + w * T >= c->slots[i].ctl.n_sweeps) c->finishing.push_back(i);
     }
-    // The compute of a tick as one graph, rebuilt when the batch size changes.
+    // The compute of a tick as one graph, rebuilt when the batch size or T changes.
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t err = cudaMemcpyAsync(c->d_ctl, c->h_ctl, (size_t)n * sizeof(ChainCtl), cudaMemcpyHostToDevice, q);
         if (err == cudaSuccess) err = cudaMemsetAsync(c->b.progress, 0, (size_t)n * 4, q);
-        if (err == cudaSuccess) err = cudaMemsetAsync(c->d_counter, 0, 4, q);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->d_counter, 0, (size_t)T * 4, q);
         if (err == cudaSuccess) {
             tick_stamp_kernel<<<1, 1, 0, q>>>(c->d_stamps);
             err = cudaGetLastError();
         }
-        if (err == cudaSuccess) err = enqueue_sweep(p, c->pl, c->b, &c->prm, n, c->M, max_total, 0, w, c->d_counter, q);
+        for (int t = 0; t < T && err == cudaSuccess; ++t) {
+            err = enqueue_sweep(p, c->pl, c->b, &c->prm, n, c->M, max_total, t * w, (t + 1) * w, c->d_counter + t, q);
+            if (err == cudaSuccess) {
+                s_inc_kernel<<<(n + 127) / 128, 128, 0, q>>>(c->b.S_inc, c->b.S, c->d_ctl, n, t * w);
+                err = cudaGetLastError();
+            }
+            if (err == cudaSuccess) err = enqueue_resync(p, c->pl, c->b, 0, n, true, c->b.costF, q);
+        }
         if (err == cudaSuccess) {
             tick_stamp_kernel<<<1, 1, 0, q>>>(c->d_stamps + 1);
             err = cudaGetLastError();
         }
-        if (err == cudaSuccess) err = enqueue_copy_f64(c->b.S_inc, c->b.S, n, q);
-        if (err == cudaSuccess) err = enqueue_resync(p, c->pl, c->b, 0, n, true, c->b.costF, q);
         return err;
     };
-    if (c->exec_n != n) {
+    if (c->exec_n != n || c->exec_windows != T) {
         if (c->exec) cudaGraphExecDestroy(c->exec);
         c->exec = nullptr;
         cudaGraph_t graph = nullptr;
@@ -440,9 +524,13 @@ cudaError_t satpila_server::launch_tick(Class* c) {
             c->exec = nullptr;
         }
         c->exec_n = c->exec ? n : -1;
+        c->exec_windows = T;
     }
     e = c->exec ? cudaGraphLaunch(c->exec, c->stream) : enqueue(c->stream);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        where = c->exec ? "graph launch" : "direct launches";
+        return e;
+    }
     // statistics of every chain, images of the finishing ones
     const double* src[8] = {c->b.T0, c->b.TN, c->b.cost0, c->b.costF, c->b.S_inc, c->b.drift_max,
                             (const double*)c->b.accepted, nullptr};
@@ -461,11 +549,14 @@ cudaError_t satpila_server::launch_tick(Class* c) {
                                 c->stream);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev, c->stream);
     if (e == cudaSuccess) c->in_flight = true;
+    else where = "result copies";
     return e;
 }
 
 cudaError_t satpila_server::finish_tick(Class* c) {
     c->in_flight = false;
+    for (auto& b : c->staging) pinned.put(b.first, b.second);  // copied in before the tick
+    c->staging.clear();
     const satpila_pila* p = c->g->p;
     const int w = cfg.stages_per_tick;
     const int n = (int)c->slots.size();
@@ -474,9 +565,12 @@ cudaError_t satpila_server::finish_tick(Class* c) {
     const int err_code = *c->h_err;
     c->tick_ms = 1e-6 * (double)(c->h_stamps[1] - c->h_stamps[0]);
     long long moves = 0;
+    const int ws = w * c->tick_windows;
+    if (c->tick_ms < 0.5 * kTickTargetMs && c->windows < kMaxWindowsPerTick) c->windows *= 2;
+    else if (c->tick_ms > 4.0 * kTickTargetMs && c->windows > 1) c->windows /= 2;
     for (int i = 0; i < n; ++i) {
         Slot& sl = c->slots[i];
-        const int run = std::max(0, std::min(w, sl.ctl.n_sweeps - sl.ctl.stage0));
+        const int run = std::max(0, std::min(ws, sl.ctl.n_sweeps - sl.ctl.stage0));
         moves += (long long)run * (p->n_mask > 0 ? c->M : 0);
         sl.ctl.stage0 += run;
     }
@@ -595,7 +689,20 @@ void satpila_server::fail_all(int code, const std::string& msg) {
 void satpila_server::run() {
     cudaSetDevice(cfg.device);
     cudaStreamCreateWithFlags(&build_stream, cudaStreamNonBlocking);
-    for (;;) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = cfg.device;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+        fail_all(SATPILA_ERR_CUDA, "sat_server: no device memory pool");
+        return;
+    }
+    uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool for reuse
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    bool failed = false;
+    while (!failed) {
         bool worked = false;
         // 1. admission, in arrival order, while slots and memory allow
         {
@@ -658,8 +765,9 @@ void satpila_server::run() {
             }
             cudaError_t e = setup_chains(c, first, (int)reqs.size(), reqs);
             if (e != cudaSuccess) {
-                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: ") + cudaGetErrorString(e));
-                return;
+                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: chain setup: ") + cudaGetErrorString(e));
+                failed = true;
+                break;
             }
             c->n_ready = (int)c->slots.size();
             std::lock_guard<std::mutex> lock(mu);
@@ -667,33 +775,39 @@ void satpila_server::run() {
             for (auto& r : reqs) state[r->ticket] = 1;
             worked = true;
         }
-        // 2. chains with no stages to run (n_sweeps == 0) finish at once;
-        //    every other class with chains and no tick in flight launches one
+        if (failed) break;
+        // 2. every class with chains and no tick in flight launches one (a
+        //    chain with no stages left finishes with it)
         for (auto& c : classes) {
             if (c->in_flight || c->slots.empty()) continue;
             cudaError_t e = launch_tick(c.get());
             if (e != cudaSuccess) {
-                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: ") + cudaGetErrorString(e));
-                return;
+                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: tick launch (") + where + "): " + cudaGetErrorString(e));
+                failed = true;
+                break;
             }
             worked = true;
         }
+        if (failed) break;
         // 3. retire finished ticks
         for (auto& c : classes) {
             if (!c->in_flight) continue;
             const cudaError_t q = cudaEventQuery(c->ev);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) {
-                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: ") + cudaGetErrorString(q));
-                return;
+                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: tick: ") + cudaGetErrorString(q));
+                failed = true;
+                break;
             }
             cudaError_t e = finish_tick(c.get());
             if (e != cudaSuccess) {
-                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: ") + cudaGetErrorString(e));
-                return;
+                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: retiring: ") + cudaGetErrorString(e));
+                failed = true;
+                break;
             }
             worked = true;
         }
+        if (failed) break;
         // 4. empty classes give their memory back
         for (auto it = classes.begin(); it != classes.end();) {
             Class* c = it->get();
@@ -720,11 +834,28 @@ void satpila_server::run() {
             cv_work.wait_for(lock, std::chrono::microseconds(200));
         }
     }
-    for (auto& c : classes) release_class(c.get());
+    // shutdown: every class and table back, then wait for this server's
+    // device work before its host blocks go
+    for (auto& c : classes) {
+        if (c->in_flight) cudaEventSynchronize(c->ev);
+        release_class(c.get());
+    }
     classes.clear();
-    for (auto& g : geoms) pila_free(g->p);
+    for (auto& g : geoms) {
+        for (cudaEvent_t ev : g->released) {
+            cudaStreamWaitEvent(build_stream, ev, 0);
+            cudaEventDestroy(ev);
+        }
+        g->released.clear();
+        pila_free(g->p);
+    }
     geoms.clear();
-    if (build_stream) cudaStreamDestroy(build_stream);
+    if (build_stream) {
+        cudaStreamSynchronize(build_stream);
+        cudaStreamDestroy(build_stream);
+    }
+    pinned.release();
+    if (pool) cudaMemPoolDestroy(pool);
 }
 
 // ---- C ABI -------------------------------------------------------------------
@@ -869,7 +1000,9 @@ int take_result(satpila_server* s, uint64_t ticket, float* image_out, sat_result
     }
     const int status = it->second.res.stats.status;
     s->done.erase(it);
-    return status ? fail(status, "sat_server: the request failed on the device") : SATPILA_OK;
+    if (!status) return SATPILA_OK;
+    return fail(status, s->fatal ? "sat_server: the server stopped: " + s->fatal_msg
+                                 : std::string("sat_server: a device-side check failed for the request"));
 }
 
 }  // namespace
