@@ -396,6 +396,10 @@ def run_serve(args):
     space, under a 120 GB device budget.  The arrival rate is 80% of the
     capacity measured on a closed burst of up to 400 requests of the mix.  Reported: moves/s
     over the stream and per-request latency (submit to result) p50/p99."""
+    # one hardware work queue per stream for up to 32 streams (the default 8
+    # makes classes' launches wait behind unrelated long ones); read when the
+    # CUDA context is created, so set before the first CUDA call
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     from paper_1411_4622_gb300 import api
