@@ -23,6 +23,7 @@ _lib = None
 
 SCHED_LINEAR, SCHED_GEOMETRIC, SCHED_CUBIC = 0, 1, 2
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
+BOME_SAME_PIXEL, BOME_INDEPENDENT = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -48,7 +49,8 @@ class Geom(C.Structure):
 class SatParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("bome_k", C.c_int32), ("n_sweeps", C.c_int32),
                 ("moves_per_sweep", C.c_int32), ("t0", C.c_double), ("tn", C.c_double),
-                ("schedule", C.c_int32), ("t0_samples", C.c_int32), ("seed", C.c_uint64)]
+                ("schedule", C.c_int32), ("t0_samples", C.c_int32), ("seed", C.c_uint64),
+                ("bome_mode", C.c_int32), ("pad", C.c_int32)]
 
 
 class SatStats(C.Structure):
@@ -188,9 +190,9 @@ def schedule_temp(schedule, t0, tn, s, n_sweeps):
     return _load().or_schedule_temp(schedule, t0, tn, s, n_sweeps)
 
 
-def _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed):
+def _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode=0):
     return SatParams(float(beta), int(bome_k), int(n_sweeps), int(moves_per_sweep), float(t0),
-                     float(tn), int(schedule), int(t0_samples), int(seed) & (2**64 - 1))
+                     float(tn), int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(bome_mode), 0)
 
 
 def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=None):
@@ -209,14 +211,15 @@ def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=Non
 
 
 def sat_run(pm, image, *, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn=-1.0,
-            schedule=SCHED_LINEAR, t0_samples=200, seed=0, mask=None, angles=None, trace=False):
+            schedule=SCHED_LINEAR, t0_samples=200, seed=0, mask=None, angles=None, trace=False,
+            bome_mode=BOME_SAME_PIXEL):
     """Steps 1-4 of Sec. II-A with Eqs. (6)-(7) and BoME; returns (image, stats, trace)."""
     pm_ = _f64(pm)
     img = _f64(image).copy()
     n = img.shape[0]
     g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
     m = _mask(mask, n)
-    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed)
+    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode)
     moves = moves_per_sweep if moves_per_sweep > 0 else (int(m.sum()) if m is not None else n * n)
     tr = np.zeros(n_sweeps * moves, dtype=TRACE_DTYPE) if trace else None
     st = SatStats()
@@ -229,13 +232,13 @@ def sat_run(pm, image, *, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=
 
 
 def sat_lockstep(pm, image, gpu_trace, *, t0, tn, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0,
-                 schedule=SCHED_LINEAR, seed=0, mask=None, angles=None, tol=1e-5):
+                 schedule=SCHED_LINEAR, seed=0, mask=None, angles=None, tol=1e-5, bome_mode=BOME_SAME_PIXEL):
     """Follow another implementation's move trace in FP64 (near-tie protocol)."""
     pm_ = _f64(pm)
     img = _f64(image).copy()
     n = img.shape[0]
     g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
-    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, 200, seed)
+    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, 200, seed, bome_mode)
     tr = np.ascontiguousarray(gpu_trace, dtype=GPU_TRACE_DTYPE)
     rep = LockstepReport()
     rc = _load().or_sat_lockstep(C.byref(g), _ptr(_mask(mask, n)), _ptr(pm_), _ptr(img), C.byref(prm),

@@ -69,7 +69,13 @@ typedef struct {
     int32_t schedule;       /* OR_SCHED_* */
     int32_t t0_samples;     /* Q of Eq. (8); 0 means 200 */
     uint64_t seed;          /* this chain's Philox key */
+    int32_t bome_mode;      /* OR_BOME_SAME_PIXEL or OR_BOME_INDEPENDENT */
+    int32_t pad;
 } or_sat_params;
+
+/* Sec. III-B: every estimate at the move's one pixel, or (the paper's own
+ * wording) each estimate at its own randomly chosen pixel. */
+enum { OR_BOME_SAME_PIXEL = 0, OR_BOME_INDEPENDENT = 1 };
 
 typedef struct {
     double t0, tn;

@@ -11,7 +11,11 @@
 //    A uniform is ((x >> 9) * 2 + 1) * 2^-24, exact in FP32 and FP64.
 //  * Eq. (3) with its redraw rule is the uniform law on
 //    [max(0, f - beta), min(beta, f + beta)]: one draw, same distribution.
-//  * All N_e estimates are values at the pixel drawn for the move.
+//  * BoME, OR_BOME_SAME_PIXEL: all N_e estimates are values at the pixel
+//    drawn for the move.  OR_BOME_INDEPENDENT (the paper's wording, Sec.
+//    III-B): estimate c is a value at its own pixel; draw 2 + c is its value,
+//    draw 2 + N_e + (c - 1) picks its pixel for c >= 1 (estimate 0 uses draw
+//    0), so with N_e = 1 both modes draw the same move.
 //  * Step 4 with dC == 0 accepts; with T == 0 only dC <= 0 is accepted.
 //  * Stage s = 0..S-1 runs at T_s of the chosen schedule (T_N itself is the
 //    limit that is never run).
@@ -164,6 +168,57 @@ Choice best_estimate(const Problem& pb, int p, double f, const uint32_t* w, cons
     return Choice{best, fcs[best], fcs[best] - f, sums[best], cps[best], scales[best], second - sums[best]};
 }
 
+// Words per move: 2 + N_e, plus N_e - 1 pixel draws in the independent mode.
+int move_blocks(const or_sat_params* prm) {
+    const int words = prm->bome_mode == OR_BOME_INDEPENDENT ? 2 * prm->bome_k + 1 : prm->bome_k + 2;
+    return (words + 3) / 4;
+}
+
+int estimate_pixel(const Problem& pb, const uint32_t* w, int K, int c) {
+    const uint32_t x = c == 0 ? w[0] : w[2 + K + (c - 1)];
+    return pb.list[pick(x, (uint32_t)pb.list.size())];
+}
+
+struct IndChoice {
+    Choice ch;
+    int pixel;  // the chosen estimate's pixel
+    double f;   // its value before the move
+};
+
+// Sec. III-B as written: N_e estimates, each a random pixel of the
+// reconstruction space with a random value by Eq. (3); all are evaluated on
+// the same current state and the one with the smallest cost is kept.
+IndChoice best_independent(const Problem& pb, const double* image, const uint32_t* w, const or_sat_params* prm,
+                           std::vector<double>* sums_out, std::vector<int>* pix_out) {
+    const int K = prm->bome_k;
+    std::vector<double> local;
+    std::vector<double>& sums = sums_out ? *sums_out : local;
+    std::vector<int> lpix;
+    std::vector<int>& pix = pix_out ? *pix_out : lpix;
+    sums.assign(K, 0.0);
+    pix.assign(K, 0);
+    std::vector<double> fcs(K), fs(K), scales(K), cps(K);
+    for (int c = 0; c < K; ++c) {
+        pix[c] = estimate_pixel(pb, w, K, c);
+        fs[c] = image[pix[c]];
+        const double lo = std::fmax(0.0, fs[c] - prm->beta), hi = std::fmin(prm->beta, fs[c] + prm->beta);
+        fcs[c] = lo + uniform01(w[2 + c]) * (hi - lo);
+        sums[c] = eq7_sum(pb, pix[c], fcs[c] - fs[c], &scales[c]);
+        cps[c] = cost_after(pb, sums[c]);
+    }
+    int best = 0;
+    for (int c = 1; c < K; ++c)
+        if (cps[c] < cps[best]) best = c;
+    double second = INFINITY;
+    for (int c = 0; c < K; ++c)
+        if (c != best && sums[c] < second) second = sums[c];
+    IndChoice r;
+    r.ch = Choice{best, fcs[best], fcs[best] - fs[best], sums[best], cps[best], scales[best], second - sums[best]};
+    r.pixel = pix[best];
+    r.f = fs[best];
+    return r;
+}
+
 }  // namespace
 
 extern "C" double or_schedule_temp(int32_t schedule, double t0, double tn, int32_t s, int32_t n_sweeps) {
@@ -203,7 +258,7 @@ extern "C" int or_sat_run(const or_geom* g, const uint8_t* mask, const double* p
     st.t0 = t0;
     st.tn = tn;
     const int64_t M = prm->moves_per_sweep > 0 ? prm->moves_per_sweep : (int64_t)pb.list.size();
-    const int nblk = (prm->bome_k + 2 + 3) / 4;
+    const int nblk = move_blocks(prm);
     std::vector<uint32_t> w(4 * nblk);
     int64_t rec = 0;
     for (int s = 0; s < prm->n_sweeps && !pb.list.empty(); ++s) {
@@ -211,10 +266,18 @@ extern "C" int or_sat_run(const or_geom* g, const uint8_t* mask, const double* p
         for (int64_t m = 0; m < M; ++m) {
             // Step 2: a random pixel and N_e candidate values for it.
             draw_words(prm->seed, (uint32_t)s, (uint32_t)m, kStreamSat, nblk, w.data());
-            const int p = pb.list[pick(w[0], (uint32_t)pb.list.size())];
-            const double f = image[p];
-            // Step 3 + BoME: the estimate with the smallest cost, by Eq. (7).
-            const Choice ch = best_estimate(pb, p, f, w.data(), prm, nullptr);
+            int p;
+            Choice ch;
+            if (prm->bome_mode == OR_BOME_INDEPENDENT) {
+                // Step 2 + 3 + BoME: N_e (pixel, value) estimates, the cheapest kept.
+                const IndChoice ic = best_independent(pb, image, w.data(), prm, nullptr, nullptr);
+                p = ic.pixel;
+                ch = ic.ch;
+            } else {
+                p = pb.list[pick(w[0], (uint32_t)pb.list.size())];
+                // Step 3 + BoME: the estimate with the smallest cost, by Eq. (7).
+                ch = best_estimate(pb, p, image[p], w.data(), prm, nullptr);
+            }
             const double dC = ch.Cp_best - pb.C;
             // Step 4: Metropolis acceptance.
             const double n1 = uniform01(w[1]);
@@ -265,23 +328,26 @@ extern "C" int or_sat_lockstep(const or_geom* g, const uint8_t* mask, const doub
     r.max_err_dC = 0.0;
     r.max_err_f = 0.0;
     const int64_t M = prm->moves_per_sweep > 0 ? prm->moves_per_sweep : (int64_t)pb.list.size();
-    const int nblk = (prm->bome_k + 2 + 3) / 4;
+    const int nblk = move_blocks(prm);
+    const bool indep = prm->bome_mode == OR_BOME_INDEPENDENT;
     std::vector<uint32_t> w(4 * nblk);
     std::vector<double> sums;
+    std::vector<int> pix;
     int64_t idx = 0;
     for (int s = 0; s < prm->n_sweeps && idx < n_moves && !pb.list.empty(); ++s) {
         const double T = or_schedule_temp(prm->schedule, t0, tn, s, prm->n_sweeps);
         for (int64_t m = 0; m < M && idx < n_moves; ++m, ++idx) {
             const or_gpu_trace& gt = trace[idx];
             draw_words(prm->seed, (uint32_t)s, (uint32_t)m, kStreamSat, nblk, w.data());
-            const int p = pb.list[pick(w[0], (uint32_t)pb.list.size())];
-            if (p != gt.pixel) {
+            const int p0 = pb.list[pick(w[0], (uint32_t)pb.list.size())];
+            if (!indep && p0 != gt.pixel) {
                 r.pixel_mismatch = idx;
                 goto done;
             }
             {
-                const double f = image[p];
-                Choice ch = best_estimate(pb, p, f, w.data(), prm, &sums);
+                Choice ch;
+                if (indep) ch = best_independent(pb, image, w.data(), prm, &sums, &pix).ch;
+                else ch = best_estimate(pb, p0, image[p0], w.data(), prm, &sums);
                 int c = ch.cstar;
                 if (gt.cstar != c) {
                     // BoME near-tie: the other side's pick is within tolerance of ours.
@@ -297,6 +363,13 @@ extern "C" int or_sat_lockstep(const or_geom* g, const uint8_t* mask, const doub
                     ++r.near_ties;
                     c = gt.cstar;
                 }
+                // the move the other side made: estimate c at its pixel
+                const int p = indep ? pix[c] : p0;
+                if (p != gt.pixel) {
+                    r.pixel_mismatch = idx;
+                    goto done;
+                }
+                const double f = image[p];
                 const double lo = std::fmax(0.0, f - prm->beta), hi = std::fmin(prm->beta, f + prm->beta);
                 const double fc = lo + uniform01(w[2 + c]) * (hi - lo);
                 double scale = 0.0;

@@ -225,6 +225,57 @@ def test_eq7_and_bome_against_brute_force(orc):
     assert np.allclose(cur, img, atol=1e-15)
 
 
+def test_bome_independent_pixels_against_brute_force(orc):
+    """Sec. III-B as written: each estimate is a random pixel with a random
+    value.  Every move's chosen estimate is the exhaustive argmin of C' over
+    the N_e (pixel, value) pairs, each C' recomputed from scratch with the DRT
+    and Eq. (4); draw 2 + c is estimate c's value and draw 2 + N_e + c - 1 its
+    pixel (estimate 0 takes draw 0)."""
+    n, U, K, seed, beta = 8, 9, 4, 78, 1.0
+    ph, B, _ = _small_problem(n, U)
+    pm = orc.drt(ph, U, B)
+    img0 = np.full((n, n), 0.5)
+    M = 40
+    img, st, tr = orc.sat_run(pm, img0, bome_k=K, n_sweeps=2, moves_per_sweep=M, t0=1e-3, tn=1e-4,
+                              seed=seed, trace=True, bome_mode=orc.BOME_INDEPENDENT)
+    cur = img0.copy()
+    nblk = (2 * K + 1 + 3) // 4
+    distinct = 0
+    for idx, rec in enumerate(tr):
+        s, m = divmod(idx, M)
+        w = _draw(orc, seed, s, m, 1, nblk)
+        pix = [(w[0] * n * n) >> 32] + [(w[2 + K + c - 1] * n * n) >> 32 for c in range(1, K)]
+        distinct += len(set(pix)) > 1
+        c_now = orc.cost(orc.drt(cur, U, B), pm)
+        costs, vals = [], []
+        for c in range(K):
+            f = cur.flat[pix[c]]
+            lo, hi = max(0.0, f - beta), min(beta, f + beta)
+            vals.append(lo + _u01(w[2 + c]) * (hi - lo))
+            trial = cur.copy()
+            trial.flat[pix[c]] = vals[c]
+            costs.append(orc.cost(orc.drt(trial, U, B), pm))
+        best = int(np.argmin(costs))
+        assert rec["cstar"] == best and rec["pixel"] == pix[best]
+        assert abs(rec["dC"] - (costs[best] - c_now)) < 1e-12
+        if rec["accepted"]:
+            cur.flat[pix[best]] = vals[best]
+    assert distinct > 0.9 * len(tr)
+    assert np.allclose(cur, img, atol=1e-15)
+
+
+def test_bome_modes_agree_for_one_estimate(orc):
+    """With N_e = 1 both BoME readings draw the same single (pixel, value)
+    proposal, so the chains are identical."""
+    n, U = 12, 10
+    ph, B, _ = _small_problem(n, U)
+    pm = synth.gaussian_noise(orc.drt(ph, U, B), 0.01, 5)
+    a, sa, _ = orc.sat_run(pm, np.full((n, n), 0.5), bome_k=1, n_sweeps=3, seed=12)
+    b, sb, _ = orc.sat_run(pm, np.full((n, n), 0.5), bome_k=1, n_sweeps=3, seed=12,
+                           bome_mode=orc.BOME_INDEPENDENT)
+    assert np.array_equal(a, b) and sa["accepted"] == sb["accepted"]
+
+
 def test_incremental_state_matches_fresh_drt(orc):
     n, U = 16, 20
     ph, B, _ = _small_problem(n, U)
