@@ -135,6 +135,11 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
                                  warps per chain (angle tiling), chains per CTA and residency */
 #define SAT_FLAG_HYBRID 4u    /* with more chains than shared-memory slots, also run chains on
                                  global-memory warps beside them (same arithmetic) */
+#define SAT_FLAG_BOME_INDEPENDENT 8u /* BoME as Sec. III-B words it: each estimate is its own random
+                                 pixel with its own value (default: bome_k values at one pixel).
+                                 Draw 2 + e is estimate e's value, draw 0 (e = 0) or
+                                 2 + bome_k + e - 1 (e >= 1) picks its pixel; the trace records
+                                 the chosen estimate's pixel.  Residual in global memory. */
 
 typedef struct {
     int32_t pixel;     /* pixel index i*n + j */

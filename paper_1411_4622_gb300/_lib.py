@@ -18,7 +18,7 @@ ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS, ERR_BUSY, ERR_NOT_F
 PILA_F32, PILA_F16 = 0, 1
 SAT_SCHED_LINEAR, SAT_SCHED_GEOMETRIC, SAT_SCHED_CUBIC = 0, 1, 2
 SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
-SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID = 1, 2, 4
+SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID, SAT_FLAG_BOME_INDEPENDENT = 1, 2, 4, 8
 (SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
  SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4) = range(7)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1

@@ -31,13 +31,16 @@ SweepFn sweep_kernel_f16_smem(int jmax, int kmax);
 SweepFn sweep_kernel_f16_glob(int jmax, int kmax);
 SweepFn window_kernel(bool f16, bool smem, int jmax, int kmax);
 SweepFn hybrid_kernel(bool f16, int jmax, int kmax);
+SweepFn bome_kernel(bool f16, int jmax, int kmax);
+int bome_warps_per_cta();
 
 namespace {
 
-// kind: 0 pipelined, 1 windowed, 2 hybrid
+// kind: 0 pipelined, 1 windowed, 2 hybrid, 3 independent-pixel BoME
 SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax, int kind = 0) {
     if (kind == 1) return window_kernel(f16, smem, jmax, kmax);
     if (kind == 2) return hybrid_kernel(f16, jmax, kmax);
+    if (kind == 3) return bome_kernel(f16, jmax, kmax);
     if (f16) return smem ? sweep_kernel_f16_smem(jmax, kmax) : sweep_kernel_f16_glob(jmax, kmax);
     return smem ? sweep_kernel_f32_smem(jmax, kmax) : sweep_kernel_f32_glob(jmax, kmax);
 }
@@ -220,6 +223,38 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     if (projector_plan(p->U, p->B, &pl->proj_A, &pl->proj_G) != SATPILA_OK)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many bins");
     pl->variant = variant;
+    // Sec. III-B as written (an independent pixel per estimate): its own
+    // kernel, one warp per chain, residual in global memory.
+    if (prm->flags & SAT_FLAG_BOME_INDEPENDENT) {
+        if (prm->residency == SAT_RESIDENT_SMEM)
+            return fail(SATPILA_ERR_INVALID_ARG, "sat_run: independent-pixel BoME keeps the residual in global memory");
+        const int J = records_per_lane(1);
+        int jmax = 0;
+        for (int c : {2, 4, 8, 16})
+            if (J <= c) {
+                jmax = c;
+                break;
+            }
+        if (!jmax) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many angles for independent-pixel BoME");
+        pl->kind = 3;
+        pl->smem = false;
+        pl->W = 1;
+        pl->J = pl->jmax = jmax;
+        pl->D = 2;
+        pl->stage_bytes = 512 * (f16 ? jmax / 2 : jmax);
+        pl->group_smem = (int)align_up((size_t)2 * prm->bome_k * pl->stage_bytes, 128);
+        const int warps = std::max(1, std::min(bome_warps_per_cta(), maxopt / pl->group_smem));
+        pl->groups = pl->warps = std::min(warps, std::max(1, n_chains));
+        int per_sm = sweep_blocks_per_sm(f16, false, 3, jmax, kmax_for(prm->bome_k), pl->warps,
+                                         (size_t)pl->warps * pl->group_smem);
+        if (per_sm < 1) per_sm = 1;
+        const long long slots = (long long)sms * per_sm * pl->warps;
+        pl->spt = n_chains <= slots ? window : 1;
+        const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
+        const long long want = (std::min<long long>(tasks, slots) + pl->warps - 1) / pl->warps;
+        pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
+        return SATPILA_OK;
+    }
     // The windowed kernel: one warp per chain; residual in shared memory, in
     // global memory, or both kinds of warp side by side (hybrid).
     const bool window_ok = records_per_lane(1) <= 4;
@@ -798,7 +833,8 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
 
     // Launch plan, chosen by rules or by the autotuner.
     int variant = PLAN_RULES;
-    if ((prm->flags & SAT_FLAG_AUTOTUNE) && S_total > 0 && p->n_mask > 0)
+    if ((prm->flags & SAT_FLAG_AUTOTUNE) && !(prm->flags & SAT_FLAG_BOME_INDEPENDENT) && S_total > 0 &&
+        p->n_mask > 0)
         variant = autotune(p, n_chains, (const float*)d_sino.dev, (const float*)d_img.dev, prm, M, s);
     Plan pl;
     if ((rc = choose_plan(p, n_chains, shape.window, prm, variant, &pl)) != SATPILA_OK) {

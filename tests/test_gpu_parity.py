@@ -486,3 +486,50 @@ def test_autotune_picks_a_layout_and_is_repeatable(api):
     r_rule = np.mean([synth.rmse(rule.cpu().numpy()[c], ph[c]) for c in range(C)])
     assert abs(r_tuned - r_rule) <= 0.02 * r_rule
     api.pila_free(p)
+
+
+@pytest.mark.parametrize("K,prec", [(1, 0), (4, 0), (16, 0), (8, 1)])
+def test_bome_independent_lockstep(api, K, prec):
+    """BoME as Sec. III-B words it (each estimate its own random pixel):
+    every move against the oracle's independent-pixel reading, with the
+    disk reconstruction space and Gaussian noise."""
+    n, U = 48, 40
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, 8, 1005) * mask
+    pm = synth.gaussian_noise(oracle.drt(ph, U, B), 0.01, 2005)
+    img0 = synth.initial_image(n, 0.5, mask)
+    p = api.pila_build(n, U, B, prec, mask=mask)
+    S, M = 3, 1500
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=K, t0=2e-3, tn=2e-5, seed=3005, moves_per_sweep=M,
+                              flags=api.SAT_FLAG_BOME_INDEPENDENT)
+    assert st["status"] == 0 and st["proposed"] == S * M
+    if K > 1:
+        assert np.mean(tr["cstar"] > 0) > 0.3  # estimates other than the first are chosen
+    if prec == 0:
+        _, rep = oracle.sat_lockstep(pm, img0, tr, t0=2e-3, tn=2e-5, bome_k=K, n_sweeps=S, seed=3005,
+                                     moves_per_sweep=M, mask=mask, bome_mode=oracle.BOME_INDEPENDENT)
+        assert rep["moves"] == S * M
+        assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+        assert rep["max_err_dS"] <= 1e-5, rep
+        assert rep["near_ties"] <= 1e-3 * S * M, rep
+    assert st["max_resync_drift"] <= 1e-4 * np.max(np.abs(pm))
+    api.pila_free(p)
+
+
+def test_bome_independent_batched_equals_single(api):
+    n, U = 40, 30
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    sinos = np.stack([oracle.drt(synth.phantom(n, 6, 160 + i), U, B) for i in range(5)]).astype(np.float32)
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * 5).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    kw = dict(bome_k=8, n_sweeps=4, t0=-1.0, tn=-1.0, resync_every=2, flags=api.SAT_FLAG_BOME_INDEPENDENT)
+    imgs = dev(img0)
+    st = api.sat_run(p, dev(sinos), imgs, seed=31, **kw)
+    out = imgs.cpu().numpy()
+    for c in (0, 4):
+        one = dev(img0[c:c + 1])
+        s1 = api.sat_run(p, dev(sinos[c:c + 1]), one, seed=31 + c, **kw)
+        assert np.array_equal(one.cpu().numpy()[0], out[c]) and s1[0]["accepted"] == st[c]["accepted"]
+    api.pila_free(p)
