@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     ap.add_argument("--flags", type=int, default=0, help="SAT_FLAG_* bits for the batched run")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve"],
-                    help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome"],
+                    help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
+                         "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C)")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     return ap.parse_args()
 
@@ -475,12 +476,73 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def nrmse(img, ref):
+    """Root mean square of (img - ref) divided by the mean of ref (Sec. III-B)."""
+    d = np.asarray(img, np.float64) - np.asarray(ref, np.float64)
+    return float(np.sqrt(np.mean(d * d)) / np.mean(ref))
+
+
+def run_bome(args):
+    """The experiments of Sec. III-B and III-C on synthetic phantoms: final
+    NRMSE against N_e (both readings of BoME), N_e = 1 with the evaluations of
+    N_e = 4 spread over more stages or moves, and the three cooling
+    schedules at N_e = 1 and 16.  64x64 slices (10 random ellipses, the disk
+    reconstruction space), 60 angles, beta = 0.9, T0 by Eq. (8), T_N = T0/1000;
+    each configuration runs C chains (C phantoms) in one launch."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    n, U, C = 64, 60, args.slices or 16
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    N, M = (args.sweeps or 200), 2000
+    ph = np.stack([synth.phantom(n, 10, synth.slice_seeds(i)[0]) * mask for i in range(C)])
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    sino = api.pila_forward(p, torch.tensor(ph, dtype=torch.float32, device="cuda")).float().contiguous()
+    init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * C), dtype=torch.float32, device="cuda")
+
+    def run(K, flags=0, sweeps=N, moves=M, schedule=api.SAT_SCHED_LINEAR):
+        imgs = init.clone()
+        t = time.perf_counter()
+        st = api.sat_run(p, sino, imgs, bome_k=K, n_sweeps=sweeps, moves_per_sweep=moves, beta=0.9, t0=-1.0,
+                         tn=-1.0, schedule=schedule, seed=synth.slice_seeds(0)[2], resync_every=max(1, sweeps // 10),
+                         flags=flags)
+        dt = time.perf_counter() - t
+        out = imgs.cpu().numpy()
+        return {"nrmse": float(np.mean([nrmse(out[i], ph[i]) for i in range(C)])),
+                "moves_per_s": C * sweeps * moves / dt, "cost": float(np.mean([x["final_cost"] for x in st]))}
+
+    ks = [1, 2, 4, 8, 16, 32]
+    vs_k = {"independent": {k: run(k, api.SAT_FLAG_BOME_INDEPENDENT) for k in ks},
+            "one_pixel": {k: run(k) for k in ks}}
+    equal_eval = {f"N={N * f}, M={M * 4 // f}": run(1, 0, N * f, M * 4 // f) for f in (1, 2, 4)}
+    scheds = {}
+    for k in (1, 16):
+        for name, sc in (("linear", api.SAT_SCHED_LINEAR), ("geometric", api.SAT_SCHED_GEOMETRIC),
+                         ("cubic", api.SAT_SCHED_CUBIC)):
+            scheds[f"N_e={k} {name}"] = run(k, api.SAT_FLAG_BOME_INDEPENDENT, schedule=sc)
+    api.pila_free(p)
+    out = {"metric": "final NRMSE (mean over slices)", "unit": "nrmse", "higher_is_better": False,
+           "data": "synthetic",
+           "config": {"workload": "bome", "n": n, "angles": U, "bins": B, "slices": C, "stages": N,
+                      "moves_per_stage": M, "beta": 0.9, "pila": "f32"},
+           "vs_estimates": vs_k, "equal_evaluations_Ne1": equal_eval,
+           "equal_evaluations_Ne4": vs_k["independent"][4], "schedules": scheds}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.workload == "precision512":
         return run_precision(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "bome":
+        return run_bome(args)
     cfg = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
