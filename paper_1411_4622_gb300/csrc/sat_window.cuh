@@ -1,5 +1,6 @@
 // Windowed form of the annealing move for one warp per chain, with the
 // residual in shared memory or in global memory (identical arithmetic).
+// Windows of kWin = 2 moves; the notes below hold for any kWin dividing 4.
 //
 // Moves are still decided one after the other, each on the exact state left
 // by all earlier moves; what changes is how that state is read.  For a window
@@ -19,7 +20,7 @@
 
 namespace satpila {
 
-constexpr int kWin = 4;
+constexpr int kWin = 2;  // measured best: 2 beat 4 (fewer pair terms, less live state) and 1 (no batching)
 constexpr int kPairs = kWin * (kWin - 1) / 2;
 
 // For slot s, the lengths that move i (records ki, a0, a1) puts on the two
@@ -77,8 +78,6 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         pw_prev[j] = -1;
         fw_prev[j] = 0.0f;
     }
-    float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
-
     for (int w = 0; w < nwin; ++w) {
         const int m0 = w * kWin;
         __syncwarp();
@@ -185,8 +184,12 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                 if (i < j) f = pc[i] == pc[j] ? fnew[i] : f;
             const uint32_t* drw = G.draws + (m % kDrawRing) * kWords;
             const float L = __uint_as_float(drw[1]);
+            // Step 4 as x < T L (2 C + T L) with x = dS / (B U), C = sqrt(S / (B U)),
+            // squared so that no square root sits on the chain:
+            // x <= 0, or x - (T L)^2 < 0, or (x - (T L)^2)^2 < 4 (T L)^2 S / (B U).
             const float TL = x.T * L;
-            const float theta = TL * fmaf(2.0f, C, TL);
+            const float TL2 = TL * TL;
+            const float rhs = 4.0f * TL2 * fmaxf(0.0f, S_hi * a.inv_BU);
             const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
             const float g2 = 2.0f * g;
             float dS[KMAX], fcand[KMAX];
@@ -209,10 +212,12 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                 }
             }
             const float xs = dS[0] * a.inv_BU;
-            const bool accept = live && (xs <= 0.0f || xs < theta);
+            const float xm = xs - TL2;
+            const bool accept = live && (xs <= 0.0f || xm < 0.0f || xm * xm < rhs);
             df[j] = accept ? fcand[0] - f : 0.0f;
             fnew[j] = accept ? fcand[0] : f;
             if (x.tracing && live && x.lane == 0) {
+                const float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
                 const float Cp = sqrtf(fmaxf(0.0f, fmaf(C, C, xs)));
                 const float den = Cp + C;
                 const long long idx = (long long)x.s * M + m;
@@ -233,8 +238,6 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             const float t = S_hi + y;
             S_lo = (t - S_hi) - y;
             S_hi = t;
-            const float C2 = fmaxf(0.0f, S_hi * a.inv_BU);
-            C = accept ? (C2 > 0.0f ? C2 * rsqrtf(C2) : 0.0f) : C;
             n_acc += accept ? 1ull : 0ull;
         }
 
