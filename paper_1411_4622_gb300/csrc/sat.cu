@@ -372,7 +372,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
 namespace {
 
 struct BatchLayout {
-    size_t resid, S, T0, TN, found, acc, prog, err, psq, pdr, dmax, c0, cF, Sinc, bytes;
+    size_t resid, S, T0, TN, found, acc, prog, claim, err, psq, pdr, dmax, c0, cF, Sinc, bytes;
 };
 
 BatchLayout batch_layout(const Plan& pl, long long cap) {
@@ -391,6 +391,7 @@ BatchLayout batch_layout(const Plan& pl, long long cap) {
     L.found = carve(n * 4);
     L.acc = carve(n * 8);
     L.prog = carve(n * 4);
+    L.claim = carve(n * 4);
     L.err = carve(4);
     L.psq = carve(n * G * 8);
     L.pdr = carve(n * G * 4);
@@ -416,6 +417,7 @@ void batch_carve(void* base, const Plan& pl, long long cap, BatchDev* b) {
     b->found = (int*)(c + L.found);
     b->accepted = (unsigned long long*)(c + L.acc);
     b->progress = (int*)(c + L.prog);
+    b->claim = (int*)(c + L.claim);
     b->error = (int*)(c + L.err);
     b->part_sq = (double*)(c + L.psq);
     b->part_drift = (float*)(c + L.pdr);
@@ -557,6 +559,8 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.trace_chain = b.trace_chain;
     sa.trace_cap = b.trace_cap;
     sa.ctl = b.ctl;
+    // ready-first scheduling where warps of different speed share the chains
+    sa.claim = pl.kind == 2 ? b.claim : nullptr;
     sa.sweep_begin = s_begin;
     sa.sweep_end = s_end;
     sa.sweeps_per_task = pl.spt;

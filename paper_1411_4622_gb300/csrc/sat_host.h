@@ -55,6 +55,7 @@ struct BatchDev {
     int* found = nullptr;          // uphill samples found by Eq. (8)
     unsigned long long* accepted = nullptr;
     int* progress = nullptr;       // per chain: stages done in the current sweep launch
+    int* claim = nullptr;          // per chain: 1 while a warp runs it (ready-first scheduling)
     int* error = nullptr;          // [1]
     double* part_sq = nullptr;     // [n][proj_G]
     float* part_drift = nullptr;   // [n][proj_G]

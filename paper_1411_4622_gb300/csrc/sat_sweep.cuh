@@ -87,6 +87,7 @@ struct SatArgs {
     int trace_chain;
     long long trace_cap;
     const ChainCtl* ctl;         // [n_chains] or NULL
+    int* claim;                  // windowed kernels: [n_chains] 1 while a warp runs the chain, or NULL
 };
 
 constexpr int kSatMaxWarps = 8;

@@ -159,6 +159,29 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 
         // ---- decisions, in move order ----
         float df[kWin], fnew[kWin];
+        // Candidates from the values before this window's decisions; a move
+        // whose pixel an earlier move of the window also drew recomputes them
+        // after that move (a warp-uniform, rare branch).
+        bool rep[kWin];
+        float fpre[kWin], fcp[kWin][KMAX], dpre[kWin][KMAX];
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            float f = fc0[j];
+#pragma unroll
+            for (int i = 0; i < kWin; ++i) f = pw_prev[i] == pc[j] ? fw_prev[i] : f;
+            fpre[j] = f;
+            rep[j] = false;
+#pragma unroll
+            for (int i = 0; i < kWin; ++i)
+                if (i < j) rep[j] = rep[j] || pc[i] == pc[j];
+            const uint32_t* drw = G.draws + ((m0 + j) % kDrawRing) * kWords;
+            const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
+#pragma unroll
+            for (int e = 0; e < KMAX; ++e) {
+                fcp[j][e] = fmaf(__uint_as_float(drw[2 + e]), span, lo);
+                dpre[j][e] = fcp[j][e] - f;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
             const int m = m0 + j;
@@ -174,15 +197,25 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                         ++e;
                     }
             }
-            // current value of the pixel: latest earlier write in this window,
-            // else in the previous window, else the loaded value
-            float f = fc0[j];
-#pragma unroll
-            for (int i = 0; i < kWin; ++i) f = pw_prev[i] == pc[j] ? fw_prev[i] : f;
-#pragma unroll
-            for (int i = 0; i < kWin; ++i)
-                if (i < j) f = pc[i] == pc[j] ? fnew[i] : f;
             const uint32_t* drw = G.draws + (m % kDrawRing) * kWords;
+            float f = fpre[j];
+            float fcand[KMAX], dd[KMAX];
+#pragma unroll
+            for (int e = 0; e < KMAX; ++e) {
+                fcand[e] = fcp[j][e];
+                dd[e] = dpre[j][e];
+            }
+            if (rep[j]) {
+#pragma unroll
+                for (int i = 0; i < kWin; ++i)
+                    if (i < j) f = pc[i] == pc[j] ? fnew[i] : f;
+                const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
+#pragma unroll
+                for (int e = 0; e < KMAX; ++e) {
+                    fcand[e] = fmaf(__uint_as_float(drw[2 + e]), span, lo);
+                    dd[e] = fcand[e] - f;
+                }
+            }
             const float L = __uint_as_float(drw[1]);
             // Step 4 as x < T L (2 C + T L) with x = dS / (B U), C = sqrt(S / (B U)),
             // squared so that no square root sits on the chain:
@@ -190,14 +223,12 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             const float TL = x.T * L;
             const float TL2 = TL * TL;
             const float rhs = 4.0f * TL2 * fmaxf(0.0f, S_hi * a.inv_BU);
-            const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
             const float g2 = 2.0f * g;
-            float dS[KMAX], fcand[KMAX];
+            float dS[KMAX];
             int ci[KMAX];
 #pragma unroll
             for (int e = 0; e < KMAX; ++e) {
-                fcand[e] = fmaf(__uint_as_float(drw[2 + e]), span, lo);
-                const float d = fcand[e] - f;
+                const float d = dd[e];
                 dS[e] = e < a.K ? d * fmaf(d, hc[j], g2) : __int_as_float(0x7f800000);
                 ci[e] = e;
             }
@@ -322,24 +353,73 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     }
 
     uint32_t phase = 0;
+    // Ready-first scheduling (a.claim set): a warp takes the next stages of
+    // any chain that is neither running nor finished, so no warp waits on a
+    // chain another warp is still running (warps of different speed share
+    // the chains).  Otherwise tasks come in (stage block, chain) order from a
+    // counter and a task waits for its chain's earlier stages.
+    int scan = (int)(((unsigned)blockIdx.x * 8u + (unsigned)warp) * 37u % (unsigned)max(1, a.n_chains));
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.task_counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= a.n_tasks) break;
-        const int c = t % a.n_chains;
-        const int blk = t / a.n_chains;
-        const int s0 = a.sweep_begin + blk * a.sweeps_per_task;
-        const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
-        if (blk > 0) {
-            int ok = 1;
-            if (lane == 0) ok = wait_progress(&a.progress[c], s0) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
-                break;
+        int c = -1, s0 = 0;
+        if (a.claim) {
+            const unsigned long long t_start = global_ns();
+            for (;;) {
+                int got = -1;
+                for (int base = 0; base < a.n_chains && got < 0; base += 32) {
+                    const int q = scan + base + lane;
+                    const int cq = q % a.n_chains;
+                    const bool ready = base + lane < a.n_chains && ld_acquire(&a.claim[cq]) == 0 &&
+                                       ld_acquire(&a.progress[cq]) < a.sweep_end;
+                    unsigned m = __ballot_sync(0xffffffffu, ready);
+                    while (m && got < 0) {
+                        const int l = __ffs(m) - 1;
+                        m &= m - 1;
+                        int won = 0;
+                        if (lane == l) won = atomicCAS(&a.claim[cq], 0, 1) == 0 ? 1 : 0;
+                        won = __shfl_sync(0xffffffffu, won, l);
+                        if (won) got = __shfl_sync(0xffffffffu, cq, l);
+                    }
+                }
+                if (got >= 0) {
+                    c = got;
+                    scan = (got + 1) % a.n_chains;
+                    break;
+                }
+                int all_done = 0;
+                if (lane == 0) all_done = ld_acquire(a.task_counter) >= a.n_chains ? 1 : 0;
+                if (__shfl_sync(0xffffffffu, all_done, 0)) break;
+                if (global_ns() - t_start > 20000000000ull) {
+                    if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(512);
+            }
+            if (c < 0) break;
+            if (lane == 0) s0 = ld_acquire(&a.progress[c]);
+            s0 = __shfl_sync(0xffffffffu, s0, 0);
+            if (s0 >= a.sweep_end) {  // finished meanwhile: hand it back
+                if (lane == 0) st_release(&a.claim[c], 0);
+                continue;
+            }
+        } else {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(a.task_counter, 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= a.n_tasks) break;
+            c = t % a.n_chains;
+            const int blk = t / a.n_chains;
+            s0 = a.sweep_begin + blk * a.sweeps_per_task;
+            if (blk > 0) {
+                int ok = 1;
+                if (lane == 0) ok = wait_progress(&a.progress[c], s0) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                    break;
+                }
             }
         }
+        const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
         float* gres = a.resid + (long long)c * a.resid_floats;
         if (SMEM) {
             // The band of every residual row into shared memory, one bulk copy
@@ -405,7 +485,13 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release(&a.progress[c], s1);
+        if (lane == 0) {
+            st_release(&a.progress[c], s1);
+            if (a.claim) {
+                if (s1 >= a.sweep_end) atomicAdd(a.task_counter, 1);  // chains finished in this launch
+                st_release(&a.claim[c], 0);
+            }
+        }
     }
 }
 
