@@ -16,7 +16,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["geometry.cpp", "sat.cpp", "sirt.cpp"]
+_SOURCES = ["geometry.cpp", "sat.cpp", "sirt.cpp", "drt_bilinear.cpp"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -156,6 +156,35 @@ def drt(image, n_angles, n_bins, angles=None):
     if _load().or_drt(C.byref(g), _ptr(img), _ptr(out)) != 0:
         raise RuntimeError("drt failed")
     return out
+
+
+def drt_bilinear(image, n_angles, n_bins, angles=None):
+    """The conventional DRT (bilinear interpolation, unit steps) -> [U, B]."""
+    img = _f64(image)
+    n = img.shape[0]
+    g, keep = _geom(n, n_angles, n_bins, angles)
+    out = np.zeros((n_angles, n_bins), dtype=np.float64)
+    if _load().or_drt_bilinear(C.byref(g), _ptr(img), _ptr(out)) != 0:
+        raise RuntimeError("drt_bilinear failed")
+    return out
+
+
+def sat_drt_run(pm, image, *, t0, tn=-1.0, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0,
+                schedule=SCHED_LINEAR, seed=0, mask=None, angles=None, trace=False):
+    """SAT with a full bilinear DRT per estimate (Sec. III-A's baseline)."""
+    pm_ = _f64(pm)
+    img = _f64(image).copy()
+    n = img.shape[0]
+    g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
+    m = _mask(mask, n)
+    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, 200, seed)
+    moves = moves_per_sweep if moves_per_sweep > 0 else (int(m.sum()) if m is not None else n * n)
+    tr = np.zeros(n_sweeps * moves, dtype=TRACE_DTYPE) if trace else None
+    st = SatStats()
+    rc = _load().or_sat_drt_run(C.byref(g), _ptr(m), _ptr(pm_), _ptr(img), C.byref(prm), C.byref(st), _ptr(tr))
+    if rc != 0:
+        raise RuntimeError(f"sat_drt_run failed ({rc})")
+    return img, {f: getattr(st, f) for f, _ in SatStats._fields_}, tr
 
 
 def pila(n, n_angles, n_bins, angles=None):

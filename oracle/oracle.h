@@ -44,6 +44,11 @@ int or_siddon_ray(int32_t n, double theta, double s, int32_t* pix, double* len, 
  * by ray (u, k) of image[p] * l.  Ray-driven, by Siddon traversal. */
 int or_drt(const or_geom* g, const double* image, double* sino);
 
+/* The conventional forward model of Sec. III-A: a DRT by bilinear
+ * interpolation, each ray sampled at B unit steps t_m = m - (B-1)/2 along its
+ * direction (see drt_bilinear.cpp). */
+int or_drt_bilinear(const or_geom* g, const double* image, double* sino);
+
 /* PILA, Eq. (5), built by transposing the Siddon traversals of every ray.
  * Up to two entries per (pixel, angle), sorted by bin:
  *   bins[(p*U + u)*2 + s], lens[(p*U + u)*2 + s]; an empty slot has len 0
@@ -108,6 +113,12 @@ double or_schedule_temp(int32_t schedule, double t0, double tn, int32_t s, int32
  * n_sweeps*moves records.  Returns 0 or a negative error. */
 int or_sat_run(const or_geom* g, const uint8_t* mask, const double* pm, double* image,
                const or_sat_params* prm, or_sat_stats* stats, or_trace_rec* trace);
+
+/* SAT without the PILA (Sec. III-A's baseline): every estimate evaluated by a
+ * full bilinear DRT of the candidate image; same random stream as or_sat_run;
+ * prm->t0 must be given (> 0). */
+int or_sat_drt_run(const or_geom* g, const uint8_t* mask, const double* pm, double* image,
+                   const or_sat_params* prm, or_sat_stats* stats, or_trace_rec* trace);
 
 typedef struct {
     int32_t pixel, cstar, accepted, pad;

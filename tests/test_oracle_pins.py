@@ -423,3 +423,66 @@ def test_sirt_single_update_by_hand(orc):
     pm = orc.drt(np.full((1, 1), 0.7), U, B)
     img, costs = orc.sirt_run(pm, np.zeros((1, 1)), 1, mode=0)
     assert abs(img[0, 0] - 0.7) < 1e-14 and costs[0] < 1e-14
+
+
+def test_bilinear_drt_against_scipy_interpolation(orc):
+    """The conventional forward model of Sec. III-A: every ray is the sum of B
+    unit-step samples of the bilinear interpolant.  Checked against scipy's
+    linear interpolation (zero beyond the grid) at the same sample points."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(3)
+    for n, U in ((9, 7), (16, 12)):
+        B = synth.bins_for(n)
+        img = rng.random((n, n))
+        got = orc.drt_bilinear(img, U, B)
+        ks = np.arange(B) - 0.5 * (B - 1)
+        ts = np.arange(B) - 0.5 * (B - 1)
+        for u in range(U):
+            th = np.pi * u / U
+            c, s = np.cos(th), np.sin(th)
+            c = 0.0 if abs(c) < 1e-12 else c
+            s = 0.0 if abs(s) < 1e-12 else s
+            x = ks[:, None] * c - ts[None, :] * s
+            y = ks[:, None] * s + ts[None, :] * c
+            rows, cols = 0.5 * (n - 1) - y, x + 0.5 * (n - 1)
+            vals = ndimage.map_coordinates(img, [rows.ravel(), cols.ravel()], order=1, mode="grid-constant", cval=0.0)
+            np.testing.assert_allclose(got[u], vals.reshape(B, B).sum(axis=1), rtol=1e-12, atol=1e-12)
+
+
+def test_sat_with_full_drt_against_recomputation(orc):
+    """SAT without the PILA: each move's dC is C' - C of a fresh bilinear DRT,
+    the best of the estimates is kept, and the chain follows Step 4."""
+    n, U, K, seed = 8, 7, 3, 21
+    B = synth.bins_for(n)
+    ph = synth.phantom(n, 3, 5)
+    pm = orc.drt_bilinear(ph, U, B)
+    img0 = np.full((n, n), 0.5)
+    M = 30
+    img, st, tr = orc.sat_drt_run(pm, img0, t0=1e-3, tn=1e-5, bome_k=K, n_sweeps=2, moves_per_sweep=M, seed=seed,
+                                  trace=True)
+    cur = img0.copy()
+    cost = lambda im: float(np.sqrt(np.mean((orc.drt_bilinear(im, U, B) - pm) ** 2)))
+    nblk = (K + 2 + 3) // 4
+    for idx, rec in enumerate(tr):
+        s, m = divmod(idx, M)
+        w = _draw(orc, seed, s, m, 1, nblk)
+        p = (w[0] * n * n) >> 32
+        assert rec["pixel"] == p
+        f = cur.flat[p]
+        lo, hi = max(0.0, f - 1.0), min(1.0, f + 1.0)
+        vals = [lo + _u01(w[2 + e]) * (hi - lo) for e in range(K)]
+        costs = []
+        for v in vals:
+            t = cur.copy()
+            t.flat[p] = v
+            costs.append(cost(t))
+        best = int(np.argmin(costs))
+        assert rec["cstar"] == best
+        assert abs(rec["dC"] - (costs[best] - cost(cur))) < 1e-12
+        T = orc.schedule_temp(orc.SCHED_LINEAR, 1e-3, 1e-5, s, 2)
+        dC = rec["dC"]
+        assert bool(rec["accepted"]) == (dC <= 0 or _u01(w[1]) < np.exp(-dC / T))
+        if rec["accepted"]:
+            cur.flat[p] = vals[best]
+    assert np.allclose(cur, img, atol=1e-15)
+    assert abs(st["final_cost"] - st["final_cost_fresh"]) < 1e-12
