@@ -303,6 +303,37 @@ int sat_server_info(satpila_server* s, sat_server_stats* out);
 int sat_server_destroy(satpila_server* s);
 
 /* ------------------------------------------------------------------------ */
+/* The conventional SAT that the PILA replaces (Sec. III-A, Fig. 3): a full   */
+/* DRT by bilinear interpolation for every estimate.  A speed baseline.       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Bilinear-interpolation DRT of n_items images ([n][n] each, device memory)
+ * into sino ([n_items][n_angles][n_bins], device memory).  Ray (u, k) is the
+ * line x cos + y sin = s_k, sampled at n_bins unit steps
+ * t_m = m - (n_bins - 1)/2 along (-sin, cos); each sample interpolates
+ * bilinearly between pixel centres (zero outside); angles_rad (host, may be
+ * NULL: u pi / n_angles).  Synchronizes `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+int drt_bilinear(int32_t n, int32_t n_angles, int32_t n_bins, const double* angles_rad, int32_t n_items,
+                 const float* images, float* sino, void* stream);
+
+/*
+ * SAT without the PILA: Steps 1-4 with the random stream of sat_run (key
+ * seed + c, draw 0 the pixel of the mask list (host mask, NULL: all pixels),
+ * draw 1 N1, draw 2 + e estimate e), each estimate evaluated by a full
+ * bilinear DRT of the candidate image and Eq. (4), the best kept, Step 4 with
+ * the exponential.  One CTA per chain.  sino_meas [n_chains][U][B] and images
+ * [n_chains][n][n] are device memory (images annealed in place); prm->t0 must
+ * be > 0 (no Eq. (8)); resync, residency, flags, group_warps and
+ * pipeline_depth are ignored; trace (device) records trace_chain's moves
+ * with dS = S' - S.  stats: final_cost, accepted, proposed, sweep_ms (the
+ * kernel's time).  Synchronizes `stream`.
+ */
+int sat_drt_run(int32_t n, int32_t n_angles, int32_t n_bins, const uint8_t* mask, int32_t n_chains,
+                const float* sino_meas, float* images, const sat_params* prm, sat_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* SIRT with PILA: Eqs. (10)-(11), Sec. III-D.                                */
 /* ------------------------------------------------------------------------ */
 

@@ -162,6 +162,33 @@ def sat_run(p: Pila, sino_meas, images, stream=None, **kw) -> list[dict]:
     return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
 
 
+def drt_bilinear(images, n_angles, n_bins, stream=None):
+    """Bilinear-interpolation DRT (Sec. III-A's conventional forward model) of
+    device images [items, n, n] -> float32 [items, U, B] tensor."""
+    import torch
+
+    n = int(images.shape[-1])
+    items = int(images.shape[0]) if images.ndim == 3 else 1
+    out = torch.empty((items, n_angles, n_bins), dtype=torch.float32, device=images.device)
+    L.check(L.load().drt_bilinear(n, n_angles, n_bins, None, items, _ptr(images, np.float32), _ptr(out, np.float32),
+                                  _stream(stream)))
+    return out
+
+
+def sat_drt_run(sino_meas, images, *, mask=None, stream=None, **kw) -> list[dict]:
+    """SAT with a full bilinear DRT per estimate (the baseline the PILA
+    replaces); device tensors; keyword arguments as sat_params (t0 > 0)."""
+    n_chains = int(images.shape[0]) if images.ndim == 3 else 1
+    n = int(images.shape[-1])
+    U, B = int(sino_meas.shape[-2]), int(sino_meas.shape[-1])
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    prm = sat_params(**kw)
+    stats = (L.SatStats * max(n_chains, 1))()
+    L.check(L.load().sat_drt_run(n, U, B, _ptr(m), n_chains, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
+                                 C.byref(prm), C.cast(stats, C.c_void_p), _stream(stream)))
+    return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
+
+
 class Server:
     """Continuous-batching annealing server (sat_server_* of include/satpila.h).
 

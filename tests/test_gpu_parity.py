@@ -533,3 +533,49 @@ def test_bome_independent_batched_equals_single(api):
         s1 = api.sat_run(p, dev(sinos[c:c + 1]), one, seed=31 + c, **kw)
         assert np.array_equal(one.cpu().numpy()[0], out[c]) and s1[0]["accepted"] == st[c]["accepted"]
     api.pila_free(p)
+
+
+@pytest.mark.parametrize("n,U", [(24, 18), (64, 90)])
+def test_drt_bilinear_vs_oracle(api, n, U):
+    """The conventional forward model (bilinear interpolation, unit steps) in
+    FP32 against the oracle's FP64."""
+    B = synth.bins_for(n)
+    rng = np.random.default_rng(n)
+    imgs = rng.random((3, n, n))
+    got = api.drt_bilinear(dev(imgs), U, B).cpu().numpy()
+    for i in range(3):
+        ref = oracle.drt_bilinear(imgs[i], U, B)
+        assert np.max(np.abs(got[i] - ref)) <= 2e-6 * B * max(1.0, np.max(np.abs(ref)))
+
+
+def test_sat_drt_follows_oracle(api):
+    """SAT with a full bilinear DRT per estimate: the GPU chain and the oracle
+    draw the same moves; their decisions agree (FP32 vs FP64 costs) until a
+    near-tie, and the costs agree to FP32 accuracy."""
+    n, U, K, S, M = 16, 12, 2, 2, 60
+    B = synth.bins_for(n)
+    ph = synth.phantom(n, 4, 33)
+    pm = oracle.drt_bilinear(ph, U, B)
+    img0 = np.full((n, n), 0.5)
+    kw = dict(t0=2e-3, tn=2e-5, bome_k=K, n_sweeps=S, moves_per_sweep=M, seed=44)
+    _, st_o, tr_o = oracle.sat_drt_run(pm, img0, trace=True, **kw)
+    trace = torch.zeros(S * M * 32, dtype=torch.uint8, device="cuda")
+    img = dev(img0).reshape(1, n, n)
+    st = api.sat_drt_run(dev(pm).reshape(1, U, B), img, trace=trace, trace_chain=0, **kw)[0]
+    tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
+    assert st["proposed"] == S * M
+    cref = st_o["initial_cost"]
+    first_diff = S * M
+    for i in range(S * M):
+        assert tr["pixel"][i] == tr_o["pixel"][i]
+        if tr["cstar"][i] != tr_o["cstar"][i] or tr["accepted"][i] != tr_o["accepted"][i]:
+            first_diff = i
+            break
+        assert abs(float(tr["dC"][i]) - tr_o["dC"][i]) <= 1e-4 * cref, i
+        assert abs(float(tr["fnew"][i]) - tr_o["fnew"][i]) <= 1e-6, i
+    if first_diff < S * M:  # only a near-tie may separate them
+        i = first_diff
+        T = oracle.schedule_temp(oracle.SCHED_LINEAR, 2e-3, 2e-5, i // M, S)
+        thr = -T * np.log(tr_o["u_acc"][i])
+        assert abs(tr_o["dC"][i] - thr) <= 1e-4 * cref or abs(tr_o["dC"][i]) <= 1e-4 * cref
+    assert first_diff >= 0.5 * S * M
