@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     ap.add_argument("--flags", type=int, default=0, help="SAT_FLAG_* bits for the batched run")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
-                         "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C)")
+                         "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
+                         "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A)")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     return ap.parse_args()
 
@@ -535,6 +536,77 @@ def run_bome(args):
     print(json.dumps(out))
 
 
+def run_drt(args):
+    """Sec. III-A's speed comparison (Fig. 3) on this GPU: SAT with the PILA
+    against SAT with a full bilinear-interpolation DRT per move, for 64, 128
+    and 256 pixel slices at 90, 180 and 360 angles, N = 1 stage of M = 200
+    moves, one estimate, T0 = 1e-3.  Both on the GPU, one chain and 152
+    chains (one CTA per SM for the DRT form); and both single-threaded on
+    the host (the oracle), the paper's own setting, on a subset."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+    import oracle
+
+    libbuild.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    M = 200
+    kw = dict(bome_k=1, n_sweeps=1, moves_per_sweep=M, t0=1e-3, tn=1e-6, seed=777)
+    rows = []
+    for n in (64, 128, 256):
+        B = synth.bins_for(n)
+        mask = synth.disk_mask(n)
+        ph = synth.phantom(n, 10, synth.slice_seeds(0)[0]) * mask
+        for U in (90, 180, 360):
+            pm = oracle.drt(ph, U, B) if n <= 128 else None
+            pf = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+            pm_d = api.pila_forward(pf, torch.tensor(ph[None], dtype=torch.float32, device="cuda")).float()
+            api.pila_free(pf)
+            row = {"n": n, "angles": U}
+            for C in (1, 152):
+                sino = pm_d.expand(C, U, B).contiguous()
+                init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * C), dtype=torch.float32,
+                                    device="cuda")
+                p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+                img = init.clone()
+                api.sat_run(p, sino, img, **kw)
+                img = init.clone()
+                st = api.sat_run(p, sino, img, **kw)
+                pila_rate = C * M / (st[0]["sweep_ms"] / 1e3)
+                api.pila_free(p)
+                img = init.clone()
+                st = api.sat_drt_run(sino, img, mask=mask, **kw)
+                drt_rate = C * M / (st[0]["sweep_ms"] / 1e3)
+                row[f"gpu_chains{C}"] = {"pila_moves_per_s": pila_rate, "drt_moves_per_s": drt_rate,
+                                         "speedup": pila_rate / drt_rate}
+            if pm is not None and U == 90:
+                # the paper's setting: one CPU thread, both forms
+                # per-move time as the difference of two run lengths (the setup cancels)
+                def per_move(fn, m1, m2):
+                    ts = []
+                    for mm in (m1, m2):
+                        t = time.perf_counter()
+                        fn(pm, synth.initial_image(n, 0.5, mask), t0=1e-3, tn=1e-6, n_sweeps=1, moves_per_sweep=mm,
+                           seed=777, mask=mask)
+                        ts.append(time.perf_counter() - t)
+                    return (ts[1] - ts[0]) / (m2 - m1)
+
+                m_drt = (10, 30) if n == 128 else (20, 80)
+                t_drt = per_move(oracle.sat_drt_run, *m_drt)
+                t_pila = per_move(oracle.sat_run, 2000, 42000)
+                row["cpu_one_thread"] = {"pila_s_per_move": t_pila, "drt_s_per_move": t_drt,
+                                         "speedup": t_drt / t_pila, "note": "oracle FP64, single thread"}
+            rows.append(row)
+    out = {"metric": "SAT moves/s with the PILA over SAT with a full DRT per move", "unit": "ratio",
+           "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "drt", "moves": M, "stages": 1, "bome_k": 1, "pila": "f32",
+                      "drt": "bilinear interpolation, B unit steps per ray"},
+           "rows": rows}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.workload == "precision512":
@@ -543,6 +615,8 @@ def main():
         return run_serve(args)
     if args.workload == "bome":
         return run_bome(args)
+    if args.workload == "drt":
+        return run_drt(args)
     cfg = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
