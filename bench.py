@@ -55,6 +55,8 @@ def parse():
                          "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
                          "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A)")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
+                    help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
     return ap.parse_args()
 
 
@@ -654,9 +656,11 @@ def main():
     stream = torch.cuda.current_stream()
     info = {}
 
+    prec = {"f16": api.PILA_F16, "u8": api.PILA_U8, "f32": api.PILA_F32}[args.pila]
+
     def step():
         images.copy_(init)
-        p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+        p = api.pila_build(n, U, B, prec, mask=mask)
         st = api.sat_run(p, sino, images, **run_kw)
         if not info:
             info.update(api.pila_info(p))
@@ -702,7 +706,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+        p = api.pila_build(n, U, B, prec, mask=mask)
         api.sat_run(p, sino_h, work, **run_kw)
         api.pila_free(p)
         if it > 0:
@@ -728,7 +732,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "slices_per_gpu": slices, "n": n, "angles": U, "bins": B,
-                      "bome_k": K, "stages": S, "moves_per_stage": M, "pila": "f16",
+                      "bome_k": K, "stages": S, "moves_per_stage": M, "pila": args.pila,
                       "l2": "flushed between timed steps (256 MB write)"},
            "evaluations_per_s": value * K, "acceptance": acc,
            "rmse": {"batched_mean": float(rmse_batched.mean())}, "plain": plain,

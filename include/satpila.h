@@ -57,13 +57,16 @@ int satpila_version(void);
 
 #define PILA_F32 0 /* record: int32 bin0, int32 bin1, float len0, float len1 (16 B) */
 #define PILA_F16 1 /* record: int16 bin0, int16 bin1, half len0, half len1 (8 B)    */
+#define PILA_U8 2  /* record: uint16 bin0, uint8 180*len0, uint8 180*len1 (4 B): the
+                      one-byte lengths of Sec. II-B (length = q * fl(1/180)); entry 1
+                      sits on bin0 + 1.  Read by the windowed kernel (<= 128 angles) */
 
 typedef struct satpila_pila satpila_pila;
 
 typedef struct {
     int32_t n;                /* image side, >= 1 */
     int32_t n_angles;         /* U, >= 1 */
-    int32_t n_bins;           /* B, >= 1 (<= 32767 for PILA_F16) */
+    int32_t n_bins;           /* B, >= 1 (<= 32767 for PILA_F16 and PILA_U8) */
     const double* angles_rad; /* host, U angles; NULL: theta_u = pi*u/U */
     const uint8_t* mask;      /* host, n*n reconstruction space (Sec. III, Fig. 2(c));
                                  NULL: every pixel.  Moves pick pixels from it and
@@ -246,7 +249,7 @@ typedef struct {
 
 typedef struct {
     int32_t n, n_angles, n_bins; /* geometry, as pila_geom */
-    int32_t precision;           /* PILA_F32 or PILA_F16 */
+    int32_t precision;           /* PILA_F32, PILA_F16 or PILA_U8 */
     const double* angles_rad;    /* [n_angles] or NULL (u * pi / U) */
     const uint8_t* mask;         /* [n][n] reconstruction space or NULL (all pixels) */
     const float* sino;           /* [n_angles][n_bins] measured sinogram P_m */

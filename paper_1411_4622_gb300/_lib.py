@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libsatpila.so")
 OK = 0
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS, ERR_BUSY, ERR_NOT_FOUND, ERR_PENDING = (
     -1, -2, -3, -4, -5, -6, -7, -8)
-PILA_F32, PILA_F16 = 0, 1
+PILA_F32, PILA_F16, PILA_U8 = 0, 1, 2
 SAT_SCHED_LINEAR, SAT_SCHED_GEOMETRIC, SAT_SCHED_CUBIC = 0, 1, 2
 SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
 SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID, SAT_FLAG_BOME_INDEPENDENT = 1, 2, 4, 8

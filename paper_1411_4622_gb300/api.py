@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib as L
-from ._lib import (PILA_F16, PILA_F32, SAT_FLAG_AUTOTUNE, SAT_FLAG_BOME_INDEPENDENT, SAT_FLAG_HYBRID,  # noqa: F401
+from ._lib import (PILA_F16, PILA_F32, PILA_U8, SAT_FLAG_AUTOTUNE, SAT_FLAG_BOME_INDEPENDENT, SAT_FLAG_HYBRID,  # noqa: F401
                    SAT_FLAG_NO_GRAPH,
                    SAT_RESIDENT_AUTO,
                    SAT_RESIDENT_GLOBAL, SAT_RESIDENT_SMEM, SAT_SCHED_CUBIC, SAT_SCHED_GEOMETRIC,

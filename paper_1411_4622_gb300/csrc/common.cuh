@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "satpila.h"
+
 namespace satpila {
 
 constexpr uint32_t kStreamSat = 1u;  // Philox stream id of the annealing moves
@@ -141,6 +143,31 @@ __device__ __forceinline__ Entry2 decode_f16(uint32_t bins, uint32_t lens) {
     e.l0 = __half2float(__ushort_as_half((unsigned short)(lens & 0xffffu)));
     e.l1 = __half2float(__ushort_as_half((unsigned short)(lens >> 16)));
     return e;
+}
+
+// Record of the one-byte table (the storage Sec. II-B describes): bits 0-15
+// the bin of entry 0 (entry 1, when present, sits on the next bin), bits
+// 16-23 and 24-31 the two lengths times 180, rounded.  A stored length is
+// q * fl(1/180), the same value wherever the table is read.
+constexpr float kU8Unit = 1.0f / 180.0f;
+
+__device__ __forceinline__ Entry2 decode_u8(uint32_t v) {
+    Entry2 e;
+    e.k0 = (int)(v & 0xffffu);
+    e.l0 = (float)((v >> 16) & 0xffu) * kU8Unit;
+    e.l1 = (float)(v >> 24) * kU8Unit;
+    e.k1 = e.l1 != 0.0f ? e.k0 + 1 : e.k0;
+    return e;
+}
+
+// Record rec of a table of precision prec (PILA_F32, PILA_F16, PILA_U8).
+__device__ __forceinline__ Entry2 decode_rec(const unsigned char* table, long long rec, int prec) {
+    if (prec == PILA_F16) {
+        const uint2 v = reinterpret_cast<const uint2*>(table)[rec];
+        return decode_f16(v.x, v.y);
+    }
+    if (prec == PILA_U8) return decode_u8(reinterpret_cast<const uint32_t*>(table)[rec]);
+    return decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
 }
 
 // ---- exact fixed-point accumulation ------------------------------------------

@@ -59,7 +59,7 @@ enum ProjMode { PROJ_FORWARD = 0, PROJ_RESYNC = 1, PROJ_FACTOR = 2, PROJ_SIRT = 
 
 struct ProjArgs {
     const unsigned char* table;
-    int f16;
+    int f16;                    // table precision (PILA_F32, PILA_F16, PILA_U8)
     int row_records;
     int n, U, B;
     int angles_per_group, n_groups;

@@ -58,7 +58,13 @@ __global__ void pila_build_kernel(unsigned char* table, int f16, int row_records
         }
         if (cnt == 0) kk[0] = kk[1] = 0;
         if (cnt == 1) kk[1] = kk[0];
-        if (f16) {
+        if (f16 == PILA_U8) {
+            // lengths times 180, rounded (at most round(sqrt 2 * 180) = 255)
+            const uint32_t q0 = (uint32_t)fmin(255.0, rint(ll[0] * 180.0));
+            const uint32_t q1 = (uint32_t)fmin(255.0, rint(ll[1] * 180.0));
+            reinterpret_cast<uint32_t*>(table)[idx] = ((uint32_t)(uint16_t)kk[0]) | (q0 << 16) | (q1 << 24);
+            cnt = (q0 != 0u) + (q1 != 0u);
+        } else if (f16) {
             const __half h0 = __double2half(ll[0]), h1 = __double2half(ll[1]);
             const uint32_t bins = ((uint32_t)(uint16_t)kk[0]) | ((uint32_t)(uint16_t)kk[1] << 16);
             const uint32_t lens = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
@@ -86,9 +92,7 @@ __global__ void pila_hsum_kernel(const unsigned char* table, int f16, int row_re
     double acc = 0.0;
     for (int u = 0; u < U; ++u) {
         const long long rec = p * row_records + u;
-        Entry2 e = f16 ? decode_f16(reinterpret_cast<const uint2*>(table)[rec].x,
-                                    reinterpret_cast<const uint2*>(table)[rec].y)
-                       : decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
+        const Entry2 e = decode_rec(table, rec, f16);
         acc += (double)e.l0 * e.l0 + (double)e.l1 * e.l1;
     }
     hsum[p] = (float)acc;
@@ -103,9 +107,7 @@ __global__ void pila_band_kernel(const unsigned char* table, int f16, int row_re
     int lo = 0x7fffffff, hi = -1;
     if (idx < n_list * U) {
         const long long rec = (long long)list[idx / U] * row_records + idx % U;
-        Entry2 e = f16 ? decode_f16(reinterpret_cast<const uint2*>(table)[rec].x,
-                                    reinterpret_cast<const uint2*>(table)[rec].y)
-                       : decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
+        const Entry2 e = decode_rec(table, rec, f16);
         lo = e.k0;
         hi = e.k0 + 1;
     }
@@ -126,9 +128,7 @@ __global__ void pila_export_kernel(const unsigned char* table, int f16, int row_
     const long long p = idx / U;
     const int u = (int)(idx % U);
     const long long rec = p * row_records + u;
-    Entry2 e = f16 ? decode_f16(reinterpret_cast<const uint2*>(table)[rec].x,
-                                reinterpret_cast<const uint2*>(table)[rec].y)
-                   : decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
+    const Entry2 e = decode_rec(table, rec, f16);
     bins[idx * 2] = e.l0 != 0.0f ? e.k0 : -1;
     bins[idx * 2 + 1] = e.l1 != 0.0f ? e.k1 : -1;
     lens[idx * 2] = e.l0;
@@ -150,10 +150,10 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
     *out = nullptr;
     if (g->n < 1 || g->n_angles < 1 || g->n_bins < 1)
         return fail(SATPILA_ERR_INVALID_ARG, "pila_build: n, n_angles and n_bins must be >= 1");
-    if (precision != PILA_F32 && precision != PILA_F16)
-        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: precision must be PILA_F32 or PILA_F16");
-    if (precision == PILA_F16 && g->n_bins > 32767)
-        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: PILA_F16 needs n_bins <= 32767");
+    if (precision != PILA_F32 && precision != PILA_F16 && precision != PILA_U8)
+        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: precision must be PILA_F32, PILA_F16 or PILA_U8");
+    if (precision != PILA_F32 && g->n_bins > 32767)
+        return fail(SATPILA_ERR_INVALID_ARG, "pila_build: 16-bit bins need n_bins <= 32767");
     if ((long long)g->n * g->n > (1LL << 30))
         return fail(SATPILA_ERR_INVALID_ARG, "pila_build: image too large");
     cudaStream_t s = stream;
@@ -165,8 +165,9 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
     p->U = g->n_angles;
     p->B = g->n_bins;
     p->precision = precision;
-    p->record_bytes = precision == PILA_F16 ? 8 : 16;
-    p->row_records = precision == PILA_F16 ? (p->U + 1) / 2 * 2 : p->U;
+    p->record_bytes = precision == PILA_U8 ? 4 : precision == PILA_F16 ? 8 : 16;
+    // rows are whole 16-byte chunks
+    p->row_records = (p->U + 16 / p->record_bytes - 1) / (16 / p->record_bytes) * (16 / p->record_bytes);
     p->row_bytes = (int64_t)p->row_records * p->record_bytes;
     const long long P = (long long)p->n * p->n;
     p->table_bytes = P * p->row_bytes;
@@ -223,19 +224,19 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
         const long long total = P * p->row_records;
         const int threads = 256;
         const long long blocks = (total + threads - 1) / threads;
-        pila_build_kernel<<<(unsigned)blocks, threads, 0, s>>>(p->d_table, precision == PILA_F16, p->row_records,
+        pila_build_kernel<<<(unsigned)blocks, threads, 0, s>>>(p->d_table, precision, p->row_records,
                                                                 p->n, p->U, p->B, p->d_cos, p->d_sin, d_entries);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        pila_hsum_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(p->d_table, precision == PILA_F16,
+        pila_hsum_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(p->d_table, precision,
                                                                      p->row_records, p->U, P, p->d_hsum);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !list.empty()) {
         const long long total = (long long)list.size() * p->U;
         pila_band_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-            p->d_table, precision == PILA_F16, p->row_records, p->U, p->d_list, (long long)list.size(),
+            p->d_table, precision, p->row_records, p->U, p->d_list, (long long)list.size(),
             reinterpret_cast<int*>(d_entries + 1));
         e = cudaGetLastError();
     }
@@ -299,7 +300,7 @@ extern "C" int pila_export(const satpila_pila* p, int32_t* bins, float* lens, vo
     if (!dev_b) SP_CUDA(cudaMalloc(&db, cnt * sizeof(int32_t)));
     if (!dev_l) SP_CUDA(cudaMalloc(&dl, cnt * sizeof(float)));
     const long long total = P * p->U;
-    pila_export_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p->d_table, p->precision == PILA_F16,
+    pila_export_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p->d_table, p->precision,
                                                                        p->row_records, p->U, P, db, dl);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !dev_b) e = cudaMemcpyAsync(bins, db, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, s);

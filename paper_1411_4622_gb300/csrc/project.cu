@@ -89,13 +89,7 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
         const long long row = q * a.row_records;
         for (int ul = lane; ul < A; ul += 32) {
             const long long rec = row + u0 + ul;
-            Entry2 e;
-            if (a.f16) {
-                const uint2 v = reinterpret_cast<const uint2*>(a.table)[rec];
-                e = decode_f16(v.x, v.y);
-            } else {
-                e = decode_f32(reinterpret_cast<const uint4*>(a.table)[rec]);
-            }
+            const Entry2 e = decode_rec(a.table, rec, a.f16);
             if (e.l0 != 0.0f) {
                 const long long t = a.mode == PROJ_FACTOR ? fixed_product(e.l0, e.l0, F) : fixed_product(f, e.l0, F);
                 atomicAdd(reinterpret_cast<unsigned long long*>(&acc[ul * B + e.k0]), (unsigned long long)t);
@@ -220,7 +214,7 @@ int ensure_factor(satpila_pila* p, cudaStream_t s) {
     SP_CUDA(cudaMalloc(&p->d_w32, cells * sizeof(float)));
     ProjArgs a{};
     a.table = p->d_table;
-    a.f16 = p->precision == PILA_F16;
+    a.f16 = p->precision;
     a.row_records = p->row_records;
     a.n = p->n;
     a.U = p->U;
@@ -262,7 +256,7 @@ extern "C" int pila_forward(const satpila_pila* p, int32_t n_images, const float
     }
     ProjArgs a{};
     a.table = p->d_table;
-    a.f16 = p->precision == PILA_F16;
+    a.f16 = p->precision;
     a.row_records = p->row_records;
     a.n = p->n;
     a.U = p->U;

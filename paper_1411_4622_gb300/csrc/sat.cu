@@ -29,17 +29,20 @@ SweepFn sweep_kernel_f32_smem(int jmax, int kmax);
 SweepFn sweep_kernel_f32_glob(int jmax, int kmax);
 SweepFn sweep_kernel_f16_smem(int jmax, int kmax);
 SweepFn sweep_kernel_f16_glob(int jmax, int kmax);
-SweepFn window_kernel(bool f16, bool smem, int jmax, int kmax);
-SweepFn hybrid_kernel(bool f16, int jmax, int kmax);
+SweepFn window_kernel(int rt, bool smem, int jmax, int kmax);
+SweepFn hybrid_kernel(int rt, int jmax, int kmax);
 SweepFn bome_kernel(bool f16, int jmax, int kmax);
 int bome_warps_per_cta();
 
 namespace {
 
-// kind: 0 pipelined, 1 windowed, 2 hybrid, 3 independent-pixel BoME
-SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax, int kind = 0) {
-    if (kind == 1) return window_kernel(f16, smem, jmax, kmax);
-    if (kind == 2) return hybrid_kernel(f16, jmax, kmax);
+// kind: 0 pipelined, 1 windowed, 2 hybrid, 3 independent-pixel BoME; rt: the
+// table precision (one-byte tables are read by the windowed kernel only)
+SweepFn sweep_kernel(int rt, bool smem, int jmax, int kmax, int kind = 0) {
+    if (kind == 1) return window_kernel(rt, smem, jmax, kmax);
+    if (rt == PILA_U8) return nullptr;
+    const bool f16 = rt == PILA_F16;
+    if (kind == 2) return hybrid_kernel(rt, jmax, kmax);
     if (kind == 3) return bome_kernel(f16, jmax, kmax);
     if (f16) return smem ? sweep_kernel_f16_smem(jmax, kmax) : sweep_kernel_f16_glob(jmax, kmax);
     return smem ? sweep_kernel_f32_smem(jmax, kmax) : sweep_kernel_f32_glob(jmax, kmax);
@@ -48,9 +51,9 @@ SweepFn sweep_kernel(bool f16, bool smem, int jmax, int kmax, int kind = 0) {
 int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : 32; }
 
 // The kernel's shared-memory limit must have been set (prepare_launches).
-cudaError_t launch_sweep(bool f16, bool smem, int kind, int jmax, int kmax, const SatArgs& a, int grid,
+cudaError_t launch_sweep(int rt, bool smem, int kind, int jmax, int kmax, const SatArgs& a, int grid,
                          int warps, size_t smem_bytes, cudaStream_t s) {
-    SweepFn k = sweep_kernel(f16, smem, jmax, kmax, kind);
+    SweepFn k = sweep_kernel(rt, smem, jmax, kmax, kind);
     if (!k) return cudaErrorInvalidValue;
     k<<<grid, warps * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
@@ -68,8 +71,8 @@ cudaError_t allow_max_smem(SweepFn k) {
     return e;
 }
 
-int sweep_blocks_per_sm(bool f16, bool smem, int kind, int jmax, int kmax, int warps, size_t smem_bytes) {
-    SweepFn k = sweep_kernel(f16, smem, jmax, kmax, kind);
+int sweep_blocks_per_sm(int rt, bool smem, int kind, int jmax, int kmax, int warps, size_t smem_bytes) {
+    SweepFn k = sweep_kernel(rt, smem, jmax, kmax, kind);
     if (!k) return 0;
     if (allow_max_smem(k) != cudaSuccess) {
         cudaGetLastError();
@@ -84,7 +87,7 @@ int sweep_blocks_per_sm(bool f16, bool smem, int kind, int jmax, int kmax, int w
 
 namespace {
 
-template <bool F16>
+template <int RT>
 __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
     const int c = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -129,13 +132,7 @@ __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
                 float g = 0.0f, h = 0.0f;
                 const unsigned char* row = a.table + (long long)p * a.row_stride;
                 for (int u = lane; u < a.U; u += 32) {
-                    Entry2 e;
-                    if (F16) {
-                        const uint2 v = reinterpret_cast<const uint2*>(row)[u];
-                        e = decode_f16(v.x, v.y);
-                    } else {
-                        e = decode_f32(reinterpret_cast<const uint4*>(row)[u]);
-                    }
+                    const Entry2 e = decode_rec(row, u, RT);
                     if (e.l0 != 0.0f) {
                         g = fmaf(R[u * a.pitch + e.k0], e.l0, g);
                         h = fmaf(e.l0, e.l0, h);
@@ -199,7 +196,9 @@ size_t Plan::sweep_smem_bytes() const {
 }
 
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl) {
-    const bool f16 = p->precision == PILA_F16;
+    const int rt = p->precision;
+    const bool f16 = rt == PILA_F16;
+    const int rpc = rt == PILA_U8 ? 4 : f16 ? 2 : 1;  // records per 16-byte chunk
     int dev = 0, maxopt = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -207,7 +206,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     // Warps per chain: the fewest that leave each lane at most two records
     // (four for very many angles).
     auto records_per_lane = [&](int W) {
-        return f16 ? 2 * ((p->row_records + 64 * W - 1) / (64 * W)) : (p->U + 32 * W - 1) / (32 * W);
+        return rpc * ((p->row_records + 32 * rpc * W - 1) / (32 * rpc * W));
     };
     // Rows of B + 1 cells (the last one private to the row's lane; rows padded
     // to 16 bytes), then 2 dummy cells per lane of a group.
@@ -226,6 +225,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     // Sec. III-B as written (an independent pixel per estimate): its own
     // kernel, one warp per chain, residual in global memory.
     if (prm->flags & SAT_FLAG_BOME_INDEPENDENT) {
+        if (rt == PILA_U8) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: one-byte tables are read by the windowed kernel only");
         if (prm->residency == SAT_RESIDENT_SMEM)
             return fail(SATPILA_ERR_INVALID_ARG, "sat_run: independent-pixel BoME keeps the residual in global memory");
         const int J = records_per_lane(1);
@@ -241,11 +241,11 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
         pl->W = 1;
         pl->J = pl->jmax = jmax;
         pl->D = 2;
-        pl->stage_bytes = 512 * (f16 ? jmax / 2 : jmax);
+        pl->stage_bytes = 512 * (jmax / rpc);
         pl->group_smem = (int)align_up((size_t)2 * prm->bome_k * pl->stage_bytes, 128);
         const int warps = std::max(1, std::min(bome_warps_per_cta(), maxopt / pl->group_smem));
         pl->groups = pl->warps = std::min(warps, std::max(1, n_chains));
-        int per_sm = sweep_blocks_per_sm(f16, false, 3, jmax, kmax_for(prm->bome_k), pl->warps,
+        int per_sm = sweep_blocks_per_sm(rt, false, 3, jmax, kmax_for(prm->bome_k), pl->warps,
                                          (size_t)pl->warps * pl->group_smem);
         if (per_sm < 1) per_sm = 1;
         const long long slots = (long long)sms * per_sm * pl->warps;
@@ -264,14 +264,17 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
                                       variant == PLAN_WINDOW_HYBRID;
     if (use_window && !window_ok)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many angles for the windowed kernel");
+    if (rt == PILA_U8 && !use_window)
+        return fail(SATPILA_ERR_INVALID_ARG,
+                    "sat_run: one-byte tables are read by the windowed kernel only (at most 128 angles)");
     if (use_window) {
         const int residency = variant == PLAN_WINDOW_SMEM     ? SAT_RESIDENT_SMEM
                               : variant == PLAN_WINDOW_GLOBAL ? SAT_RESIDENT_GLOBAL
                                                               : prm->residency;
-        const bool want_hybrid =
-            variant == PLAN_WINDOW_HYBRID || (variant == PLAN_RULES && (prm->flags & SAT_FLAG_HYBRID));
+        const bool want_hybrid = rt != PILA_U8 && (variant == PLAN_WINDOW_HYBRID ||
+                                                   (variant == PLAN_RULES && (prm->flags & SAT_FLAG_HYBRID)));
         const int jw = records_per_lane(1) <= 2 ? 2 : 4;
-        const int stage = 512 * (f16 ? jw / 2 : jw);
+        const int stage = 512 * (jw / rpc);
         const size_t ring1 = group_ring_bytes(1) + (size_t)2 * kWin * stage;
         const size_t gsm = align_up(ring1 + (size_t)pl->band_floats * 4, 128);  // shared-memory warp
         const size_t glob = align_up(ring1, 128);                                   // global-memory warp
@@ -285,7 +288,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
             pl->smem = smem;
             pl->groups = warps;
             pl->warps = warps;
-            int per_sm = sweep_blocks_per_sm(f16, smem, kind, jw, kmax, warps, smem_bytes);
+            int per_sm = sweep_blocks_per_sm(rt, smem, kind, jw, kmax, warps, smem_bytes);
             if (per_sm < 1) per_sm = 1;
             const long long slots = (long long)sms * per_sm * warps;
             pl->spt = (!dynamic_tasks && n_chains <= slots) ? window : 1;
@@ -336,7 +339,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->jmax = jmax;
     pl->D = prm->pipeline_depth > 0 ? prm->pipeline_depth : 4;
     if (pl->D < 3 || pl->D > kMaxStages) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: pipeline_depth must be in [3, 8]");
-    pl->stage_bytes = 512 * W * (f16 ? jmax / 2 : jmax);  // 16-byte chunks of all lanes
+    pl->stage_bytes = 512 * W * (jmax / rpc);  // 16-byte chunks of all lanes
     const size_t ring = group_ring_bytes(W) + (size_t)pl->D * pl->stage_bytes;
     const size_t smem_group = align_up(ring + (size_t)pl->resid_floats * 4, 128);
     const size_t glob_group = align_up(ring, 128);
@@ -358,7 +361,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->groups = groups;
     pl->warps = groups * W;
     const size_t smem_bytes = (size_t)groups * pl->group_smem;
-    int per_sm = sweep_blocks_per_sm(f16, smem, 0, jmax, kmax_for(prm->bome_k), pl->warps, smem_bytes);
+    int per_sm = sweep_blocks_per_sm(rt, smem, 0, jmax, kmax_for(prm->bome_k), pl->warps, smem_bytes);
     if (per_sm < 1) per_sm = 1;
     const long long slots = (long long)sms * per_sm * groups;
     pl->spt = n_chains <= slots ? window : 1;
@@ -430,7 +433,7 @@ void batch_carve(void* base, const Plan& pl, long long cap, BatchDev* b) {
 cudaError_t prepare_launches(const satpila_pila* p, const Plan& pl, int bome_k) {
     cudaError_t e = prepare_projector();
     if (e != cudaSuccess) return e;
-    SweepFn k = sweep_kernel(p->precision == PILA_F16, pl.smem, pl.jmax, kmax_for(bome_k), pl.kind);
+    SweepFn k = sweep_kernel(p->precision, pl.smem, pl.jmax, kmax_for(bome_k), pl.kind);
     if (!k) return cudaErrorInvalidValue;
     return allow_max_smem(k);
 }
@@ -442,7 +445,7 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
     const int G = pl.proj_G;
     ProjArgs pa{};
     pa.table = p->d_table;
-    pa.f16 = p->precision == PILA_F16;
+    pa.f16 = p->precision;
     pa.row_records = p->row_records;
     pa.n = p->n;
     pa.U = p->U;
@@ -482,7 +485,7 @@ cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b,
     T0Args ta{};
     ta.table = p->d_table;
     ta.row_stride = p->row_bytes;
-    ta.f16 = p->precision == PILA_F16;
+    ta.f16 = p->precision;
     ta.n = p->n;
     ta.U = p->U;
     ta.B = p->B;
@@ -505,8 +508,9 @@ cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b,
     ta.TN = b.TN + c0;
     ta.found = b.found + c0;
     ta.ctl = b.ctl ? b.ctl + c0 : nullptr;
-    if (ta.f16) t0_kernel<true><<<nc, 256, 0, q>>>(ta);
-    else t0_kernel<false><<<nc, 256, 0, q>>>(ta);
+    if (ta.f16 == PILA_U8) t0_kernel<PILA_U8><<<nc, 256, 0, q>>>(ta);
+    else if (ta.f16 == PILA_F16) t0_kernel<PILA_F16><<<nc, 256, 0, q>>>(ta);
+    else t0_kernel<PILA_F32><<<nc, 256, 0, q>>>(ta);
     return cudaGetLastError();
 }
 
@@ -566,7 +570,7 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.sweeps_per_task = pl.spt;
     sa.n_tasks = n_chains * ((s_end - s_begin + pl.spt - 1) / pl.spt);
     sa.task_counter = task_counter;
-    return launch_sweep(p->precision == PILA_F16, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid,
+    return launch_sweep(p->precision, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid,
                         pl.warps, pl.sweep_smem_bytes(), q);
 }
 

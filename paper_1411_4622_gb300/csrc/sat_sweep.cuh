@@ -151,6 +151,40 @@ __device__ __forceinline__ void decode_stage(const unsigned char* stage, int gl,
     }
 }
 
+// Record-type-generic forms (RT = PILA_F32, PILA_F16 or PILA_U8): records per
+// 16-byte chunk, the lane's chunks, the record of a lane slot, decoding.
+template <int RT>
+__host__ __device__ constexpr int recs_per_chunk() { return RT == PILA_U8 ? 4 : RT == PILA_F16 ? 2 : 1; }
+
+template <int RT, int JMAX>
+__host__ __device__ constexpr int rt_chunks_per_lane() { return JMAX / recs_per_chunk<RT>(); }
+
+template <int RT>
+__device__ __forceinline__ int rt_record_of(int gl, int W, int j) {
+    constexpr int r = recs_per_chunk<RT>();
+    return r * (gl + 32 * W * (j / r)) + (j % r);
+}
+
+template <int RT, int JMAX>
+__device__ __forceinline__ void rt_decode_stage(const unsigned char* stage, int gl, int W, Recs<JMAX>& r) {
+    if constexpr (RT == PILA_U8) {
+        const uint4* q4 = reinterpret_cast<const uint4*>(stage);
+#pragma unroll
+        for (int i = 0; i < JMAX / 4; ++i) {
+            const uint4 v = q4[gl + 32 * W * i];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                r.k[4 * i + q] = (int)(w[q] & 0xffffu);
+                r.l0[4 * i + q] = (float)((w[q] >> 16) & 0xffu) * kU8Unit;
+                r.l1[4 * i + q] = (float)(w[q] >> 24) * kU8Unit;
+            }
+        }
+    } else {
+        decode_stage<RT == PILA_F16, JMAX>(stage, gl, W, r);
+    }
+}
+
 struct GroupShared {
     uint64_t* bar;         // one barrier: the residual's bulk copy at task start
     float* part;           // [2][kMaxGroupWarps][4] partial (Gs, OV) per move parity
@@ -697,7 +731,7 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_sweep_kernel(const SatA
 struct T0Args {
     const unsigned char* table;
     long long row_stride;
-    int f16;
+    int f16;  // table precision (PILA_F32, PILA_F16, PILA_U8)
     int n, U, B;
     int pitch;
     const int32_t* list;

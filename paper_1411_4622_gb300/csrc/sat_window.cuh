@@ -31,7 +31,7 @@ __device__ __forceinline__ void cell_share(int ki, float a0, float a1, int kj, f
     s1 = d == 0 ? a1 : (d == -1 ? a0 : 0.0f);
 }
 
-template <bool F16, bool SMEM, int JMAX, int KMAX>
+template <int RT, bool SMEM, int JMAX, int KMAX>
 __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupShared& G, const StageCtx& x,
                                                  float& S_hi, float& S_lo, unsigned long long& n_acc,
                                                  const int (&rowbase)[JMAX]) {
@@ -48,7 +48,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                 const unsigned char* row = a.table + (long long)G.pix[mv % kDrawRing] * a.row_stride;
                 unsigned char* st = stage_of(w, j);
 #pragma unroll
-                for (int i = 0; i < chunks_per_lane<F16, JMAX>(); ++i) {
+                for (int i = 0; i < rt_chunks_per_lane<RT, JMAX>(); ++i) {
                     const int q = x.gl + 32 * i;
                     cp_async_16_pred(q < a.row_chunks, st + 16 * q, row + 16 * (q < a.row_chunks ? q : 0));
                 }
@@ -109,7 +109,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
             Recs<JMAX> r;
-            decode_stage<F16, JMAX>(stage_of(w, j), x.gl, 1, r);
+            rt_decode_stage<RT, JMAX>(stage_of(w, j), x.gl, 1, r);
 #pragma unroll
             for (int s = 0; s < JMAX; ++s) {
                 k[j][s] = r.k[s];
@@ -313,7 +313,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 
 // Task loop of one warp with its residual in shared memory (gb, window_bytes
 // of shared memory; barrier id 1 + warp).
-template <bool F16, bool SMEM, int JMAX, int KMAX>
+template <int RT, bool SMEM, int JMAX, int KMAX>
 __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb, int warp, int lane) {
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
@@ -344,7 +344,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        const int u = record_of<F16>(lane, 1, j);
+        const int u = rt_record_of<RT>(lane, 1, j);
         rowbase[j] = u < a.U ? u * rpitch - rshift : a.U * rpitch + 2 * lane;
     }
     if (SMEM) {
@@ -466,7 +466,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
             x.s = s_base + s;
             x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<F16, SMEM, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
+            run_stage_window<RT, SMEM, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
             if (a.sweep_cost && lane == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
         }
@@ -495,11 +495,11 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     }
 }
 
-template <bool F16, bool SMEM, int JMAX, int KMAX>
+template <int RT, bool SMEM, int JMAX, int KMAX>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    window_warp<F16, SMEM, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
+    window_warp<RT, SMEM, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
 }
 
 // Both kinds of warp in one CTA, pulling from the same task queue: the first
@@ -507,16 +507,16 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_kernel(const Sat
 // work on it in global memory.  Both run the same windowed arithmetic, so a
 // chain's result does not depend on which warps ran its stages; faster warps
 // simply take more tasks.
-template <bool F16, int JMAX, int KMAX>
+template <int RT, int JMAX, int KMAX>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ns = a.hybrid_smem_warps;
     if (warp < ns) {
-        window_warp<F16, true, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
+        window_warp<RT, true, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
     } else {
         const int g = warp - ns;
-        window_warp<F16, false, JMAX, KMAX>(a, smem + (size_t)ns * a.group_smem_bytes + (size_t)g * a.hybrid_glob_bytes,
+        window_warp<RT, false, JMAX, KMAX>(a, smem + (size_t)ns * a.group_smem_bytes + (size_t)g * a.hybrid_glob_bytes,
                                             warp, lane);
     }
 }

@@ -211,8 +211,8 @@ Geometry* satpila_server::geometry_for(const Request& r, size_t budget_left) {
         if (g->key == key) return g.get();
     // a table of this size: records + list + mask + per-pixel sums
     const size_t P = (size_t)r.n * r.n;
-    const size_t rec = r.precision == PILA_F16 ? 8 : 16;
-    const size_t rows = r.precision == PILA_F16 ? ((size_t)r.U + 1) / 2 * 2 : (size_t)r.U;
+    const size_t rec = r.precision == PILA_U8 ? 4 : r.precision == PILA_F16 ? 8 : 16;
+    const size_t rows = ((size_t)r.U + 16 / rec - 1) / (16 / rec) * (16 / rec);
     const size_t need = P * rows * rec + P * 9 + (size_t)r.U * 16 + 4096;
     // evict unused tables, least recently used first
     while (need > budget_left) {
@@ -864,8 +864,8 @@ namespace {
 
 size_t request_bytes_estimate(int n, int U, int B, int precision) {
     const size_t P = (size_t)n * n;
-    const size_t rec = precision == PILA_F16 ? 8 : 16;
-    const size_t rows = precision == PILA_F16 ? ((size_t)U + 1) / 2 * 2 : (size_t)U;
+    const size_t rec = precision == PILA_U8 ? 4 : precision == PILA_F16 ? 8 : 16;
+    const size_t rows = ((size_t)U + 16 / rec - 1) / (16 / rec) * (16 / rec);
     const size_t table = P * rows * rec + P * 9 + (size_t)U * 16 + 4096;
     const size_t chain = ((size_t)U * (((size_t)B + 4) & ~(size_t)3) + 256 + P + (size_t)U * B) * 4 + 1024;
     return table + 4 * chain + 8192;  // the class arrays hold at least four chains
@@ -922,10 +922,12 @@ extern "C" int sat_server_submit(satpila_server* s, const sat_request* r, uint64
     const sat_params& prm = r->prm;
     if (r->n < 1 || r->n_angles < 1 || r->n_bins < 1 || !r->sino)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: bad geometry or no sinogram");
-    if (r->precision != PILA_F32 && r->precision != PILA_F16)
+    if (r->precision != PILA_F32 && r->precision != PILA_F16 && r->precision != PILA_U8)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: unknown precision");
-    if (r->precision == PILA_F16 && r->n_bins > 32767)
+    if (r->precision != PILA_F32 && r->n_bins > 32767)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: too many bins for 16-bit indices");
+    if (r->precision == PILA_U8 && r->n_angles > 128)
+        return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: one-byte tables take at most 128 angles");
     if (prm.bome_k < 1 || prm.bome_k > kMaxK || !(prm.beta > 0.0f) || prm.n_sweeps < 0 || prm.moves_per_sweep < 0 ||
         prm.schedule < SAT_SCHED_LINEAR || prm.schedule > SAT_SCHED_CUBIC || prm.residency < SAT_RESIDENT_AUTO ||
         prm.residency > SAT_RESIDENT_GLOBAL)

@@ -34,13 +34,7 @@ __global__ void sirt_backproject_kernel(const unsigned char* table, int f16, lon
     float acc = 0.0f;
     for (int u = lane; u < U; u += 32) {
         const long long rec = (long long)p * row_records + u;
-        Entry2 e;
-        if (f16) {
-            const uint2 v = reinterpret_cast<const uint2*>(table)[rec];
-            e = decode_f16(v.x, v.y);
-        } else {
-            e = decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
-        }
+        const Entry2 e = decode_rec(table, rec, f16);
         if (e.l0 != 0.0f) acc = fmaf(c[u * B + e.k0], e.l0, acc);
         if (e.l1 != 0.0f) acc = fmaf(c[u * B + e.k1], e.l1, acc);
     }
@@ -64,13 +58,7 @@ __global__ void sirt_sequential_kernel(const unsigned char* table, int f16, long
         float acc = 0.0f;
         for (int u = lane; u < U; u += 32) {
             const long long rec = (long long)p * row_records + u;
-            Entry2 e;
-            if (f16) {
-                const uint2 v = reinterpret_cast<const uint2*>(table)[rec];
-                e = decode_f16(v.x, v.y);
-            } else {
-                e = decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
-            }
+            const Entry2 e = decode_rec(table, rec, f16);
             if (e.l0 != 0.0f) {
                 const float wv = w[u * B + e.k0];
                 if (wv > 0.0f) acc = fmaf(-r[u * B + e.k0] / wv, e.l0, acc);
@@ -86,13 +74,7 @@ __global__ void sirt_sequential_kernel(const unsigned char* table, int f16, long
         if (lane == 0) f[p] += d;
         for (int u = lane; u < U; u += 32) {
             const long long rec = (long long)p * row_records + u;
-            Entry2 e;
-            if (f16) {
-                const uint2 v = reinterpret_cast<const uint2*>(table)[rec];
-                e = decode_f16(v.x, v.y);
-            } else {
-                e = decode_f32(reinterpret_cast<const uint4*>(table)[rec]);
-            }
+            const Entry2 e = decode_rec(table, rec, f16);
             if (e.l0 != 0.0f) r[u * B + e.k0] = fmaf(d, e.l0, r[u * B + e.k0]);
             if (e.l1 != 0.0f) r[u * B + e.k1] = fmaf(d, e.l1, r[u * B + e.k1]);
         }
@@ -158,7 +140,7 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
 
     ProjArgs pa{};
     pa.table = p->d_table;
-    pa.f16 = p->precision == PILA_F16;
+    pa.f16 = p->precision;
     pa.row_records = p->row_records;
     pa.n = p->n;
     pa.U = p->U;
@@ -307,7 +289,7 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
 
     ProjArgs pa{};
     pa.table = p->d_table;
-    pa.f16 = p->precision == PILA_F16;
+    pa.f16 = p->precision;
     pa.row_records = p->row_records;
     pa.n = p->n;
     pa.U = p->U;

@@ -54,7 +54,7 @@ GEOMS = [(64, 90, 91, None), (37, 45, 53, None), (16, 7, 23, None), (5, 3, 7, No
 
 
 @pytest.mark.parametrize("n,U,B,ang", GEOMS)
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_pila_matches_oracle(api, n, U, B, ang, prec):
     angles = None
     if ang == "random":
@@ -63,7 +63,21 @@ def test_pila_matches_oracle(api, n, U, B, ang, prec):
     p = api.pila_build(n, U, B, prec, angles=angles)
     gb, gl = api.pila_export(p)
     info = api.pila_info(p)
-    assert info["record_bytes"] == (8 if prec else 16)
+    assert info["record_bytes"] == {0: 16, 1: 8, 2: 4}[prec]
+    if prec == 2:
+        # one-byte lengths (q / 180, Sec. II-B): entries longer than half a
+        # unit are present, on the same bins, within half a unit; shorter ones
+        # are absent (records holding an entry within 1e-7 of half a unit,
+        # where rounding decides, are left out)
+        half = 0.5 / 180.0
+        amb = np.any(np.abs(ol - half) < 1e-7, axis=-1)
+        ob2, ol2 = compact(ob, ol, half)
+        gb2, gl2 = compact(gb, gl.astype(np.float64), half)
+        assert np.array_equal(ob2[~amb], gb2[~amb])
+        assert np.all(np.abs(gl2 - ol2)[~amb] <= half + 1e-7)
+        assert info["entries"] == int((gl > 0).sum())
+        api.pila_free(p)
+        return
     ob_, ol_ = compact(ob, ol, 1e-9)
     gb_, gl_ = compact(gb, gl.astype(np.float64), 1e-9)
     if prec == 0:
@@ -244,6 +258,44 @@ def test_sat_final_rmse_plain64_vs_oracle(api):
     r_orc = synth.rmse(oimg, ph)
     assert abs(r_gpu - r_orc) <= 0.02 * r_orc, (r_gpu, r_orc)
     assert abs(st[0]["final_cost"] - ost["final_cost_fresh"]) <= 0.02 * ost["final_cost_fresh"]
+    api.pila_free(p)
+
+
+def test_sat_u8_table(api):
+    """The one-byte table of Sec. II-B (lengths q / 180): its forward
+    projection is the exact sum of its stored lengths, the windowed kernel
+    gives the same chain whichever memory holds the residual, and the final
+    RMSE of the 128^2 / 120-angle slice stays within 5% of the FP64 oracle's
+    (exact lengths); the FP16 table's is within 2% (next test)."""
+    n, U, B = 128, 120, 181
+    ph = synth.phantom(n, 20, 1002)
+    mask = synth.disk_mask(n)
+    pm = oracle.drt(ph, U, B)
+    img0 = synth.initial_image(n, 0.5, mask)
+    p = api.pila_build(n, U, B, api.PILA_U8, mask=mask)
+    bins, lens = api.pila_export(p)
+    x = np.random.default_rng(8).random((n, n)).astype(np.float32)
+    fwd = api.pila_forward(p, dev(x).reshape(1, n, n)).cpu().numpy()[0]
+    ref = np.zeros((U, B))
+    P = n * n
+    pix = np.repeat(np.arange(P), U * 2).reshape(P, U, 2)
+    ang = np.tile(np.repeat(np.arange(U), 2).reshape(U, 2), (P, 1, 1))
+    ok = bins >= 0
+    np.add.at(ref, (ang[ok], bins[ok]), lens[ok].astype(np.float64) * x.ravel()[pix[ok]])
+    assert np.max(np.abs(fwd - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    kw = dict(bome_k=4, n_sweeps=8, t0=-1.0, tn=-1.0, seed=3002)
+    outs = []
+    for res in (api.SAT_RESIDENT_SMEM, api.SAT_RESIDENT_GLOBAL):
+        img = dev(img0).reshape(1, n, n)
+        st = api.sat_run(p, dev(pm).reshape(1, U, B), img, residency=res, **kw)
+        assert st[0]["status"] == 0
+        outs.append(img.cpu().numpy()[0])
+    assert np.array_equal(outs[0], outs[1])
+    oimg, ost, _ = oracle.sat_run(pm, img0, mask=mask, **kw)
+    r_gpu, r_orc = synth.rmse(outs[0], ph, mask), synth.rmse(oimg, ph, mask)
+    assert abs(r_gpu - r_orc) <= 0.05 * r_orc, (r_gpu, r_orc)
+    with pytest.raises(api.SatpilaError):
+        api.sat_run(p, dev(pm).reshape(1, U, B), dev(img0).reshape(1, n, n), pipeline_depth=4, **kw)
     api.pila_free(p)
 
 
