@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     ap.add_argument("--flags", type=int, default=0, help="SAT_FLAG_* bits for the batched run")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt", "fbp"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
                          "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
-                         "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A)")
+                         "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A); "
+                         "fbp: FBP against SAT with and without the FBP spatial constraint (Fig. 9)")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
                     help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
@@ -609,6 +610,61 @@ def run_drt(args):
     print(json.dumps(out))
 
 
+def run_fbp(args):
+    """Fig. 9 on synthetic phantoms: 16 slices of 128x128 whose ellipses sit
+    off the centre of rotation, noiseless; FBP (Ram-Lak) at 90 and 200
+    angles; SAT at 90 angles with the spatial constraint (FBP thresholded at
+    10% of its maximum, FBP start image, beta = FBP maximum) and without it
+    (every pixel, uniform 0.5 start, beta = 1); 8 estimates, 100 stages,
+    T0 by Eq. (8).  Reported: mean NRMSE (RMS error over the phantom's mean)."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    n, C, S, K = 128, args.slices or 16, args.sweeps or 100, 8
+    ph = []
+    for i in range(C):
+        base = synth.phantom(n, 10, synth.slice_seeds(i)[0]) * synth.disk_mask(n, 0.3 * n)
+        shifted = np.zeros_like(base)
+        shifted[n // 6:, n // 5:] = base[: n - n // 6, : n - n // 5]  # off the centre of rotation
+        ph.append(shifted)
+    ph = np.stack(ph)
+    out = {}
+    sinos = {}
+    for U in (90, 200):
+        B = synth.bins_for(n)
+        pf = api.pila_build(n, U, B, api.PILA_F32)
+        sinos[U] = api.pila_forward(pf, torch.tensor(ph, dtype=torch.float32, device="cuda")).float().contiguous()
+        api.pila_free(pf)
+        rec = api.fbp(sinos[U], n).cpu().numpy()
+        out[f"fbp_U{U}"] = float(np.mean([nrmse(rec[i], ph[i]) for i in range(C)]))
+    U, B = 90, synth.bins_for(n)
+    rec = api.fbp(sinos[U], n)
+    init, mask, beta = api.fbp_prior(rec, 0.1)
+    masks, inits = mask.cpu().numpy(), init
+    constrained = []
+    for i in range(C):
+        p = api.pila_build(n, U, B, api.PILA_F16, mask=masks[i])
+        img = inits[i:i + 1].clone()
+        api.sat_run(p, sinos[U][i:i + 1], img, bome_k=K, n_sweeps=S, beta=float(beta[i]), t0=-1.0, tn=-1.0,
+                    seed=synth.slice_seeds(i)[2])
+        constrained.append(nrmse(img.cpu().numpy()[0], ph[i]))
+        api.pila_free(p)
+    out["sat_U90_constrained"] = float(np.mean(constrained))
+    p = api.pila_build(n, U, B, api.PILA_F16)
+    img = torch.full((C, n, n), 0.5, dtype=torch.float32, device="cuda")
+    api.sat_run(p, sinos[U], img, bome_k=K, n_sweeps=S, beta=1.0, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2])
+    api.pila_free(p)
+    img = img.cpu().numpy()
+    out["sat_U90_unconstrained"] = float(np.mean([nrmse(img[i], ph[i]) for i in range(C)]))
+    print(json.dumps({"metric": "mean NRMSE", "unit": "nrmse", "higher_is_better": False, "data": "synthetic",
+                      "config": {"workload": "fbp", "n": n, "slices": C, "stages": S, "bome_k": K,
+                                 "mask_threshold": 0.1, "filter": "Ram-Lak"}, "results": out}))
+
+
 def main():
     args = parse()
     if args.workload == "precision512":
@@ -619,6 +675,8 @@ def main():
         return run_bome(args)
     if args.workload == "drt":
         return run_drt(args)
+    if args.workload == "fbp":
+        return run_fbp(args)
     cfg = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -337,6 +337,32 @@ int sat_drt_run(int32_t n, int32_t n_angles, int32_t n_bins, const uint8_t* mask
                 const float* sino_meas, float* images, const sat_params* prm, sat_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* FBP prior (Step 1, Step 2, Fig. 9): start image, beta and spatial          */
+/* constraint from a filtered back-projection.                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Parallel-beam FBP of n_items sinograms ([n_items][n_angles][n_bins], device)
+ * into images ([n_items][n][n], device).  The paper gives no filter; this uses
+ * the discrete Ram-Lak filter for unit bins (h(0) = 1/4, h(k) = -1/(pi^2 k^2)
+ * for odd k, 0 otherwise) and linear interpolation between bin centres in the
+ * back-projection f(x, y) = (pi / U) sum_u q_u(x cos + y sin).  angles_rad
+ * (host) may be NULL (u pi / U).  Synchronizes `stream`.
+ */
+int fbp(int32_t n, int32_t n_angles, int32_t n_bins, const double* angles_rad, int32_t n_items,
+        const float* sino, float* images, void* stream);
+
+/*
+ * From FBP images ([n_items][n][n], device): beta[i] = max(0, max image i)
+ * (the pixel range of Eq. (3), Step 2), mask = pixels above mask_frac * beta
+ * (the spatial constraint, by a threshold filter), init = the image clipped to
+ * [0, beta] on the mask and 0 elsewhere (the start image of Step 1).  Each
+ * output (device) may be NULL.  Synchronizes `stream`.
+ */
+int fbp_prior(int32_t n, int32_t n_items, const float* images, float mask_frac, float* init, uint8_t* mask,
+              float* beta, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* SIRT with PILA: Eqs. (10)-(11), Sec. III-D.                                */
 /* ------------------------------------------------------------------------ */
 

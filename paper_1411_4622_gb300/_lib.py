@@ -26,7 +26,7 @@ SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["satpila_last_error", "satpila_version", "pila_build", "pila_free", "pila_info", "pila_export",
            "pila_forward", "pila_sirt_factor", "sat_run", "sat_server_create", "sat_server_submit", "sat_server_poll",
-           "sat_server_wait", "sat_server_info", "sat_server_destroy", "drt_bilinear", "sat_drt_run", "sirt_run",
+           "sat_server_wait", "sat_server_info", "sat_server_destroy", "drt_bilinear", "sat_drt_run", "fbp", "fbp_prior", "sirt_run",
            "sirt_run_noalloc"]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -122,6 +122,8 @@ def load():
         lib.sat_server_destroy.argtypes = [V]
         lib.drt_bilinear.argtypes = [C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V, V, V]
         lib.sat_drt_run.argtypes = [C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V, V, C.POINTER(SatParams), V, V]
+        lib.fbp.argtypes = [C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V, V, V]
+        lib.fbp_prior.argtypes = [C.c_int32, C.c_int32, V, C.c_float, V, V, V, V]
         lib.sirt_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
         lib.sirt_run_noalloc.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
         for name in EXPORTS:

@@ -189,6 +189,32 @@ def sat_drt_run(sino_meas, images, *, mask=None, stream=None, **kw) -> list[dict
     return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
 
 
+def fbp(sino, n, stream=None):
+    """FBP images [items, n, n] (float32 tensor) of device sinograms [items, U, B]."""
+    import torch
+
+    items = int(sino.shape[0]) if sino.ndim == 3 else 1
+    U, B = int(sino.shape[-2]), int(sino.shape[-1])
+    out = torch.empty((items, n, n), dtype=torch.float32, device=sino.device)
+    L.check(L.load().fbp(int(n), U, B, None, items, _ptr(sino, np.float32), _ptr(out, np.float32), _stream(stream)))
+    return out
+
+
+def fbp_prior(images, mask_frac, stream=None):
+    """(init, mask, beta) from FBP images: start image, spatial constraint
+    (pixels above mask_frac * max) and the pixel range beta = max."""
+    import torch
+
+    items = int(images.shape[0]) if images.ndim == 3 else 1
+    n = int(images.shape[-1])
+    init = torch.empty((items, n, n), dtype=torch.float32, device=images.device)
+    mask = torch.empty((items, n, n), dtype=torch.uint8, device=images.device)
+    beta = torch.empty((items,), dtype=torch.float32, device=images.device)
+    L.check(L.load().fbp_prior(n, items, _ptr(images, np.float32), float(mask_frac), _ptr(init, np.float32),
+                               _ptr(mask, np.uint8), _ptr(beta, np.float32), _stream(stream)))
+    return init, mask, beta
+
+
 class Server:
     """Continuous-batching annealing server (sat_server_* of include/satpila.h).
 

@@ -631,3 +631,28 @@ def test_sat_drt_follows_oracle(api):
         thr = -T * np.log(tr_o["u_acc"][i])
         assert abs(tr_o["dC"][i] - thr) <= 1e-4 * cref or abs(tr_o["dC"][i]) <= 1e-4 * cref
     assert first_diff >= 0.5 * S * M
+
+
+def test_fbp_and_prior_vs_oracle(api):
+    """FBP (Ram-Lak) in FP32 against the oracle's FP64, and the prior (beta,
+    threshold mask, clipped start image) against its definition applied to
+    the GPU's own FBP image."""
+    from oracle import fbp as F
+
+    n, U = 64, 90
+    B = synth.bins_for(n)
+    phs = [synth.phantom(n, 8, 500 + i) for i in range(3)]
+    sinos = np.stack([oracle.drt(ph, U, B) for ph in phs])
+    rec = api.fbp(dev(sinos), n)
+    got = rec.cpu().numpy()
+    for i in range(3):
+        ref = F.fbp(sinos[i], n)
+        assert np.max(np.abs(got[i] - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+    init, mask, beta = api.fbp_prior(rec, 0.1)
+    init, mask, beta = init.cpu().numpy(), mask.cpu().numpy(), beta.cpu().numpy()
+    for i in range(3):
+        mx = max(float(got[i].max()), 0.0)
+        assert beta[i] == np.float32(mx)
+        m = got[i] > np.float32(0.1) * np.float32(mx)
+        assert np.array_equal(mask[i].astype(bool), m)
+        assert np.array_equal(init[i], np.where(m, np.clip(got[i], 0.0, mx), 0.0).astype(np.float32))

@@ -486,3 +486,30 @@ def test_sat_with_full_drt_against_recomputation(orc):
             cur.flat[p] = vals[best]
     assert np.allclose(cur, img, atol=1e-15)
     assert abs(st["final_cost"] - st["final_cost_fresh"]) < 1e-12
+
+
+def test_fbp_ramlak_and_reconstruction(orc):
+    """FBP (the start image and spatial constraint of Step 1 / Fig. 9; filter
+    read as Ram-Lak): the taps sum to zero up to the truncation bound
+    1/(pi^2 (B - 1)), FBP is linear, and it reconstructs a uniform disk from
+    exact line integrals: ~1 inside, ~0 outside, peak at an isolated pixel."""
+    from oracle import fbp as F
+
+    for B in (91, 363, 725):
+        assert abs(F.ramlak(B).sum()) <= 1.0 / (np.pi ** 2 * (B - 1)) + 1e-12
+    n, U = 64, 100
+    B = synth.bins_for(n)
+    disk = synth.disk_mask(n, 20.0).astype(np.float64)
+    rec = F.fbp(orc.drt(disk, U, B), n)
+    j = np.arange(n) - 0.5 * (n - 1)
+    r = np.sqrt(j[None, :] ** 2 + j[:, None] ** 2)
+    assert np.all(np.abs(rec[r < 17] - 1.0) < 0.06)
+    ring = (r > 24) & (r < 31)  # just outside the disk: ringing of the pixelised edge only
+    assert np.max(np.abs(rec[ring])) < 0.1 and np.mean(np.abs(rec[ring])) < 0.03
+    assert np.mean(np.abs(rec[r > 23])) < 0.02
+    a, b = np.random.default_rng(1).random((2, U, B))
+    np.testing.assert_allclose(F.fbp(2.0 * a - 3.0 * b, n), 2.0 * F.fbp(a, n) - 3.0 * F.fbp(b, n), atol=1e-12)
+    dot = np.zeros((n, n))
+    dot[20, 41] = 1.0
+    rd = F.fbp(orc.drt(dot, U, B), n)
+    assert np.unravel_index(np.argmax(rd), rd.shape) == (20, 41)
