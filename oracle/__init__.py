@@ -50,7 +50,7 @@ class SatParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("bome_k", C.c_int32), ("n_sweeps", C.c_int32),
                 ("moves_per_sweep", C.c_int32), ("t0", C.c_double), ("tn", C.c_double),
                 ("schedule", C.c_int32), ("t0_samples", C.c_int32), ("seed", C.c_uint64),
-                ("bome_mode", C.c_int32), ("pad", C.c_int32)]
+                ("bome_mode", C.c_int32), ("grid_levels", C.c_int32)]
 
 
 class SatStats(C.Structure):
@@ -187,6 +187,21 @@ def sat_drt_run(pm, image, *, t0, tn=-1.0, beta=1.0, bome_k=1, n_sweeps=1, moves
     return img, {f: getattr(st, f) for f, _ in SatStats._fields_}, tr
 
 
+def exhaustive_grid(pm, n, levels, beta=1.0, angles=None):
+    """Least Eq. (4) cost over every n x n image with pixel values on the
+    grid {0, beta/(L-1), ..., beta}: (min cost, images attaining it, first one)."""
+    pm_ = _f64(pm)
+    g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
+    cost = C.c_double(0.0)
+    cnt = C.c_int64(0)
+    arg = np.zeros((n, n), dtype=np.float64)
+    rc = _load().or_exhaustive_grid(C.byref(g), _ptr(pm_), C.c_int32(int(levels)), C.c_double(float(beta)),
+                                    C.byref(cost), C.byref(cnt), _ptr(arg))
+    if rc != 0:
+        raise RuntimeError(f"exhaustive_grid failed ({rc})")
+    return cost.value, cnt.value, arg
+
+
 def pila(n, n_angles, n_bins, angles=None):
     """Eq. (5): the PILA, bins [P, U, 2] (int32, -1 = empty) and lengths [P, U, 2]."""
     g, keep = _geom(n, n_angles, n_bins, angles)
@@ -219,9 +234,11 @@ def schedule_temp(schedule, t0, tn, s, n_sweeps):
     return _load().or_schedule_temp(schedule, t0, tn, s, n_sweeps)
 
 
-def _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode=0):
+def _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode=0,
+            grid_levels=0):
     return SatParams(float(beta), int(bome_k), int(n_sweeps), int(moves_per_sweep), float(t0),
-                     float(tn), int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(bome_mode), 0)
+                     float(tn), int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(bome_mode),
+                     int(grid_levels))
 
 
 def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=None):
@@ -241,14 +258,15 @@ def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=Non
 
 def sat_run(pm, image, *, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn=-1.0,
             schedule=SCHED_LINEAR, t0_samples=200, seed=0, mask=None, angles=None, trace=False,
-            bome_mode=BOME_SAME_PIXEL):
+            bome_mode=BOME_SAME_PIXEL, grid_levels=0):
     """Steps 1-4 of Sec. II-A with Eqs. (6)-(7) and BoME; returns (image, stats, trace)."""
     pm_ = _f64(pm)
     img = _f64(image).copy()
     n = img.shape[0]
     g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
     m = _mask(mask, n)
-    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode)
+    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode,
+                  grid_levels)
     moves = moves_per_sweep if moves_per_sweep > 0 else (int(m.sum()) if m is not None else n * n)
     tr = np.zeros(n_sweeps * moves, dtype=TRACE_DTYPE) if trace else None
     st = SatStats()

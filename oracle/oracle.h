@@ -75,8 +75,18 @@ typedef struct {
     int32_t t0_samples;     /* Q of Eq. (8); 0 means 200 */
     uint64_t seed;          /* this chain's Philox key */
     int32_t bome_mode;      /* OR_BOME_SAME_PIXEL or OR_BOME_INDEPENDENT */
-    int32_t pad;
+    int32_t grid_levels;    /* 0: Eq. (3); L >= 2: an estimate is level floor(u L) of the grid
+                               {0, beta/(L-1), ..., beta} (for the exhaustive-search check) */
 } or_sat_params;
+
+/* Exhaustive search over every image whose pixels take the L grid values
+ * {0, beta/(L-1), ..., beta} (n*n <= 16, L^(n*n) <= 2^26 images): the least
+ * Eq. (4) cost against pm, how many images attain it (within 1e-9 of the
+ * least sum of squares, relative to max(1, sum P_m^2)), and the first such
+ * image.  The sinogram is updated along a reflected Gray order (one pixel,
+ * one level per step) through the PILA. */
+int or_exhaustive_grid(const or_geom* g, const double* pm, int32_t levels, double beta, double* min_cost,
+                       int64_t* n_min, double* argmin_image);
 
 /* Sec. III-B: every estimate at the move's one pixel, or (the paper's own
  * wording) each estimate at its own randomly chosen pixel. */

@@ -23,6 +23,7 @@
 //    (try, 0, block, 2)), single estimate, first Q with C' > C.
 #include "oracle.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -138,6 +139,18 @@ int t0_estimate(const Problem& pb, const double* image, const or_sat_params* prm
     return 0;
 }
 
+// Eq. (3): uniform on [lo, hi]; or, for the exhaustive-search check, a
+// uniformly drawn level of the grid {0, beta/(L-1), ..., beta}.
+double estimate_value(const or_sat_params* prm, double f, double lo, double hi, uint32_t word) {
+    (void)f;
+    if (prm->grid_levels >= 2) {
+        const int L = prm->grid_levels;
+        const int lev = std::min(L - 1, (int)(uniform01(word) * L));
+        return prm->beta * (double)lev / (double)(L - 1);
+    }
+    return lo + uniform01(word) * (hi - lo);
+}
+
 struct Choice {
     int cstar;
     double fbest, dfbest, sum_best, Cp_best, scale_best, gap;
@@ -155,7 +168,7 @@ Choice best_estimate(const Problem& pb, int p, double f, const uint32_t* w, cons
     sums.assign(K, 0.0);
     std::vector<double> fcs(K), scales(K), cps(K);
     for (int c = 0; c < K; ++c) {
-        fcs[c] = lo + uniform01(w[2 + c]) * (hi - lo);
+        fcs[c] = estimate_value(prm, f, lo, hi, w[2 + c]);
         sums[c] = eq7_sum(pb, p, fcs[c] - f, &scales[c]);
         cps[c] = cost_after(pb, sums[c]);
     }
@@ -202,7 +215,7 @@ IndChoice best_independent(const Problem& pb, const double* image, const uint32_
         pix[c] = estimate_pixel(pb, w, K, c);
         fs[c] = image[pix[c]];
         const double lo = std::fmax(0.0, fs[c] - prm->beta), hi = std::fmin(prm->beta, fs[c] + prm->beta);
-        fcs[c] = lo + uniform01(w[2 + c]) * (hi - lo);
+        fcs[c] = estimate_value(prm, fs[c], lo, hi, w[2 + c]);
         sums[c] = eq7_sum(pb, pix[c], fcs[c] - fs[c], &scales[c]);
         cps[c] = cost_after(pb, sums[c]);
     }
@@ -371,7 +384,7 @@ extern "C" int or_sat_lockstep(const or_geom* g, const uint8_t* mask, const doub
                 }
                 const double f = image[p];
                 const double lo = std::fmax(0.0, f - prm->beta), hi = std::fmin(prm->beta, f + prm->beta);
-                const double fc = lo + uniform01(w[2 + c]) * (hi - lo);
+                const double fc = estimate_value(prm, f, lo, hi, w[2 + c]);
                 double scale = 0.0;
                 const double sum = eq7_sum(pb, p, fc - f, &scale);
                 const double Cp = cost_after(pb, sum);
@@ -405,5 +418,90 @@ extern "C" int or_sat_lockstep(const or_geom* g, const uint8_t* mask, const doub
 done:
     r.moves = idx;
     if (rep) *rep = r;
+    return 0;
+}
+
+// ---- exhaustive search over grid-valued images -----------------------------
+
+namespace {
+
+struct Exhaustive {
+    int P = 0, L = 0, cells = 0;
+    double beta = 0.0, tol = 0.0;
+    std::vector<int32_t> bins;   // PILA [P][U][2]
+    std::vector<double> lens;
+    int U = 0, B = 0;
+    const double* pm = nullptr;
+    std::vector<double> pc;      // current projections
+    std::vector<int> lev, dir;   // current level and direction per pixel
+    double best = INFINITY;
+    int64_t count = 0;
+    std::vector<double> arg;
+
+    void change(int p, int d) {  // pixel p moves by d levels
+        const double df = beta * (double)d / (double)(L - 1);
+        for (int u = 0; u < U; ++u)
+            for (int e = 0; e < 2; ++e) {
+                const size_t q = ((size_t)p * U + u) * 2 + e;
+                if (bins[q] >= 0) pc[(size_t)u * B + bins[q]] += df * lens[q];
+            }
+        lev[p] += d;
+    }
+    void leaf() {
+        double S = 0.0;
+        for (int c = 0; c < cells; ++c) {
+            const double r = pc[c] - pm[c];
+            S += r * r;
+        }
+        if (S < best - tol) {
+            best = S;
+            count = 1;
+            for (int p = 0; p < P; ++p) arg[p] = beta * (double)lev[p] / (double)(L - 1);
+        } else if (S <= best + tol) {
+            ++count;
+        }
+    }
+    void visit(int d) {
+        if (d == P) {
+            leaf();
+            return;
+        }
+        for (int t = 0; t < L; ++t) {
+            if (t > 0) change(d, dir[d]);
+            visit(d + 1);
+        }
+        dir[d] = -dir[d];
+    }
+};
+
+}  // namespace
+
+extern "C" int or_exhaustive_grid(const or_geom* g, const double* pm, int32_t levels, double beta, double* min_cost,
+                                  int64_t* n_min, double* argmin_image) {
+    const int P = g->n * g->n;
+    if (levels < 2 || P > 16 || std::pow((double)levels, (double)P) > 67108864.0) return -2;
+    Exhaustive ex;
+    ex.P = P;
+    ex.L = levels;
+    ex.beta = beta;
+    ex.U = g->n_angles;
+    ex.B = g->n_bins;
+    ex.cells = ex.U * ex.B;
+    ex.pm = pm;
+    ex.bins.resize((size_t)P * ex.U * 2);
+    ex.lens.resize((size_t)P * ex.U * 2);
+    if (or_pila(g, ex.bins.data(), ex.lens.data()) != 0) return -1;
+    ex.pc.assign(ex.cells, 0.0);  // every pixel starts at level 0
+    ex.lev.assign(P, 0);
+    ex.dir.assign(P, 1);
+    ex.arg.assign(P, 0.0);
+    double norm = 0.0;
+    for (int c = 0; c < ex.cells; ++c) norm += pm[c] * pm[c];
+    ex.tol = 1e-9 * std::max(1.0, norm);
+    ex.visit(0);
+    if (min_cost) *min_cost = std::sqrt(ex.best / (double)ex.cells);
+    if (n_min) *n_min = ex.count;
+    if (argmin_image)
+        for (int p = 0; p < P; ++p) argmin_image[p] = ex.arg[p];
     return 0;
 }

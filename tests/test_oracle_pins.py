@@ -513,3 +513,32 @@ def test_fbp_ramlak_and_reconstruction(orc):
     dot[20, 41] = 1.0
     rd = F.fbp(orc.drt(dot, U, B), n)
     assert np.unravel_index(np.argmax(rd), rd.shape) == (20, 41)
+
+
+def test_exhaustive_search_on_4x4_grid_images(orc):
+    """Brute force on 4x4 images: every image with pixels in {0, 0.5, 1}
+    (3^16 = 43 M) is scored by Eq. (4) through a Gray-ordered sinogram
+    update.  With noiseless data of a grid phantom the least cost is 0, the
+    phantom attains it, and SAT restricted to grid values (Steps 1-4 with
+    Eq. (7), a slow schedule) ends at a global minimiser."""
+    n, U, L = 4, 4, 3
+    B = synth.bins_for(n)
+    ph = np.array([[0.0, 0.5, 1.0, 0.5], [1.0, 0.0, 0.5, 0.0], [0.5, 1.0, 0.0, 1.0], [0.0, 0.5, 0.5, 1.0]])
+    pm = orc.drt(ph, U, B)
+    cmin, count, arg = orc.exhaustive_grid(pm, n, L, 1.0)
+    assert cmin < 1e-9 and count >= 1
+    assert orc.cost(orc.drt(arg, U, B), pm) < 1e-9
+    # a wrong image is measurably worse: the grid search is not degenerate
+    worse = ph.copy()
+    worse[0, 0] = 1.0
+    assert orc.cost(orc.drt(worse, U, B), pm) > 1e-3
+    # SAT never beats the exhaustive minimum and, being stochastic, reaches
+    # it in most runs (single-pixel moves can stall in a local minimum)
+    reached = 0
+    for seed in range(16):
+        img, st, _ = orc.sat_run(pm, np.full((n, n), 0.5), bome_k=1, n_sweeps=2000, moves_per_sweep=16, t0=5e-2,
+                                 tn=1e-5, seed=seed, grid_levels=L)
+        assert st["final_cost_fresh"] >= cmin - 1e-9
+        assert set(np.round(img.ravel() * 2).astype(int)) <= {0, 1, 2}
+        reached += st["final_cost_fresh"] <= cmin + 1e-9
+    assert reached >= 8
