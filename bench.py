@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 from paper_1411_4622_gb300 import shard, synth  # noqa: E402
 
 WORKLOAD = "batch128x512"
+PLAN_NAMES = {0: "rules", 1: "autotuned: windowed, band residual in shared memory",
+              2: "autotuned: windowed, residual in global memory", 3: "autotuned: windowed hybrid",
+              4: "autotuned: pipelined, 1 warp per chain", 5: "autotuned: pipelined, 2 warps per chain",
+              6: "autotuned: pipelined, 4 warps per chain"}
 METRIC = "SAT pixel-moves/s at equal final RMSE (batched vs plain); slice p50/p99 ms"
 UNIT = "pixel-moves/s"
 
@@ -49,7 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
-    ap.add_argument("--flags", type=int, default=0, help="SAT_FLAG_* bits for the batched run")
+    ap.add_argument("--flags", type=int, default=2,
+                    help="SAT_FLAG_* bits for the batched run (default 2: the autotuner picks the launch layout)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt", "fbp"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
                          "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
@@ -791,7 +796,8 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "slices_per_gpu": slices, "n": n, "angles": U, "bins": B,
                       "bome_k": K, "stages": S, "moves_per_stage": M, "pila": args.pila,
-                      "l2": "flushed between timed steps (256 MB write)"},
+                      "l2": "flushed between timed steps (256 MB write)",
+                      "launch": PLAN_NAMES.get(st[0]["plan"], str(st[0]["plan"])), "graph": True},
            "evaluations_per_s": value * K, "acceptance": acc,
            "rmse": {"batched_mean": float(rmse_batched.mean())}, "plain": plain,
            "latency_ms": {"slice_p50": float(np.percentile(step_ms, 50)),
