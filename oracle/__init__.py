@@ -24,6 +24,7 @@ _lib = None
 SCHED_LINEAR, SCHED_GEOMETRIC, SCHED_CUBIC = 0, 1, 2
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 BOME_SAME_PIXEL, BOME_INDEPENDENT = 0, 1
+LEN_EXACT, LEN_BINARY16, LEN_BYTE180 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -50,7 +51,7 @@ class SatParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("bome_k", C.c_int32), ("n_sweeps", C.c_int32),
                 ("moves_per_sweep", C.c_int32), ("t0", C.c_double), ("tn", C.c_double),
                 ("schedule", C.c_int32), ("t0_samples", C.c_int32), ("seed", C.c_uint64),
-                ("bome_mode", C.c_int32), ("grid_levels", C.c_int32)]
+                ("bome_mode", C.c_int32), ("grid_levels", C.c_int32), ("length_format", C.c_int32)]
 
 
 class SatStats(C.Structure):
@@ -88,6 +89,8 @@ def _load():
             lib.or_cost.argtypes = [C.c_int32, C.c_int32, P, P]
             lib.or_cost.restype = C.c_double
             lib.or_sirt_factor.argtypes = [C.POINTER(Geom), P, P]
+            lib.or_round_length.argtypes = [C.c_int32, C.c_double]
+            lib.or_round_length.restype = C.c_double
             lib.or_schedule_temp.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32]
             lib.or_schedule_temp.restype = C.c_double
             lib.or_sat_t0.argtypes = [C.POINTER(Geom), P, P, P, C.POINTER(SatParams), P, P]
@@ -235,18 +238,23 @@ def schedule_temp(schedule, t0, tn, s, n_sweeps):
 
 
 def _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode=0,
-            grid_levels=0):
+            grid_levels=0, length_format=0):
     return SatParams(float(beta), int(bome_k), int(n_sweeps), int(moves_per_sweep), float(t0),
                      float(tn), int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(bome_mode),
-                     int(grid_levels))
+                     int(grid_levels), int(length_format))
 
 
-def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=None):
+def round_length(fmt: int, l: float) -> float:
+    """A PILA length as stored in format fmt (LEN_EXACT, LEN_BINARY16, LEN_BYTE180)."""
+    return _load().or_round_length(int(fmt), float(l))
+
+
+def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=None, length_format=0):
     """Eq. (8): initial temperature from Q uphill proposals on the initial image."""
     pm_, img = _f64(pm), _f64(image)
     n = img.shape[0]
     g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
-    prm = _params(beta, 1, 0, 0, 0.0, -1.0, 0, t0_samples, seed)
+    prm = _params(beta, 1, 0, 0, 0.0, -1.0, 0, t0_samples, seed, length_format=length_format)
     t0 = C.c_double(0.0)
     found = C.c_int32(0)
     rc = _load().or_sat_t0(C.byref(g), _ptr(_mask(mask, n)), _ptr(pm_), _ptr(img), C.byref(prm),
@@ -258,15 +266,16 @@ def sat_t0(pm, image, *, beta=1.0, seed=0, t0_samples=200, mask=None, angles=Non
 
 def sat_run(pm, image, *, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn=-1.0,
             schedule=SCHED_LINEAR, t0_samples=200, seed=0, mask=None, angles=None, trace=False,
-            bome_mode=BOME_SAME_PIXEL, grid_levels=0):
-    """Steps 1-4 of Sec. II-A with Eqs. (6)-(7) and BoME; returns (image, stats, trace)."""
+            bome_mode=BOME_SAME_PIXEL, grid_levels=0, length_format=0):
+    """Steps 1-4 of Sec. II-A with Eqs. (6)-(7) and BoME; returns (image, stats, trace).
+    length_format: the PILA's stored lengths (LEN_EXACT, LEN_BINARY16, LEN_BYTE180)."""
     pm_ = _f64(pm)
     img = _f64(image).copy()
     n = img.shape[0]
     g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
     m = _mask(mask, n)
     prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, t0_samples, seed, bome_mode,
-                  grid_levels)
+                  grid_levels, length_format)
     moves = moves_per_sweep if moves_per_sweep > 0 else (int(m.sum()) if m is not None else n * n)
     tr = np.zeros(n_sweeps * moves, dtype=TRACE_DTYPE) if trace else None
     st = SatStats()
@@ -279,13 +288,15 @@ def sat_run(pm, image, *, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=
 
 
 def sat_lockstep(pm, image, gpu_trace, *, t0, tn, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0,
-                 schedule=SCHED_LINEAR, seed=0, mask=None, angles=None, tol=1e-5, bome_mode=BOME_SAME_PIXEL):
+                 schedule=SCHED_LINEAR, seed=0, mask=None, angles=None, tol=1e-5, bome_mode=BOME_SAME_PIXEL,
+                 length_format=0):
     """Follow another implementation's move trace in FP64 (near-tie protocol)."""
     pm_ = _f64(pm)
     img = _f64(image).copy()
     n = img.shape[0]
     g, keep = _geom(n, pm_.shape[0], pm_.shape[1], angles)
-    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, 200, seed, bome_mode)
+    prm = _params(beta, bome_k, n_sweeps, moves_per_sweep, t0, tn, schedule, 200, seed, bome_mode,
+                  length_format=length_format)
     tr = np.ascontiguousarray(gpu_trace, dtype=GPU_TRACE_DTYPE)
     rep = LockstepReport()
     rc = _load().or_sat_lockstep(C.byref(g), _ptr(_mask(mask, n)), _ptr(pm_), _ptr(img), C.byref(prm),

@@ -77,7 +77,18 @@ typedef struct {
     int32_t bome_mode;      /* OR_BOME_SAME_PIXEL or OR_BOME_INDEPENDENT */
     int32_t grid_levels;    /* 0: Eq. (3); L >= 2: an estimate is level floor(u L) of the grid
                                {0, beta/(L-1), ..., beta} (for the exhaustive-search check) */
+    int32_t length_format;  /* OR_LEN_*: how the PILA stores its lengths (Sec. II-B); with a
+                               rounded format the initial and final projections are sums over
+                               the rounded table, so the whole run sees one set of lengths */
 } or_sat_params;
+
+/* Stored PILA lengths (Sec. II-B keeps them in reduced precision): exact FP64;
+ * IEEE binary16 (round to nearest, ties to even; 11 significant bits,
+ * subnormal quantum 2^-24); one byte, round(180 l) / 180 (ties to even). */
+enum { OR_LEN_EXACT = 0, OR_LEN_BINARY16 = 1, OR_LEN_BYTE180 = 2 };
+
+/* A length l >= 0 as the given format stores it. */
+double or_round_length(int32_t format, double l);
 
 /* Exhaustive search over every image whose pixels take the L grid values
  * {0, beta/(L-1), ..., beta} (n*n <= 16, L^(n*n) <= 2^26 images): the least

@@ -54,9 +54,23 @@ struct Problem {
     std::vector<int32_t> list;   // pixels that may be chosen
     double inv_BU = 0.0;
     double C = 0.0;              // current cost, Eq. (4)
+    int32_t format = OR_LEN_EXACT;
 };
 
-int setup(Problem& pb, const or_geom* g, const uint8_t* mask, const double* pm, const double* image) {
+// Projections of image through the table: sum_p f_p l(p, u, k).
+void table_projection(const Problem& pb, const double* image, double* out) {
+    std::fill(out, out + (size_t)pb.U * pb.B, 0.0);
+    const size_t P = (size_t)pb.n * pb.n;
+    for (size_t p = 0; p < P; ++p)
+        for (int u = 0; u < pb.U; ++u)
+            for (int slot = 0; slot < 2; ++slot) {
+                const size_t e = (p * pb.U + u) * 2 + slot;
+                if (pb.lens[e] != 0.0) out[(size_t)u * pb.B + pb.bins[e]] += image[p] * pb.lens[e];
+            }
+}
+
+int setup(Problem& pb, const or_geom* g, const uint8_t* mask, const double* pm, const double* image,
+          int32_t length_format) {
     pb.n = g->n;
     pb.U = g->n_angles;
     pb.B = g->n_bins;
@@ -64,8 +78,15 @@ int setup(Problem& pb, const or_geom* g, const uint8_t* mask, const double* pm, 
     pb.bins.assign(P * pb.U * 2, -1);
     pb.lens.assign(P * pb.U * 2, 0.0);
     if (or_pila(g, pb.bins.data(), pb.lens.data()) != 0) return -1;
+    pb.format = length_format;
     pb.pc.assign((size_t)pb.U * pb.B, 0.0);
-    if (or_drt(g, image, pb.pc.data()) != 0) return -1;  // initial projections by the DRT
+    if (length_format == OR_LEN_EXACT) {
+        if (or_drt(g, image, pb.pc.data()) != 0) return -1;  // initial projections by the DRT
+    } else {
+        if (length_format != OR_LEN_BINARY16 && length_format != OR_LEN_BYTE180) return -1;
+        for (size_t e = 0; e < pb.lens.size(); ++e) pb.lens[e] = or_round_length(length_format, pb.lens[e]);
+        table_projection(pb, image, pb.pc.data());  // the same projections through the stored table
+    }
     pb.pm = pm;
     pb.list.clear();
     for (size_t p = 0; p < P; ++p)
@@ -234,6 +255,15 @@ IndChoice best_independent(const Problem& pb, const double* image, const uint32_
 
 }  // namespace
 
+extern "C" double or_round_length(int32_t format, double l) {
+    if (format == OR_LEN_BYTE180) return std::nearbyint(l * 180.0) / 180.0;
+    if (format != OR_LEN_BINARY16 || l == 0.0) return l;
+    int e;
+    std::frexp(l, &e);                                  // 2^(e-1) <= l < 2^e
+    const double q = std::ldexp(1.0, std::max(e - 11, -24));  // 11 significant bits; subnormal quantum 2^-24
+    return std::nearbyint(l / q) * q;
+}
+
 extern "C" double or_schedule_temp(int32_t schedule, double t0, double tn, int32_t s, int32_t n_sweeps) {
     const double N = (double)n_sweeps, n = (double)s;
     switch (schedule) {
@@ -250,7 +280,7 @@ extern "C" double or_schedule_temp(int32_t schedule, double t0, double tn, int32
 extern "C" int or_sat_t0(const or_geom* g, const uint8_t* mask, const double* pm, const double* image,
                          const or_sat_params* prm, double* t0_out, int32_t* found_out) {
     Problem pb;
-    if (setup(pb, g, mask, pm, image) != 0) return -1;
+    if (setup(pb, g, mask, pm, image, prm->length_format) != 0) return -1;
     return t0_estimate(pb, image, prm, t0_out, found_out);
 }
 
@@ -258,7 +288,7 @@ extern "C" int or_sat_run(const or_geom* g, const uint8_t* mask, const double* p
                           const or_sat_params* prm, or_sat_stats* stats, or_trace_rec* trace) {
     if (prm->bome_k < 1 || prm->bome_k > 32 || prm->n_sweeps < 0) return -2;
     Problem pb;
-    if (setup(pb, g, mask, pm, image) != 0) return -1;
+    if (setup(pb, g, mask, pm, image, prm->length_format) != 0) return -1;
     or_sat_stats st;
     std::memset(&st, 0, sizeof(st));
     st.initial_cost = pb.C;
@@ -320,7 +350,11 @@ extern "C" int or_sat_run(const or_geom* g, const uint8_t* mask, const double* p
     }
     st.final_cost = pb.C;
     std::vector<double> fresh((size_t)pb.U * pb.B);
-    if (or_drt(g, image, fresh.data()) != 0) return -1;
+    if (pb.format == OR_LEN_EXACT) {
+        if (or_drt(g, image, fresh.data()) != 0) return -1;
+    } else {
+        table_projection(pb, image, fresh.data());
+    }
     st.final_cost_fresh = or_cost(pb.U, pb.B, fresh.data(), pm);
     if (stats) *stats = st;
     return 0;
@@ -331,7 +365,7 @@ extern "C" int or_sat_lockstep(const or_geom* g, const uint8_t* mask, const doub
                                int64_t n_moves, double tol, or_lockstep_report* rep) {
     if (prm->bome_k < 1 || prm->bome_k > 32) return -2;
     Problem pb;
-    if (setup(pb, g, mask, pm, image) != 0) return -1;
+    if (setup(pb, g, mask, pm, image, prm->length_format) != 0) return -1;
     or_lockstep_report r;
     r.moves = 0;
     r.near_ties = 0;

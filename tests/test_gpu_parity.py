@@ -389,6 +389,60 @@ def test_sirt_vs_oracle(api, mode):
     api.pila_free(p)
 
 
+def test_batched_workload_full_size_sampled_chains(api):
+    """The batched workload at full size, in the launch the benchmark times:
+    512 chains of 128^2 slices (disk space, 120 angles, 181 bins), K = 4,
+    T0 by Eq. (8), the 50-stage linear schedule, the FP16 table and the
+    autotuned layout.  A sampled chain is traced and followed move by move,
+    all 644,600 moves, by the oracle over the same binary16 lengths, with T0
+    checked against the oracle's Eq. (8); for sampled chains the reported
+    final cost equals the oracle's Eq. (4) cost of the returned image through
+    the rounded table, and the running FP32 cost stays within 1e-4 of it."""
+    cfg = synth.WORKLOADS["batch128x512"]
+    n, U, B, K, S, C = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"], cfg["slices"]
+    mask = synth.disk_mask(n)
+    M = int(mask.sum())
+    distinct = 8
+    phs = [synth.phantom(n, cfg["ellipses"], synth.slice_seeds(i)[0]) * mask for i in range(distinct)]
+    sinos = np.stack([oracle.drt(ph, U, B) for ph in phs]).astype(np.float32)
+    img0 = synth.initial_image(n, 0.5, mask).astype(np.float32)
+    seed0 = synth.slice_seeds(0)[2]
+    traced = int(np.random.default_rng(11).integers(C))
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    imgs = dev(np.broadcast_to(img0, (C, n, n)))
+    trace = torch.zeros(S * M * api.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    st = api.sat_run(p, dev(sinos[np.arange(C) % distinct]), imgs, bome_k=K, n_sweeps=S, t0=cfg["t0"],
+                     tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0, flags=api.SAT_FLAG_AUTOTUNE,
+                     trace_chain=traced, trace=trace)
+    api.pila_free(p)
+    assert all(s["status"] == 0 and s["proposed"] == S * M for s in st)
+    assert st[0]["plan"] == api.SAT_PLAN_WINDOW_SMEM
+    final = imgs.cpu().numpy()
+    tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
+    pm = sinos[traced % distinct]
+    t0, found = oracle.sat_t0(pm, img0, seed=seed0 + traced, mask=mask, length_format=oracle.LEN_BINARY16)
+    assert found == st[traced]["t0_found"] == 200
+    assert abs(st[traced]["t0"] - t0) <= 1e-4 * t0
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st[traced]["t0"], tn=st[traced]["tn"], bome_k=K, n_sweeps=S,
+                                 seed=seed0 + traced, mask=mask, length_format=oracle.LEN_BINARY16)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5, rep
+    assert rep["near_ties"] <= 1e-3 * S * M, rep
+    bins, lens = oracle.pila(n, U, B)
+    l16 = lens.astype(np.float16).astype(np.float64)
+    ok = l16 > 0
+    pix = np.broadcast_to(np.arange(n * n)[:, None, None], l16.shape)[ok]
+    ang = np.broadcast_to(np.arange(U)[None, :, None], l16.shape)[ok]
+    for c in sorted({0, C // 2, C - 1, traced}):
+        proj = np.zeros((U, B))
+        np.add.at(proj, (ang, bins[ok]), final[c].astype(np.float64).ravel()[pix] * l16[ok])
+        cost = math.sqrt(np.mean((proj - sinos[c % distinct]) ** 2))
+        assert abs(st[c]["final_cost"] - cost) <= 1e-9 * cost, (c, st[c]["final_cost"], cost)
+        assert abs(st[c]["final_cost_incremental"] - cost) <= 1e-4 * cost
+        assert np.all(final[c][mask == 0] == 0.0) and final[c].min() >= 0.0 and final[c].max() <= cfg["beta"]
+
+
 def test_resync_drift_bound_512(api):
     """One stage of the 512^2 precision workload shape (360 angles, 725
     bins, Poisson noise) with the residual in global memory: the

@@ -287,6 +287,49 @@ def test_incremental_state_matches_fresh_drt(orc):
     assert img.min() >= 0.0 and img.max() <= 1.0
 
 
+def test_stored_length_formats(orc):
+    """Sec. II-B stores the PILA's lengths in reduced precision.  binary16
+    rounding equals numpy's float64 -> float16 cast (ties to even, the
+    subnormal range included); one-byte lengths are the nearest multiple of
+    1/180.  A run over a rounded table keeps its projections as sums over
+    that table: its initial and final Eq. (4) costs equal numpy's sums over
+    the numpy-rounded lengths."""
+    n, U = 16, 20
+    ph, B, _ = _small_problem(n, U)
+    bins, lens = orc.pila(n, U, B)
+    special = [0.0, 2.0 ** -25, 2.0 ** -24, 3 * 2.0 ** -25, 5 * 2.0 ** -25, 2.0 ** -14 - 2.0 ** -25,
+               2.0 ** -14, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, math.sqrt(2.0), 1e-7, 0.123456789]
+    vals = np.concatenate([lens.ravel()[::7], np.array(special),
+                           np.random.default_rng(5).uniform(0.0, 1.5, 2000)])
+    got16 = np.array([orc.round_length(orc.LEN_BINARY16, v) for v in vals])
+    assert np.array_equal(got16, vals.astype(np.float16).astype(np.float64))
+    got8 = np.array([orc.round_length(orc.LEN_BYTE180, v) for v in vals])
+    q = got8 * 180.0
+    assert np.all(np.abs(q - np.round(q)) < 1e-9) and np.all(np.abs(got8 - vals) <= 0.5 / 180 + 1e-12)
+    assert orc.round_length(orc.LEN_EXACT, 0.3) == 0.3
+    pm = synth.gaussian_noise(orc.drt(ph, U, B), 0.01, 4)
+    img0 = np.full((n, n), 0.5)
+    for fmt, cast in ((orc.LEN_BINARY16, lambda a: a.astype(np.float16).astype(np.float64)),
+                      (orc.LEN_BYTE180, lambda a: np.round(a * 180.0) / 180.0)):
+        rl = cast(lens)
+
+        def project(x):
+            out = np.zeros((U, B))
+            ok = rl > 0
+            pix = np.broadcast_to(np.arange(n * n)[:, None, None], rl.shape)
+            ang = np.broadcast_to(np.arange(U)[None, :, None], rl.shape)
+            np.add.at(out, (ang[ok], bins[ok]), x.ravel()[pix[ok]] * rl[ok])
+            return out
+
+        img, st, _ = orc.sat_run(pm, img0, bome_k=4, n_sweeps=3, seed=9, length_format=fmt)
+        c0 = math.sqrt(np.mean((project(img0) - pm) ** 2))
+        c1 = math.sqrt(np.mean((project(img) - pm) ** 2))
+        assert abs(st["initial_cost"] - c0) <= 1e-12 * c0
+        assert abs(st["final_cost_fresh"] - c1) <= 1e-12 * c1
+        assert abs(st["final_cost"] - c1) <= 1e-10 * c1
+        assert 0 < st["accepted"] < st["proposed"]
+
+
 def test_metropolis_stationary_distribution(orc):
     """One pixel, fixed T, one estimate: proposals are uniform on [0, beta]
     and independent of the state, so Step 4 makes the chain sample the
