@@ -224,9 +224,9 @@ class OraclePool:
         self.pool = mp.get_context("spawn").Pool(self.procs)
         self.run(0)  # import the oracle and set up every worker's slice
 
-    def run(self, stages):
-        """All workers run their slice for `stages` stages; (moves, wall s)."""
-        jobs = [(self.cfg, i, stages) for i in range(self.procs)]
+    def run(self, stages, per_proc=1):
+        """per_proc x procs slices, each run for `stages` stages; (moves, wall s)."""
+        jobs = [(self.cfg, i, stages) for i in range(self.procs * per_proc)]
         t = time.perf_counter()
         res = self.pool.map(_oracle_slice, jobs, chunksize=1)
         return sum(r[0] for r in res), time.perf_counter() - t
@@ -236,27 +236,30 @@ class OraclePool:
         self.pool.join()
 
 
-def oracle_stages_for(cfg, budget_s):
-    """Stages of one slice that take the oracle about budget_s on one core:
+def oracle_slices_for(cfg, budget_s):
+    """Whole-schedule slices per core that take the oracle about budget_s:
     per-stage time from a 1-stage and a 3-stage run (setup cancels)."""
     t1 = _oracle_slice((cfg, 0, 1))[1]
     t3 = _oracle_slice((cfg, 0, 3))[1]
     per = max((t3 - t1) / 2.0, 1e-4)
-    return int(max(1, min(cfg["n_sweeps"] * 4, budget_s / per)))
+    return int(max(1, min(16, round(budget_s / (per * cfg["n_sweeps"])))))
 
 
 def cpu_baseline(cfg, budget_s=12.0):
     """The FP64 oracle as it stands (single-threaded per process), one process
-    per host core, each on its own slice of the workload for about budget_s."""
-    stages = oracle_stages_for(cfg, budget_s)
+    per host core, on distinct slices of the workload, each annealed over the
+    workload's whole schedule, about budget_s in all."""
+    per_proc = oracle_slices_for(cfg, budget_s)
+    stages = cfg["n_sweeps"]
     pool = OraclePool(cfg)
     try:
-        moves, wall = pool.run(stages)
+        moves, wall = pool.run(stages, per_proc)
     finally:
         pool.close()
+    count = pool.procs * per_proc
     return {"value": moves / wall, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
-            "sample": f"{pool.procs} slices of {WORKLOAD} (one per process), {stages} stages x "
-                      f"{moves // max(1, stages * pool.procs)} moves each, K={cfg['bome_k']}, FP64, "
+            "sample": f"{count} slices of {WORKLOAD} ({per_proc} per process), {stages} stages x "
+                      f"{moves // max(1, stages * count)} moves each, K={cfg['bome_k']}, FP64, "
                       f"{wall:.1f} s wall"}
 
 

@@ -264,7 +264,8 @@ def test_sat_final_rmse_plain64_vs_oracle(api):
 def test_sat_u8_table(api):
     """The one-byte table of Sec. II-B (lengths q / 180): its forward
     projection is the exact sum of its stored lengths, the windowed kernel
-    gives the same chain whichever memory holds the residual, and the final
+    gives the same chain whichever memory holds the residual, follows the
+    oracle move by move over the same one-byte lengths, and the final
     RMSE of the 128^2 / 120-angle slice stays within 5% of the FP64 oracle's
     (exact lengths); the FP16 table's is within 2% (next test)."""
     n, U, B = 128, 120, 181
@@ -291,6 +292,19 @@ def test_sat_u8_table(api):
         assert st[0]["status"] == 0
         outs.append(img.cpu().numpy()[0])
     assert np.array_equal(outs[0], outs[1])
+    # move by move against the oracle over the same one-byte lengths
+    S, M = kw["n_sweeps"], int(mask.sum())
+    st, tr, img = _run_traced(api, p, pm.astype(np.float32), img0, S, M, residency=api.SAT_RESIDENT_SMEM, **{
+        k: v for k, v in kw.items() if k != "n_sweeps"})
+    assert np.array_equal(img, outs[0])
+    t0, found = oracle.sat_t0(pm.astype(np.float32), img0, seed=kw["seed"], mask=mask,
+                              length_format=oracle.LEN_BYTE180)
+    assert found == st["t0_found"] == 200 and abs(st["t0"] - t0) <= 1e-4 * t0
+    _, rep = oracle.sat_lockstep(pm.astype(np.float32), img0, tr, t0=st["t0"], tn=st["tn"], bome_k=4, n_sweeps=S,
+                                 seed=kw["seed"], mask=mask, length_format=oracle.LEN_BYTE180)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5, rep
     oimg, ost, _ = oracle.sat_run(pm, img0, mask=mask, **kw)
     r_gpu, r_orc = synth.rmse(outs[0], ph, mask), synth.rmse(oimg, ph, mask)
     assert abs(r_gpu - r_orc) <= 0.05 * r_orc, (r_gpu, r_orc)
