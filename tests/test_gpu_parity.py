@@ -529,6 +529,63 @@ def test_window_band_residual_off_centre_mask(api):
         api.pila_free(p)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_window_pixel_repeats_and_ragged_last_window(api, prec):
+    """A reconstruction space of two adjacent pixels makes the two moves of a
+    window draw the same pixel about half the time (the windowed kernel then
+    recomputes the later move's candidates after the earlier decision) and
+    their footprints share cells at every angle; an odd number of moves per
+    stage leaves a ragged last window.  Both residencies follow the oracle
+    move by move (the FP16 table over binary16 lengths)."""
+    n, U = 24, 30
+    B = synth.bins_for(n)
+    mask = np.zeros((n, n), np.uint8)
+    mask[11, 12] = mask[12, 12] = 1
+    pm = oracle.drt(synth.phantom(n, 4, 1004), U, B).astype(np.float32)
+    img0 = np.where(mask > 0, 0.5, 0.0)
+    S, M = 3, 401
+    fmt = oracle.LEN_EXACT if prec == api.PILA_F32 else oracle.LEN_BINARY16
+    p = api.pila_build(n, U, B, prec, mask=mask)
+    imgs = []
+    for res in (api.SAT_RESIDENT_SMEM, api.SAT_RESIDENT_GLOBAL):
+        st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=4, t0=1e-3, tn=1e-5, seed=3004,
+                                  moves_per_sweep=M, residency=res, group_warps=1)
+        assert st["status"] == 0 and st["proposed"] == S * M
+        pix = tr["pixel"].reshape(S, M)[:, :M - 1].reshape(S, -1, 2)
+        assert np.mean(pix[..., 0] == pix[..., 1]) > 0.3
+        _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=4, n_sweeps=S, seed=3004,
+                                     moves_per_sweep=M, mask=mask, length_format=fmt)
+        assert rep["moves"] == S * M
+        assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+        assert rep["max_err_dS"] <= 1e-5, rep
+        imgs.append(img)
+    assert np.array_equal(imgs[0], imgs[1])
+    assert np.all(imgs[0][mask == 0] == 0.0)
+    api.pila_free(p)
+
+
+@pytest.mark.parametrize("U", [128, 129])
+def test_window_angle_limit(api, U):
+    """128 angles fill every record slot of a windowed warp's lanes (4 per
+    lane); at 129 the rules fall back to the pipelined kernel.  Both follow
+    the oracle move by move."""
+    n = 32
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    pm = oracle.drt(synth.phantom(n, 5, 1005), U, B).astype(np.float32)
+    img0 = synth.initial_image(n, 0.5, mask)
+    S, M = 2, int(mask.sum())
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=4, t0=-1.0, tn=-1.0, seed=3005, group_warps=1)
+    assert st["status"] == 0 and st["proposed"] == S * M
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=4, n_sweeps=S, seed=3005,
+                                 mask=mask)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5, rep
+    api.pila_free(p)
+
+
 def test_hybrid_batch_matches_single_chains(api):
     """More chains than shared-memory slots: the batch runs on shared-memory
     and global-memory warps side by side, with chains moving between them
