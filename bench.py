@@ -55,11 +55,13 @@ def parse():
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     ap.add_argument("--flags", type=int, default=2,
                     help="SAT_FLAG_* bits for the batched run (default 2: the autotuner picks the launch layout)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt", "fbp"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt", "fbp", "rows"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
                          "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
                          "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A); "
-                         "fbp: FBP against SAT with and without the FBP spatial constraint (Fig. 9)")
+                         "fbp: FBP against SAT with and without the FBP spatial constraint (Fig. 9); "
+                         "rows: the other steps of the path (table build, forward projection, SIRT, one chain), "
+                         "each timed alone")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
                     help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
@@ -618,6 +620,132 @@ def run_drt(args):
     print(json.dumps(out))
 
 
+def _timed_call(fn, reps, flush):
+    """Mean ms of fn() over reps calls, CUDA events on the current stream, L2
+    flushed (256 MB write) before each; one untimed call first."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
+def run_rows(args):
+    """The steps of the path besides the move, each timed alone through its
+    C-ABI call (inputs resident in HBM, L2 flushed before each call), with the
+    algorithmic bytes each must move against the measured HBM copy bandwidth:
+      a0 PILA build: the table, the per-pixel sums and the band written once;
+      a7 forward projection (the resync): the table read once, the images read
+         and the FP64 projections written;
+      a9 SIRT, simultaneous: per iteration the table read twice (forward and
+         back projection) plus the sinogram, the factor matrix, the correction
+         and the image;
+      one 256^2 chain (K = 8): a single chain is sequential, so it is reported
+         as time per stage and moves/s."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    peak, peak_kind = peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    reps = max(1, args.steps)
+    rows = []
+
+    def add(row, cfg, ms, algo_bytes, unit_count=None, unit=None):
+        gbs = algo_bytes / (ms / 1e3) / 1e9
+        r = {"row": row, "config": cfg, "ms": ms, "algorithmic_bytes": algo_bytes, "achieved_gbs": gbs,
+             "peak_gbs": peak, "frac": gbs / peak}
+        if unit_count is not None:
+            r["rate"] = unit_count / (ms / 1e3)
+            r["rate_unit"] = unit
+        rows.append(r)
+
+    geoms = {"batch128x512": (128, 120, 181, 512), "precision512": (512, 360, 725, 304)}
+    for name, (n, U, B, C) in geoms.items():
+        C = args.slices or C
+        mask = synth.disk_mask(n)
+        holder = {}
+
+        def build():
+            if "p" in holder:
+                api.pila_free(holder.pop("p"))
+            holder["p"] = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+
+        ms = _timed_call(build, reps, flush)
+        info = api.pila_info(holder["p"])
+        P = n * n
+        table = info["table_bytes"]
+        add("a0 PILA build (FP16)", f"{name}: {n}^2, {U} angles, {B} bins", ms, table + 4 * P,
+            P * U, "records/s")
+        ph = np.stack([synth.phantom(n, 20, synth.slice_seeds(i)[0]) * mask for i in range(8)])
+        imgs = torch.tensor(ph[np.arange(C) % 8], dtype=torch.float32, device="cuda").contiguous()
+        out = torch.empty((C, U, B), dtype=torch.float64, device="cuda")
+        ms = _timed_call(lambda: api.pila_forward(holder["p"], imgs, out=out), reps, flush)
+        terms = C * info["entries"]
+        add("a7 forward projection (FP16 table, exact fixed-point sums)", f"{name}: {C} images", ms,
+            table + C * (4 * P + 8 * U * B), terms, "terms/s")
+        api.pila_free(holder.pop("p"))
+        del imgs, out
+
+    # a9 SIRT and one chain at 256^2, 180 angles, 363 bins (the SAT+SIRT configuration)
+    cfg = synth.WORKLOADS["sat256"]
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, cfg["ellipses"], synth.slice_seeds(0)[0]) * mask
+    pf = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    clean = api.pila_forward(pf, torch.tensor(ph[None], dtype=torch.float32, device="cuda")).cpu().numpy()[0]
+    sino = torch.tensor(synth.gaussian_noise(clean, cfg["noise"][1], synth.slice_seeds(0)[1])[None],
+                        dtype=torch.float32, device="cuda").contiguous()
+    init = torch.tensor(synth.initial_image(n, 0.5, mask)[None], dtype=torch.float32, device="cuda")
+    iters = cfg["sirt_iters"]
+    sirt = {}
+    for prec, label in ((api.PILA_F32, "FP32"), (api.PILA_F16, "FP16")):
+        p = pf if prec == api.PILA_F32 else api.pila_build(n, U, B, prec, mask=mask)
+        info = api.pila_info(p)
+        img = init.clone()
+        api.sirt_run(p, sino, img, n_iter=1)  # the factor matrix, cached with the table
+        ms = _timed_call(lambda: (img.copy_(init), api.sirt_run(p, sino, img, n_iter=iters)), reps, flush)
+        table = info["table_bytes"]
+        per_iter = 2 * table + U * B * (4 + 4 + 4) + 8 * n * n
+        add(f"a9 SIRT, simultaneous ({label} table)", f"sat256: {n}^2, {U} angles, {B} bins, {iters} iterations",
+            ms, iters * per_iter, iters, "iterations/s")
+        sirt[label] = iters / (ms / 1e3)
+        if p is not pf:
+            api.pila_free(p)
+    stages = args.sweeps or 10
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    img = init.clone()
+    kw = dict(bome_k=cfg["bome_k"], n_sweeps=stages, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2],
+              flags=api.SAT_FLAG_AUTOTUNE)
+    st = api.sat_run(p, sino, img, **kw)
+    M = int(mask.sum())
+    chain = {"stages": stages, "moves_per_stage": M, "sweep_ms": st[0]["sweep_ms"],
+             "ms_per_stage": st[0]["sweep_ms"] / stages, "moves_per_s": stages * M / (st[0]["sweep_ms"] / 1e3),
+             "launch": PLAN_NAMES.get(st[0]["plan"], str(st[0]["plan"])), "bome_k": cfg["bome_k"], "pila": "f16"}
+    api.pila_free(p)
+    api.pila_free(pf)
+    out = {"metric": "SIRT-PILA iterations/s, 256x256 slice (180 angles, FP32 table)", "value": sirt["FP32"],
+           "unit": "iterations/s", "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": 1e3 / sirt["FP32"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "rows", "l2": "flushed before each timed call (256 MB write)",
+                      "peak_kind": peak_kind},
+           "rows": rows, "chain256": chain}
+    print(json.dumps(out))
+
+
 def run_fbp(args):
     """Fig. 9 on synthetic phantoms: 16 slices of 128x128 whose ellipses sit
     off the centre of rotation, noiseless; FBP (Ram-Lak) at 90 and 200
@@ -685,6 +813,8 @@ def main():
         return run_drt(args)
     if args.workload == "fbp":
         return run_fbp(args)
+    if args.workload == "rows":
+        return run_rows(args)
     cfg = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -76,7 +76,7 @@ typedef struct {
 typedef struct {
     int32_t n, n_angles, n_bins, precision;
     int32_t n_mask;        /* pixels in the reconstruction space */
-    int32_t record_bytes;  /* 16 or 8 */
+    int32_t record_bytes;  /* 16, 8 or 4 */
     int32_t row_records;   /* records stored per pixel (U, or U rounded up to even for F16) */
     int32_t pad;
     int64_t table_bytes;   /* device bytes of the record table */

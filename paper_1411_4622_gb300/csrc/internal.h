@@ -62,7 +62,8 @@ struct ProjArgs {
     int f16;                    // table precision (PILA_F32, PILA_F16, PILA_U8)
     int row_records;
     int n, U, B;
-    int angles_per_group, n_groups;
+    int angles_per_group, n_groups;  // set by launch_projector from the plan
+    int lanes_log2;             // narrow groups: log2 of the angles per group; -1: wide groups
     int mode;
     int drift;                  // RESYNC: compare with the residual being replaced
     const float* img;           // FORWARD/RESYNC/SIRT images
@@ -77,17 +78,22 @@ struct ProjArgs {
     long long resid_stride;
     int resid_pitch;            // row pitch of resid (B when 0)
     const float* w;             // SIRT: factor matrix (float)
-    double* part_sq;            // [item][group] sum of (P_c - P_m)^2
-    float* part_drift;          // [item][group]
+    double* part_sq;            // [item][U] per-angle sums of (P_c - P_m)^2
+    float* part_drift;          // [item][U]
 };
 
 int projector_smem_bytes(int angles_per_group, int B);
-int projector_plan(int U, int B, int* angles_per_group, int* n_groups);
-cudaError_t launch_projector(const ProjArgs& a, int n_items, cudaStream_t s);
+// Angle groups for n_items images: wide groups (lanes over the angles of a
+// pixel) when they give enough CTAs, else narrow groups of 2^l angles.
+int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* n_groups, int* lanes_log2);
+// Chooses the plan for n_items (filling a's group fields) and launches.
+cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s);
+// The largest B the projector takes (one angle per group in shared memory).
+int projector_max_bins();
 
 // Sums the per-group partials of a RESYNC/SIRT projection in a fixed order.
 struct ReduceArgs {
-    int n_items, n_groups;
+    int n_items, n_rows;        // n_rows = U: the per-angle partials of each item
     const double* part_sq;
     const float* part_drift;    // may be NULL
     double inv_cells;           // 1 / (B*U)

@@ -25,19 +25,6 @@ namespace {
 constexpr int kProjThreads = 512;
 constexpr int kProjSmemBudget = 200 * 1024;
 
-__device__ double block_sum_fixed_order(double v, double* red) {
-    const int tid = threadIdx.x;
-    red[tid] = v;
-    __syncthreads();
-    for (int w = kProjThreads / 2; w > 0; w >>= 1) {
-        if (tid < w) red[tid] += red[tid + w];
-        __syncthreads();
-    }
-    const double r = red[0];
-    __syncthreads();
-    return r;
-}
-
 __device__ float block_max(float v, float* red) {
     const int tid = threadIdx.x;
     red[tid] = v;
@@ -51,10 +38,19 @@ __device__ float block_max(float v, float* red) {
     return r;
 }
 
+__device__ __forceinline__ void add_entry(long long* row, int k, float f, float l, int F, bool factor) {
+    const long long t = factor ? fixed_product(l, l, F) : fixed_product(f, l, F);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&row[k]), (unsigned long long)t);
+}
+
+// One CTA per (group of angles, image).  Wide groups (lanes_log2 < 0): a
+// warp takes one pixel at a time, its lanes the group's angles.  Narrow
+// groups of 2^lanes_log2 angles: a warp takes 32 >> lanes_log2 pixels at a
+// time, one per lane slot, the slots' pixels far apart in the image so that
+// lanes of one angle rarely add to the same bin.
 __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long* acc = reinterpret_cast<long long*>(smem_raw);
-    __shared__ double red_d[kProjThreads];
     __shared__ float red_f[kProjThreads];
 
     const int item = blockIdx.y, grp = blockIdx.x;
@@ -63,13 +59,14 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     const int B = a.B;
     const long long P = (long long)a.n * a.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool factor = a.mode == PROJ_FACTOR;
     const float* img = a.img ? a.img + (long long)item * a.img_stride : nullptr;
 
     for (int e = tid; e < A * B; e += kProjThreads) acc[e] = 0;
 
     // Fraction bits from a bound on |P| (every ray is at most sqrt(2)*n + 2 long).
     double bound;
-    if (a.mode == PROJ_FACTOR) {
+    if (factor) {
         bound = 2.0 * (1.4142135623730951 * a.n + 2.0);
     } else {
         float m = 0.0f;
@@ -81,67 +78,84 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     __syncthreads();
 
     const int nwarps = kProjThreads / 32;
-    for (long long q = warp; q < P; q += nwarps) {
-        float f;
-        if (a.mode == PROJ_FACTOR) f = a.mask[q] ? 1.0f : 0.0f;
-        else f = img[q];
-        if (f == 0.0f) continue;
-        const long long row = q * a.row_records;
-        for (int ul = lane; ul < A; ul += 32) {
-            const long long rec = row + u0 + ul;
-            const Entry2 e = decode_rec(a.table, rec, a.f16);
-            if (e.l0 != 0.0f) {
-                const long long t = a.mode == PROJ_FACTOR ? fixed_product(e.l0, e.l0, F) : fixed_product(f, e.l0, F);
-                atomicAdd(reinterpret_cast<unsigned long long*>(&acc[ul * B + e.k0]), (unsigned long long)t);
+    if (a.lanes_log2 < 0) {
+        for (long long q = warp; q < P; q += nwarps) {
+            const float f = factor ? (a.mask[q] ? 1.0f : 0.0f) : img[q];
+            if (f == 0.0f) continue;
+            const long long row = q * a.row_records;
+            for (int ul = lane; ul < A; ul += 32) {
+                const Entry2 e = decode_rec(a.table, row + u0 + ul, a.f16);
+                if (e.l0 != 0.0f) add_entry(acc + ul * B, e.k0, f, e.l0, F, factor);
+                if (e.l1 != 0.0f) add_entry(acc + ul * B, e.k1, f, e.l1, F, factor);
             }
-            if (e.l1 != 0.0f) {
-                const long long t = a.mode == PROJ_FACTOR ? fixed_product(e.l1, e.l1, F) : fixed_product(f, e.l1, F);
-                atomicAdd(reinterpret_cast<unsigned long long*>(&acc[ul * B + e.k1]), (unsigned long long)t);
-            }
+        }
+    } else {
+        const int la = a.lanes_log2;
+        const int ps = lane >> la, ul = lane & ((1 << la) - 1);
+        const int slots = 32 >> la;
+        const long long L = (P + slots - 1) / slots;  // pixels per slot
+        const bool on = ul < A;
+        for (long long b = warp; b < L; b += nwarps) {
+            long long off = b + 7LL * ps;  // slots start at different columns
+            if (off >= L) off -= L;
+            if (off >= L) off %= L;
+            const long long q = (long long)ps * L + off;
+            if (!on || q >= P) continue;
+            const float f = factor ? (a.mask[q] ? 1.0f : 0.0f) : img[q];
+            if (f == 0.0f) continue;
+            const Entry2 e = decode_rec(a.table, q * a.row_records + u0 + ul, a.f16);
+            if (e.l0 != 0.0f) add_entry(acc + ul * B, e.k0, f, e.l0, F, factor);
+            if (e.l1 != 0.0f) add_entry(acc + ul * B, e.k1, f, e.l1, F, factor);
         }
     }
     __syncthreads();
 
-    double sq = 0.0;
-    float drift = 0.0f;
-    for (int e = tid; e < A * B; e += kProjThreads) {
-        const int ul = e / B, k = e - ul * B;
-        const long long cell = (long long)(u0 + ul) * B + k;
-        const double val = ldexp((double)acc[e], -F);
-        switch (a.mode) {
-            case PROJ_FORWARD:
-                a.out64[(long long)item * a.out_stride + cell] = val;
-                break;
-            case PROJ_FACTOR:
-                a.out64[cell] = val;
-                a.out32[cell] = (float)val;
-                break;
-            case PROJ_RESYNC: {
-                const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
-                const float rf = (float)r;
-                const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
-                float* dst = a.resid + (long long)item * a.resid_stride + (long long)(u0 + ul) * pitch + k;
-                if (a.drift) drift = fmaxf(drift, fabsf(rf - *dst));
-                *dst = rf;
-                sq += r * r;
-                break;
-            }
-            case PROJ_SIRT: {
-                const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
-                const float w = a.w[cell];
-                a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
-                sq += r * r;
-                break;
+    // One warp per angle row: outputs, and the row's sum of squares in a
+    // fixed order (lane partials over k, then a butterfly), so that it does
+    // not depend on how angles were grouped.
+    for (int ul = warp; ul < A; ul += nwarps) {
+        const int u = u0 + ul;
+        double sq = 0.0;
+        float drift = 0.0f;
+        for (int k = lane; k < B; k += 32) {
+            const long long cell = (long long)u * B + k;
+            const double val = ldexp((double)acc[ul * B + k], -F);
+            switch (a.mode) {
+                case PROJ_FORWARD:
+                    a.out64[(long long)item * a.out_stride + cell] = val;
+                    break;
+                case PROJ_FACTOR:
+                    a.out64[cell] = val;
+                    a.out32[cell] = (float)val;
+                    break;
+                case PROJ_RESYNC: {
+                    const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
+                    const float rf = (float)r;
+                    const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
+                    float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
+                    if (a.drift) drift = fmaxf(drift, fabsf(rf - *dst));
+                    *dst = rf;
+                    sq += r * r;
+                    break;
+                }
+                case PROJ_SIRT: {
+                    const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
+                    const float w = a.w[cell];
+                    a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
+                    sq += r * r;
+                    break;
+                }
             }
         }
-    }
-    if (a.part_sq) {
-        const double s = block_sum_fixed_order(sq, red_d);
-        if (tid == 0) a.part_sq[(long long)item * a.n_groups + grp] = s;
-    }
-    if (a.part_drift) {
-        const float d = block_max(drift, red_f);
-        if (tid == 0) a.part_drift[(long long)item * a.n_groups + grp] = d;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, o));
+        }
+        if (lane == 0) {
+            if (a.part_sq) a.part_sq[(long long)item * a.U + u] = sq;
+            if (a.part_drift) a.part_drift[(long long)item * a.U + u] = drift;
+        }
     }
 }
 
@@ -150,9 +164,9 @@ __global__ void reduce_kernel(ReduceArgs a) {
     if (item >= a.n_items) return;
     double s = 0.0;
     float d = 0.0f;
-    for (int g = 0; g < a.n_groups; ++g) {
-        s += a.part_sq[(long long)item * a.n_groups + g];
-        if (a.part_drift) d = fmaxf(d, a.part_drift[(long long)item * a.n_groups + g]);
+    for (int u = 0; u < a.n_rows; ++u) {
+        s += a.part_sq[(long long)item * a.n_rows + u];
+        if (a.part_drift) d = fmaxf(d, a.part_drift[(long long)item * a.n_rows + u]);
     }
     if (a.S_out) a.S_out[item] = s;
     if (a.cost_out) a.cost_out[(long long)item * a.cost_stride] = sqrt(s * a.inv_cells);
@@ -163,15 +177,43 @@ __global__ void reduce_kernel(ReduceArgs a) {
 
 int projector_smem_bytes(int angles_per_group, int B) { return angles_per_group * B * (int)sizeof(long long); }
 
-int projector_plan(int U, int B, int* angles_per_group, int* n_groups) {
-    int A = kProjSmemBudget / (B * (int)sizeof(long long));
-    if (A < 1) return SATPILA_ERR_INVALID_ARG;
-    if (A > U) A = U;
-    // balance the groups
-    const int G = (U + A - 1) / A;
-    A = (U + G - 1) / G;
-    *angles_per_group = A;
-    *n_groups = G;
+int projector_max_bins() { return kProjSmemBudget / (int)sizeof(long long); }
+
+int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* n_groups, int* lanes_log2) {
+    int amax = kProjSmemBudget / (B * (int)sizeof(long long));
+    if (amax < 1) return SATPILA_ERR_INVALID_ARG;
+    if (amax > U) amax = U;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    const long long target = 2LL * sms;  // CTAs wanted
+    // Wide groups: the group count (from the fewest that fit in shared
+    // memory) whose group size keeps the most lanes busy.
+    const int gmin = (U + amax - 1) / amax;
+    int gw = gmin;
+    double best = -1.0;
+    for (int G = gmin; G <= gmin + 4 && G <= U; ++G) {
+        const int A = (U + G - 1) / G;
+        const double eff = (double)A / (32.0 * ((A + 31) / 32));
+        if (eff > best + 1e-9) {
+            best = eff;
+            gw = G;
+        }
+    }
+    const int aw = (U + gw - 1) / gw;
+    if (aw >= 24 && n_items * gw >= target) {
+        *angles_per_group = aw;
+        *n_groups = gw;
+        *lanes_log2 = -1;
+        return SATPILA_OK;
+    }
+    // Narrow groups of 2^l <= 16 angles: the widest that still gives enough CTAs.
+    int l = 4;
+    while (l > 0 && ((1 << l) > amax || n_items * ((U + (1 << l) - 1) >> l) < target)) --l;
+    *angles_per_group = 1 << l;
+    *n_groups = (U + (1 << l) - 1) >> l;
+    *lanes_log2 = l;
     return SATPILA_OK;
 }
 
@@ -190,8 +232,10 @@ cudaError_t prepare_projector() {
     return e;
 }
 
-cudaError_t launch_projector(const ProjArgs& a, int n_items, cudaStream_t s) {
+cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
+    if (projector_plan(a.U, a.B, n_items, &a.angles_per_group, &a.n_groups, &a.lanes_log2) != SATPILA_OK)
+        return cudaErrorInvalidValue;
     const int smem = projector_smem_bytes(a.angles_per_group, a.B);
     cudaError_t e = prepare_projector();
     if (e != cudaSuccess) return e;
@@ -219,8 +263,7 @@ int ensure_factor(satpila_pila* p, cudaStream_t s) {
     a.n = p->n;
     a.U = p->U;
     a.B = p->B;
-    if (projector_plan(p->U, p->B, &a.angles_per_group, &a.n_groups) != SATPILA_OK)
-        return fail(SATPILA_ERR_INVALID_ARG, "too many bins for the projector");
+    if (p->B > projector_max_bins()) return fail(SATPILA_ERR_INVALID_ARG, "too many bins for the projector");
     a.mode = PROJ_FACTOR;
     a.mask = p->d_mask;
     a.out64 = p->d_w64;
@@ -261,8 +304,7 @@ extern "C" int pila_forward(const satpila_pila* p, int32_t n_images, const float
     a.n = p->n;
     a.U = p->U;
     a.B = p->B;
-    if (projector_plan(p->U, p->B, &a.angles_per_group, &a.n_groups) != SATPILA_OK)
-        return fail(SATPILA_ERR_INVALID_ARG, "pila_forward: too many bins");
+    if (p->B > projector_max_bins()) return fail(SATPILA_ERR_INVALID_ARG, "pila_forward: too many bins");
     a.mode = PROJ_FORWARD;
     a.img = di;
     a.img_stride = P;

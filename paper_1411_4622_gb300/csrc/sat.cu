@@ -219,8 +219,8 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->band_lo = p->band_lo & ~3;
     pl->band_pitch = (int)align_up((size_t)(p->band_hi + 1 - pl->band_lo), 4);
     pl->band_floats = (long long)p->U * pl->band_pitch + 64;
-    if (projector_plan(p->U, p->B, &pl->proj_A, &pl->proj_G) != SATPILA_OK)
-        return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many bins");
+    if (p->B > projector_max_bins()) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many bins");
+    pl->proj_G = p->U;  // per-angle partial sums of the resync, per chain
     pl->variant = variant;
     // Sec. III-B as written (an independent pixel per estimate): its own
     // kernel, one warp per chain, residual in global memory.
@@ -442,7 +442,7 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
                            double* cost_out, cudaStream_t q) {
     if (nc <= 0) return cudaSuccess;
     const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
-    const int G = pl.proj_G;
+    const int G = pl.proj_G;  // = U
     ProjArgs pa{};
     pa.table = p->d_table;
     pa.f16 = p->precision;
@@ -450,8 +450,6 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
     pa.n = p->n;
     pa.U = p->U;
     pa.B = p->B;
-    pa.angles_per_group = pl.proj_A;
-    pa.n_groups = G;
     pa.mode = PROJ_RESYNC;
     pa.drift = drift ? 1 : 0;
     pa.img = b.img + (long long)c0 * P;
@@ -467,7 +465,7 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
     if (e != cudaSuccess) return e;
     ReduceArgs ra{};
     ra.n_items = nc;
-    ra.n_groups = G;
+    ra.n_rows = G;
     ra.part_sq = pa.part_sq;
     ra.part_drift = pa.part_drift;
     ra.inv_cells = 1.0 / (double)cells;

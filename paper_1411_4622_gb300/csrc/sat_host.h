@@ -36,7 +36,7 @@ struct Plan {
     int band_pitch = 0;          // band row length in shared memory (floats, multiple of 4)
     long long band_floats = 0;   // shared-memory residual of a windowed warp
     int spt = 1;                 // stages per task
-    int proj_A = 0, proj_G = 0;  // projector: angles per group, groups
+    int proj_G = 0;              // resync partial sums per chain (one per angle: U)
     int variant = PLAN_RULES;
     size_t sweep_smem_bytes() const;
 };
@@ -57,8 +57,8 @@ struct BatchDev {
     int* progress = nullptr;       // per chain: stages done in the current sweep launch
     int* claim = nullptr;          // per chain: 1 while a warp runs it (ready-first scheduling)
     int* error = nullptr;          // [1]
-    double* part_sq = nullptr;     // [n][proj_G]
-    float* part_drift = nullptr;   // [n][proj_G]
+    double* part_sq = nullptr;     // [n][U] per-angle partials of the resync
+    float* part_drift = nullptr;   // [n][U]
     double* drift_max = nullptr;
     double* cost0 = nullptr;       // Eq. (4) cost at the start
     double* costF = nullptr;       // Eq. (4) cost after the latest resync

@@ -105,8 +105,8 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     if (rc != SATPILA_OK) return rc;
     const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
     const int n_iter = prm->n_iter;
-    int A = 0, G = 0;
-    if (projector_plan(p->U, p->B, &A, &G) != SATPILA_OK) return fail(SATPILA_ERR_INVALID_ARG, "sirt_run: too many bins");
+    if (p->B > projector_max_bins()) return fail(SATPILA_ERR_INVALID_ARG, "sirt_run: too many bins");
+    const int G = p->U;  // per-angle partial sums of each slice's cost
 
     const bool dev_s = is_device_pointer(sino_meas), dev_i = is_device_pointer(images);
     const bool dev_c = costs ? is_device_pointer(costs) : true;
@@ -145,8 +145,6 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     pa.n = p->n;
     pa.U = p->U;
     pa.B = p->B;
-    pa.angles_per_group = A;
-    pa.n_groups = G;
     pa.img = d_img;
     pa.img_stride = P;
     pa.pm = d_sino;
@@ -157,7 +155,7 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     pa.part_sq = psq;
     ReduceArgs ra{};
     ra.n_items = n_slices;
-    ra.n_groups = G;
+    ra.n_rows = G;
     ra.part_sq = psq;
     ra.inv_cells = 1.0 / (double)cells;
     ra.cost_out = cost_now;
@@ -261,9 +259,8 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
     cudaStream_t s = (cudaStream_t)stream;
     const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
     const int n_iter = prm->n_iter;
-    int A = 0, G = 0;
-    if (projector_plan(p->U, p->B, &A, &G) != SATPILA_OK)
-        return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: too many bins");
+    if (p->B > projector_max_bins()) return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: too many bins");
+    const int G = p->U;  // per-angle partial sums of each slice's cost
     // Scratch layout: correction or residual, partial sums, costs, and the
     // factor matrix when the table has not cached one.
     const bool own_w = p->d_w32 == nullptr;
@@ -294,8 +291,6 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
     pa.n = p->n;
     pa.U = p->U;
     pa.B = p->B;
-    pa.angles_per_group = A;
-    pa.n_groups = G;
     const float* w32 = p->d_w32;
     if (e == cudaSuccess && own_w) {
         ProjArgs fa = pa;
@@ -316,7 +311,7 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
     pa.part_sq = psq;
     ReduceArgs ra{};
     ra.n_items = n_slices;
-    ra.n_groups = G;
+    ra.n_rows = G;
     ra.part_sq = psq;
     ra.inv_cells = 1.0 / (double)cells;
     ra.cost_out = cost_now;
