@@ -63,7 +63,7 @@ struct ProjArgs {
     int row_records;
     int n, U, B;
     int angles_per_group, n_groups;  // set by launch_projector from the plan
-    int lanes_log2;             // narrow groups: log2 of the angles per group; -1: wide groups
+    int lanes_log2;             // log2 of the angles per group (set with the plan)
     int mode;
     int drift;                  // RESYNC: compare with the residual being replaced
     const float* img;           // FORWARD/RESYNC/SIRT images
@@ -83,8 +83,8 @@ struct ProjArgs {
 };
 
 int projector_smem_bytes(int angles_per_group, int B);
-// Angle groups for n_items images: wide groups (lanes over the angles of a
-// pixel) when they give enough CTAs, else narrow groups of 2^l angles.
+// Angle groups of 2^l <= 16 angles for n_items images: the widest that
+// gives enough CTAs.
 int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* n_groups, int* lanes_log2);
 // Chooses the plan for n_items (filling a's group fields) and launches.
 cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s);

@@ -4,11 +4,12 @@
 // (Sec. III-D, lengths squared over the reconstruction space) and the SIRT
 // correction of Eq. (11).
 //
-// Design: one CTA per (image, group of angles) holds a shared-memory
-// accumulator for its [angles][bins] block.  Warps walk the pixels, lanes the
-// angles of a pixel's PILA row (coalesced record loads), and every product
-// f * l is added as an exact 64-bit fixed-point integer (integer units; the
-// FP64 units of this part are scarce).  Integer addition is associative, so
+// Design: one CTA per (image, group of up to 16 angles) holds a shared-memory
+// accumulator for its [angles][bins] block.  Warps walk the pixels, each lane
+// one (pixel, angle) pair of the group (a pixel's records of the group are
+// contiguous), and every product f * l is added as an exact 64-bit
+// fixed-point integer (integer units; the FP64 units of this part are
+// scarce).  Groups are as wide as the number of CTAs allows.  Integer addition is associative, so
 // the result does not depend on the order of the shared-memory atomics:
 // the projection is deterministic and at least as accurate as an FP64 sum.
 // The fraction bits are chosen per image from max|f| so nothing overflows.
@@ -43,11 +44,11 @@ __device__ __forceinline__ void add_entry(long long* row, int k, float f, float 
     atomicAdd(reinterpret_cast<unsigned long long*>(&row[k]), (unsigned long long)t);
 }
 
-// One CTA per (group of angles, image).  Wide groups (lanes_log2 < 0): a
-// warp takes one pixel at a time, its lanes the group's angles.  Narrow
-// groups of 2^lanes_log2 angles: a warp takes 32 >> lanes_log2 pixels at a
-// time, one per lane slot, the slots' pixels far apart in the image so that
-// lanes of one angle rarely add to the same bin.
+// One CTA per (group of 2^l angles, image).  A warp takes 32 >> l pixels at
+// a time, one per lane slot (a slot's lanes are the group's angles); the
+// slots walk far-apart parts of the image, starting at different columns, so
+// that lanes of one angle rarely add to the same bin.  Two steps are loaded
+// before either is added, to overlap their loads.
 __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long* acc = reinterpret_cast<long long*>(smem_raw);
@@ -78,34 +79,40 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     __syncthreads();
 
     const int nwarps = kProjThreads / 32;
-    if (a.lanes_log2 < 0) {
-        for (long long q = warp; q < P; q += nwarps) {
-            const float f = factor ? (a.mask[q] ? 1.0f : 0.0f) : img[q];
-            if (f == 0.0f) continue;
-            const long long row = q * a.row_records;
-            for (int ul = lane; ul < A; ul += 32) {
-                const Entry2 e = decode_rec(a.table, row + u0 + ul, a.f16);
-                if (e.l0 != 0.0f) add_entry(acc + ul * B, e.k0, f, e.l0, F, factor);
-                if (e.l1 != 0.0f) add_entry(acc + ul * B, e.k1, f, e.l1, F, factor);
-            }
+    const int la = a.lanes_log2;
+    const int ps = lane >> la, ul = lane & ((1 << la) - 1);
+    const int slots = 32 >> la;
+    const long long L = (P + slots - 1) / slots;  // pixels per slot
+    const bool on = ul < A;
+    const long long col = (long long)u0 + ul;
+    long long* row = acc + ul * B;
+    auto pixel_of = [&](long long b) -> long long {
+        long long off = b + 7LL * ps;
+        if (off >= L) off -= L;
+        if (off >= L) off %= L;
+        return (long long)ps * L + off;
+    };
+    for (long long b = warp; b < L; b += 2 * nwarps) {
+        const long long b2 = b + nwarps;
+        const long long q1 = pixel_of(b), q2 = b2 < L ? pixel_of(b2) : P;
+        const bool v1 = on && q1 < P, v2 = on && q2 < P;
+        float f1 = 0.0f, f2 = 0.0f;
+        Entry2 e1{0, 0, 0.0f, 0.0f}, e2{0, 0, 0.0f, 0.0f};
+        if (v1) {
+            f1 = factor ? (a.mask[q1] ? 1.0f : 0.0f) : img[q1];
+            e1 = decode_rec(a.table, q1 * a.row_records + col, a.f16);
         }
-    } else {
-        const int la = a.lanes_log2;
-        const int ps = lane >> la, ul = lane & ((1 << la) - 1);
-        const int slots = 32 >> la;
-        const long long L = (P + slots - 1) / slots;  // pixels per slot
-        const bool on = ul < A;
-        for (long long b = warp; b < L; b += nwarps) {
-            long long off = b + 7LL * ps;  // slots start at different columns
-            if (off >= L) off -= L;
-            if (off >= L) off %= L;
-            const long long q = (long long)ps * L + off;
-            if (!on || q >= P) continue;
-            const float f = factor ? (a.mask[q] ? 1.0f : 0.0f) : img[q];
-            if (f == 0.0f) continue;
-            const Entry2 e = decode_rec(a.table, q * a.row_records + u0 + ul, a.f16);
-            if (e.l0 != 0.0f) add_entry(acc + ul * B, e.k0, f, e.l0, F, factor);
-            if (e.l1 != 0.0f) add_entry(acc + ul * B, e.k1, f, e.l1, F, factor);
+        if (v2) {
+            f2 = factor ? (a.mask[q2] ? 1.0f : 0.0f) : img[q2];
+            e2 = decode_rec(a.table, q2 * a.row_records + col, a.f16);
+        }
+        if (f1 != 0.0f) {
+            if (e1.l0 != 0.0f) add_entry(row, e1.k0, f1, e1.l0, F, factor);
+            if (e1.l1 != 0.0f) add_entry(row, e1.k1, f1, e1.l1, F, factor);
+        }
+        if (f2 != 0.0f) {
+            if (e2.l0 != 0.0f) add_entry(row, e2.k0, f2, e2.l0, F, factor);
+            if (e2.l1 != 0.0f) add_entry(row, e2.k1, f2, e2.l1, F, factor);
         }
     }
     __syncthreads();
@@ -182,33 +189,13 @@ int projector_max_bins() { return kProjSmemBudget / (int)sizeof(long long); }
 int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* n_groups, int* lanes_log2) {
     int amax = kProjSmemBudget / (B * (int)sizeof(long long));
     if (amax < 1) return SATPILA_ERR_INVALID_ARG;
-    if (amax > U) amax = U;
     int dev = 0, sms = 1;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         sms = 1;
     const long long target = 2LL * sms;  // CTAs wanted
-    // Wide groups: the group count (from the fewest that fit in shared
-    // memory) whose group size keeps the most lanes busy.
-    const int gmin = (U + amax - 1) / amax;
-    int gw = gmin;
-    double best = -1.0;
-    for (int G = gmin; G <= gmin + 4 && G <= U; ++G) {
-        const int A = (U + G - 1) / G;
-        const double eff = (double)A / (32.0 * ((A + 31) / 32));
-        if (eff > best + 1e-9) {
-            best = eff;
-            gw = G;
-        }
-    }
-    const int aw = (U + gw - 1) / gw;
-    if (aw >= 24 && n_items * gw >= target) {
-        *angles_per_group = aw;
-        *n_groups = gw;
-        *lanes_log2 = -1;
-        return SATPILA_OK;
-    }
-    // Narrow groups of 2^l <= 16 angles: the widest that still gives enough CTAs.
+    // Groups of 2^l <= 16 angles: the widest that still gives enough CTAs
+    // (small groups also leave room for several CTAs per SM).
     int l = 4;
     while (l > 0 && ((1 << l) > amax || n_items * ((U + (1 << l) - 1) >> l) < target)) --l;
     *angles_per_group = 1 << l;
