@@ -39,8 +39,52 @@ __device__ float block_max(float v, float* red) {
     return r;
 }
 
-__device__ __forceinline__ void add_entry(long long* row, int k, float f, float l, int F, bool factor) {
-    const long long t = factor ? fixed_product(l, l, F) : fixed_product(f, l, F);
+// A float split for exact fixed-point products: significand (with the
+// hidden bit), exponent of its last bit, sign.
+struct FixedSplit {
+    uint32_t m;
+    int x;
+    uint32_t neg;
+};
+
+__device__ __forceinline__ FixedSplit fixed_split(float a) {
+    const uint32_t ba = __float_as_uint(a);
+    const uint32_t ea = (ba >> 23) & 0xffu;
+    FixedSplit s;
+    s.m = ba & 0x7fffffu;
+    s.x = -149;
+    if (ea) {
+        s.m |= 0x800000u;
+        s.x = (int)ea - 150;
+    }
+    s.neg = ba >> 31;
+    return s;
+}
+
+// round(a * l * 2^F) for a split a and a positive normal float l (every
+// stored length is one: at least 1e-12, or a decoded half or byte): the
+// 48-bit product of the significands shifted by the combined exponent (round
+// half away from zero), on the integer units.  F keeps it from overflowing.
+__device__ __forceinline__ long long fixed_mul(const FixedSplit& a, float l, int F) {
+    const uint32_t bl = __float_as_uint(l);
+    const uint32_t ml = (bl & 0x7fffffu) | 0x800000u;
+    const int e = a.x + (int)((bl >> 23) & 0xffu) - 150 + F;
+    const unsigned long long m = (unsigned long long)a.m * (unsigned long long)ml;
+    unsigned long long v;
+    if (e >= 0) {
+        v = m << e;
+    } else if (e > -64) {
+        const int sh = -e;
+        v = (m >> sh) + ((m >> (sh - 1)) & 1ull);
+    } else {
+        v = 0ull;
+    }
+    return a.neg ? -(long long)v : (long long)v;
+}
+
+// Adds f * l (or l * l for the factor matrix) to bin k of an accumulator row.
+__device__ __forceinline__ void add_entry(long long* row, int k, const FixedSplit& fs, float l, int F, bool factor) {
+    const long long t = fixed_mul(factor ? fixed_split(l) : fs, l, F);
     atomicAdd(reinterpret_cast<unsigned long long*>(&row[k]), (unsigned long long)t);
 }
 
@@ -82,37 +126,41 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     const int la = a.lanes_log2;
     const int ps = lane >> la, ul = lane & ((1 << la) - 1);
     const int slots = 32 >> la;
-    const long long L = (P + slots - 1) / slots;  // pixels per slot
+    // pixel indices fit in 32 bits (pila_build caps n * n at 2^30)
+    const int Pi = (int)P;
+    const int L = (Pi + slots - 1) / slots;  // pixels per slot
     const bool on = ul < A;
     const long long col = (long long)u0 + ul;
     long long* row = acc + ul * B;
-    auto pixel_of = [&](long long b) -> long long {
-        long long off = b + 7LL * ps;
+    auto pixel_of = [&](int b) -> int {
+        int off = b + 7 * ps;
         if (off >= L) off -= L;
         if (off >= L) off %= L;
-        return (long long)ps * L + off;
+        return ps * L + off;
     };
-    for (long long b = warp; b < L; b += 2 * nwarps) {
-        const long long b2 = b + nwarps;
-        const long long q1 = pixel_of(b), q2 = b2 < L ? pixel_of(b2) : P;
-        const bool v1 = on && q1 < P, v2 = on && q2 < P;
+    for (int b = warp; b < L; b += 2 * nwarps) {
+        const int b2 = b + nwarps;
+        const int q1 = pixel_of(b), q2 = b2 < L ? pixel_of(b2) : Pi;
+        const bool v1 = on && q1 < Pi, v2 = on && q2 < Pi;
         float f1 = 0.0f, f2 = 0.0f;
         Entry2 e1{0, 0, 0.0f, 0.0f}, e2{0, 0, 0.0f, 0.0f};
         if (v1) {
             f1 = factor ? (a.mask[q1] ? 1.0f : 0.0f) : img[q1];
-            e1 = decode_rec(a.table, q1 * a.row_records + col, a.f16);
+            e1 = decode_rec(a.table, (long long)q1 * a.row_records + col, a.f16);
         }
         if (v2) {
             f2 = factor ? (a.mask[q2] ? 1.0f : 0.0f) : img[q2];
-            e2 = decode_rec(a.table, q2 * a.row_records + col, a.f16);
+            e2 = decode_rec(a.table, (long long)q2 * a.row_records + col, a.f16);
         }
         if (f1 != 0.0f) {
-            if (e1.l0 != 0.0f) add_entry(row, e1.k0, f1, e1.l0, F, factor);
-            if (e1.l1 != 0.0f) add_entry(row, e1.k1, f1, e1.l1, F, factor);
+            const FixedSplit s1 = fixed_split(f1);
+            if (e1.l0 != 0.0f) add_entry(row, e1.k0, s1, e1.l0, F, factor);
+            if (e1.l1 != 0.0f) add_entry(row, e1.k1, s1, e1.l1, F, factor);
         }
         if (f2 != 0.0f) {
-            if (e2.l0 != 0.0f) add_entry(row, e2.k0, f2, e2.l0, F, factor);
-            if (e2.l1 != 0.0f) add_entry(row, e2.k1, f2, e2.l1, F, factor);
+            const FixedSplit s2 = fixed_split(f2);
+            if (e2.l0 != 0.0f) add_entry(row, e2.k0, s2, e2.l0, F, factor);
+            if (e2.l1 != 0.0f) add_entry(row, e2.k1, s2, e2.l1, F, factor);
         }
     }
     __syncthreads();
