@@ -80,12 +80,22 @@ struct ProjArgs {
     const float* w;             // SIRT: factor matrix (float)
     double* part_sq;            // [item][U] per-angle sums of (P_c - P_m)^2
     float* part_drift;          // [item][U]
+    void* ws;                   // optional, projector_ws_bytes(items, U, B), zero when first
+                                // used (the projector leaves it zero): lets few images
+                                // split their pixels over more CTAs
+    int chunks;                 // set with the plan
+    long long* acc_global;      // carved from ws when chunks > 1
+    int* fbits;
 };
 
 int projector_smem_bytes(int angles_per_group, int B);
-// Angle groups of 2^l <= 16 angles for n_items images: the widest that
-// gives enough CTAs.
-int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* n_groups, int* lanes_log2);
+// Angle groups of 2^l <= 16 angles for n_items n x n images; when they give
+// too few CTAs, pixel chunks (can_chunk: a workspace is given) or else
+// narrower groups.
+int projector_plan(int U, int B, int n, long long n_items, bool can_chunk, int* angles_per_group, int* n_groups,
+                   int* lanes_log2, int* chunks);
+// Workspace that lets launch_projector split pixels into chunks.
+size_t projector_ws_bytes(long long n_items, int U, int B);
 // Chooses the plan for n_items (filling a's group fields) and launches.
 cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s);
 // The largest B the projector takes (one angle per group in shared memory).

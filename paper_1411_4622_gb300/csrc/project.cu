@@ -13,6 +13,7 @@
 // the result does not depend on the order of the shared-memory atomics:
 // the projection is deterministic and at least as accurate as an FP64 sum.
 // The fraction bits are chosen per image from max|f| so nothing overflows.
+#include <algorithm>
 #include <cmath>
 
 #include <mutex>
@@ -88,47 +89,111 @@ __device__ __forceinline__ void add_entry(long long* row, int k, const FixedSpli
     atomicAdd(reinterpret_cast<unsigned long long*>(&row[k]), (unsigned long long)t);
 }
 
-// One CTA per (group of 2^l angles, image).  A warp takes 32 >> l pixels at
-// a time, one per lane slot (a slot's lanes are the group's angles); the
-// slots walk far-apart parts of the image, starting at different columns, so
-// that lanes of one angle rarely add to the same bin.  Two steps are loaded
-// before either is added, to overlap their loads.
+// Outputs of one angle row u from its fixed-point sums src[0..B), and the
+// row's sum of squares in a fixed order (lane partials over k, then a
+// butterfly), so that it does not depend on how the sums were formed.  clear:
+// leave src zero.
+__device__ __forceinline__ void finish_row(const ProjArgs& a, int item, int u, int F, long long* src, bool clear,
+                                           int lane) {
+    const int B = a.B;
+    double sq = 0.0;
+    float drift = 0.0f;
+    for (int k = lane; k < B; k += 32) {
+        const long long cell = (long long)u * B + k;
+        const long long raw = src[k];
+        if (clear) src[k] = 0;
+        const double val = ldexp((double)raw, -F);
+        switch (a.mode) {
+            case PROJ_FORWARD:
+                a.out64[(long long)item * a.out_stride + cell] = val;
+                break;
+            case PROJ_FACTOR:
+                a.out64[cell] = val;
+                a.out32[cell] = (float)val;
+                break;
+            case PROJ_RESYNC: {
+                const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
+                const float rf = (float)r;
+                const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
+                float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
+                if (a.drift) drift = fmaxf(drift, fabsf(rf - *dst));
+                *dst = rf;
+                sq += r * r;
+                break;
+            }
+            case PROJ_SIRT: {
+                const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
+                const float w = a.w[cell];
+                a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
+                sq += r * r;
+                break;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, o));
+    }
+    if (lane == 0) {
+        if (a.part_sq) a.part_sq[(long long)item * a.U + u] = sq;
+        if (a.part_drift) a.part_drift[(long long)item * a.U + u] = drift;
+    }
+}
+
+// Fraction bits of image item's sums: from a bound on |P| (every ray is at
+// most sqrt(2)*n + 2 long).  All threads of the block must call it.
+__device__ int item_fraction_bits(const ProjArgs& a, int item, float* red) {
+    if (a.mode == PROJ_FACTOR) return fixed_point_bits(2.0 * (1.4142135623730951 * a.n + 2.0));
+    const float* img = a.img + (long long)item * a.img_stride;
+    const long long P = (long long)a.n * a.n;
+    float m = 0.0f;
+    for (long long q = threadIdx.x; q < P; q += blockDim.x) m = fmaxf(m, fabsf(img[q]));
+    m = block_max(m, red);
+    return fixed_point_bits(1.5 * (double)m * (1.4142135623730951 * a.n + 2.0));
+}
+
+// Chunked launches: the fraction bits of every image, once.
+__global__ void __launch_bounds__(kProjThreads) proj_scale_kernel(ProjArgs a) {
+    __shared__ float red_f[kProjThreads];
+    const int F = item_fraction_bits(a, blockIdx.x, red_f);
+    if (threadIdx.x == 0) a.fbits[blockIdx.x] = F;
+}
+
+// One CTA per (group of 2^l angles, image, pixel chunk).  A warp takes
+// 32 >> l pixels of the chunk at a time, one per lane slot (a slot's lanes
+// are the group's angles); the slots walk far-apart parts of the chunk,
+// starting at different columns, so that lanes of one angle rarely add to the
+// same bin.  Two steps are loaded before either is added, to overlap their
+// loads.  With one chunk the CTA finishes its rows itself; with several it
+// adds its sums to the image's rows in acc_global (exact integer adds, so the
+// order does not matter) and proj_finish_kernel finishes them.
 __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long* acc = reinterpret_cast<long long*>(smem_raw);
     __shared__ float red_f[kProjThreads];
 
-    const int item = blockIdx.y, grp = blockIdx.x;
+    const int item = blockIdx.y, grp = blockIdx.x, chunk = blockIdx.z;
     const int u0 = grp * a.angles_per_group;
     const int A = min(a.angles_per_group, a.U - u0);
     const int B = a.B;
-    const long long P = (long long)a.n * a.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool factor = a.mode == PROJ_FACTOR;
     const float* img = a.img ? a.img + (long long)item * a.img_stride : nullptr;
 
     for (int e = tid; e < A * B; e += kProjThreads) acc[e] = 0;
-
-    // Fraction bits from a bound on |P| (every ray is at most sqrt(2)*n + 2 long).
-    double bound;
-    if (factor) {
-        bound = 2.0 * (1.4142135623730951 * a.n + 2.0);
-    } else {
-        float m = 0.0f;
-        for (long long q = tid; q < P; q += kProjThreads) m = fmaxf(m, fabsf(img[q]));
-        m = block_max(m, red_f);
-        bound = 1.5 * (double)m * (1.4142135623730951 * a.n + 2.0);
-    }
-    const int F = fixed_point_bits(bound);
+    const int F = a.chunks > 1 ? a.fbits[item] : item_fraction_bits(a, item, red_f);
     __syncthreads();
 
+    // pixel indices fit in 32 bits (pila_build caps n * n at 2^30)
+    const int Pi = a.n * a.n;
+    const int per = (Pi + a.chunks - 1) / a.chunks;
+    const int c0 = chunk * per, c1 = min(Pi, c0 + per);
     const int nwarps = kProjThreads / 32;
     const int la = a.lanes_log2;
     const int ps = lane >> la, ul = lane & ((1 << la) - 1);
     const int slots = 32 >> la;
-    // pixel indices fit in 32 bits (pila_build caps n * n at 2^30)
-    const int Pi = (int)P;
-    const int L = (Pi + slots - 1) / slots;  // pixels per slot
+    const int L = (c1 - c0 + slots - 1) / slots;  // pixels per slot
     const bool on = ul < A;
     const long long col = (long long)u0 + ul;
     long long* row = acc + ul * B;
@@ -136,12 +201,12 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
         int off = b + 7 * ps;
         if (off >= L) off -= L;
         if (off >= L) off %= L;
-        return ps * L + off;
+        return c0 + ps * L + off;
     };
     for (int b = warp; b < L; b += 2 * nwarps) {
         const int b2 = b + nwarps;
-        const int q1 = pixel_of(b), q2 = b2 < L ? pixel_of(b2) : Pi;
-        const bool v1 = on && q1 < Pi, v2 = on && q2 < Pi;
+        const int q1 = pixel_of(b), q2 = b2 < L ? pixel_of(b2) : c1;
+        const bool v1 = on && q1 < c1, v2 = on && q2 < c1;
         float f1 = 0.0f, f2 = 0.0f;
         Entry2 e1{0, 0, 0.0f, 0.0f}, e2{0, 0, 0.0f, 0.0f};
         if (v1) {
@@ -165,64 +230,43 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     }
     __syncthreads();
 
-    // One warp per angle row: outputs, and the row's sum of squares in a
-    // fixed order (lane partials over k, then a butterfly), so that it does
-    // not depend on how angles were grouped.
-    for (int ul = warp; ul < A; ul += nwarps) {
-        const int u = u0 + ul;
-        double sq = 0.0;
-        float drift = 0.0f;
-        for (int k = lane; k < B; k += 32) {
-            const long long cell = (long long)u * B + k;
-            const double val = ldexp((double)acc[ul * B + k], -F);
-            switch (a.mode) {
-                case PROJ_FORWARD:
-                    a.out64[(long long)item * a.out_stride + cell] = val;
-                    break;
-                case PROJ_FACTOR:
-                    a.out64[cell] = val;
-                    a.out32[cell] = (float)val;
-                    break;
-                case PROJ_RESYNC: {
-                    const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
-                    const float rf = (float)r;
-                    const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
-                    float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
-                    if (a.drift) drift = fmaxf(drift, fabsf(rf - *dst));
-                    *dst = rf;
-                    sq += r * r;
-                    break;
-                }
-                case PROJ_SIRT: {
-                    const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
-                    const float w = a.w[cell];
-                    a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
-                    sq += r * r;
-                    break;
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, o));
-        }
-        if (lane == 0) {
-            if (a.part_sq) a.part_sq[(long long)item * a.U + u] = sq;
-            if (a.part_drift) a.part_drift[(long long)item * a.U + u] = drift;
-        }
+    if (a.chunks == 1) {
+        for (int r = warp; r < A; r += nwarps) finish_row(a, item, u0 + r, F, acc + r * B, false, lane);
+    } else {
+        // rows u0 .. u0 + A - 1 of the image are contiguous in acc_global
+        unsigned long long* dst =
+            reinterpret_cast<unsigned long long*>(a.acc_global + ((long long)item * a.U + u0) * B);
+        for (int e = tid; e < A * B; e += kProjThreads)
+            if (acc[e] != 0) atomicAdd(dst + e, (unsigned long long)acc[e]);
     }
 }
 
+// Chunked launches: one warp per angle row of an image.
+__global__ void __launch_bounds__(kProjThreads) proj_finish_kernel(ProjArgs a) {
+    const int item = blockIdx.y;
+    const int u = blockIdx.x * (kProjThreads / 32) + (threadIdx.x >> 5);
+    if (u >= a.U) return;
+    finish_row(a, item, u, a.fbits[item], a.acc_global + ((long long)item * a.U + u) * a.B, true, threadIdx.x & 31);
+}
+
+// One warp per item: lane partials over u = lane, lane + 32, ... in order,
+// then a butterfly (a fixed order).
 __global__ void reduce_kernel(ReduceArgs a) {
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (item >= a.n_items) return;
     double s = 0.0;
     float d = 0.0f;
-    for (int u = 0; u < a.n_rows; ++u) {
+    for (int u = lane; u < a.n_rows; u += 32) {
         s += a.part_sq[(long long)item * a.n_rows + u];
         if (a.part_drift) d = fmaxf(d, a.part_drift[(long long)item * a.n_rows + u]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    }
+    if (lane != 0) return;
     if (a.S_out) a.S_out[item] = s;
     if (a.cost_out) a.cost_out[(long long)item * a.cost_stride] = sqrt(s * a.inv_cells);
     if (a.drift_max && a.part_drift) a.drift_max[item] = fmax(a.drift_max[item], (double)d);
@@ -230,11 +274,14 @@ __global__ void reduce_kernel(ReduceArgs a) {
 
 }  // namespace
 
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
 int projector_smem_bytes(int angles_per_group, int B) { return angles_per_group * B * (int)sizeof(long long); }
 
 int projector_max_bins() { return kProjSmemBudget / (int)sizeof(long long); }
 
-int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* n_groups, int* lanes_log2) {
+int projector_plan(int U, int B, int n, long long n_items, bool can_chunk, int* angles_per_group, int* n_groups,
+                   int* lanes_log2, int* chunks) {
     int amax = kProjSmemBudget / (B * (int)sizeof(long long));
     if (amax < 1) return SATPILA_ERR_INVALID_ARG;
     int dev = 0, sms = 1;
@@ -242,14 +289,30 @@ int projector_plan(int U, int B, long long n_items, int* angles_per_group, int* 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         sms = 1;
     const long long target = 2LL * sms;  // CTAs wanted
-    // Groups of 2^l <= 16 angles: the widest that still gives enough CTAs
-    // (small groups also leave room for several CTAs per SM).
     int l = 4;
-    while (l > 0 && ((1 << l) > amax || n_items * ((U + (1 << l) - 1) >> l) < target)) --l;
+    while ((1 << l) > amax) --l;
+    long long G = (U + (1 << l) - 1) >> l;
+    *chunks = 1;
+    if (n_items * G < target) {
+        if (can_chunk) {
+            // split the pixels: chunks of at least 1024 pixels
+            const long long P = (long long)n * n;
+            *chunks = (int)std::max(1LL, std::min((target + n_items * G - 1) / (n_items * G), P / 1024));
+        } else {
+            // narrower groups: the widest that still gives enough CTAs
+            while (l > 0 && n_items * ((U + (1 << l) - 1) >> l) < target) --l;
+            G = (U + (1 << l) - 1) >> l;
+        }
+    }
     *angles_per_group = 1 << l;
-    *n_groups = (U + (1 << l) - 1) >> l;
+    *n_groups = (int)G;
     *lanes_log2 = l;
     return SATPILA_OK;
+}
+
+size_t projector_ws_bytes(long long n_items, int U, int B) {
+    return round_up((size_t)n_items * U * B * sizeof(long long), 256) +
+           round_up((size_t)n_items * sizeof(int), 256);
 }
 
 // The projector's shared-memory limit, set once per device (before any
@@ -269,19 +332,36 @@ cudaError_t prepare_projector() {
 
 cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
-    if (projector_plan(a.U, a.B, n_items, &a.angles_per_group, &a.n_groups, &a.lanes_log2) != SATPILA_OK)
+    if (projector_plan(a.U, a.B, a.n, n_items, a.ws != nullptr, &a.angles_per_group, &a.n_groups, &a.lanes_log2,
+                       &a.chunks) != SATPILA_OK)
         return cudaErrorInvalidValue;
+    a.acc_global = nullptr;
+    a.fbits = nullptr;
+    if (a.chunks > 1) {
+        a.acc_global = reinterpret_cast<long long*>(a.ws);
+        a.fbits = reinterpret_cast<int*>(reinterpret_cast<char*>(a.ws) +
+                                         round_up((size_t)n_items * a.U * a.B * sizeof(long long), 256));
+    }
     const int smem = projector_smem_bytes(a.angles_per_group, a.B);
     cudaError_t e = prepare_projector();
     if (e != cudaSuccess) return e;
-    dim3 grid(a.n_groups, n_items);
-    projector_kernel<<<grid, kProjThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.chunks > 1) {
+        proj_scale_kernel<<<n_items, kProjThreads, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    projector_kernel<<<dim3(a.n_groups, n_items, a.chunks), kProjThreads, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.chunks > 1) {
+        constexpr int rows_per_block = kProjThreads / 32;
+        proj_finish_kernel<<<dim3((a.U + rows_per_block - 1) / rows_per_block, n_items), kProjThreads, 0, s>>>(a);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s) {
     if (a.n_items <= 0) return cudaSuccess;
-    reduce_kernel<<<(a.n_items + 127) / 128, 128, 0, s>>>(a);
+    reduce_kernel<<<(unsigned)((a.n_items + 3) / 4), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -345,7 +425,21 @@ extern "C" int pila_forward(const satpila_pila* p, int32_t n_images, const float
     a.img_stride = P;
     a.out64 = dout;
     a.out_stride = cells;
-    cudaError_t e = launch_projector(a, n_images, s);
+    cudaError_t e = cudaSuccess;
+    void* ws = nullptr;
+    int A = 0, G = 0, l = 0, chunks = 1;
+    // few images: a stream-ordered workspace lets their pixels spread over more CTAs
+    if (projector_plan(p->U, p->B, p->n, n_images, true, &A, &G, &l, &chunks) == SATPILA_OK && chunks > 1) {
+        const size_t bytes = projector_ws_bytes(n_images, p->U, p->B);
+        e = cudaMallocAsync(&ws, bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, bytes, s);
+        a.ws = ws;
+    }
+    if (e == cudaSuccess) e = launch_projector(a, n_images, s);
+    if (ws) {
+        const cudaError_t ef = cudaFreeAsync(ws, s);
+        if (e == cudaSuccess) e = ef;
+    }
     if (e == cudaSuccess && !dev_o)
         e = cudaMemcpyAsync(sino, dout, (size_t)n_images * cells * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && (!dev_i || !dev_o)) e = cudaStreamSynchronize(s);

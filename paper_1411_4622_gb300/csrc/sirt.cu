@@ -121,11 +121,13 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     const size_t o_corr = o_costs + (bytes_costs + 255) / 256 * 256;
     const size_t o_psq = o_corr + ((size_t)n_slices * cells * 4 + 255) / 256 * 256;
     const size_t o_cost = o_psq + ((size_t)n_slices * G * 8 + 255) / 256 * 256;
-    const size_t total = o_cost + (size_t)n_slices * 8;
+    const size_t o_proj = o_cost + ((size_t)n_slices * 8 + 255) / 256 * 256;
+    const size_t total = o_proj + projector_ws_bytes(n_slices, p->U, p->B);
     SP_CUDA(cudaMalloc(&ws, total));
     char* b = (char*)ws;
-    cudaError_t e = cudaSuccess;
-    if (!dev_s) {
+    // the projector's workspace starts zero (and stays so between launches)
+    cudaError_t e = cudaMemsetAsync(b + o_proj, 0, total - o_proj, s);
+    if (e == cudaSuccess && !dev_s) {
         d_sino = (const float*)(b + o_sino);
         e = cudaMemcpyAsync((void*)d_sino, sino_meas, bytes_sino, cudaMemcpyHostToDevice, s);
     }
@@ -153,6 +155,7 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     pa.resid_stride = cells;
     pa.w = p->d_w32;
     pa.part_sq = psq;
+    pa.ws = b + o_proj;
     ReduceArgs ra{};
     ra.n_items = n_slices;
     ra.n_rows = G;
@@ -269,11 +272,15 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
     const size_t o_cost = o_psq + round256((size_t)n_slices * G * 8);
     const size_t o_w64 = o_cost + round256((size_t)n_slices * 8);
     const size_t o_w32 = o_w64 + (own_w ? round256((size_t)cells * 8) : 0);
-    const size_t total = o_w32 + (own_w ? round256((size_t)cells * 4) : 0);
+    const size_t o_proj = o_w32 + (own_w ? round256((size_t)cells * 4) : 0);
+    size_t total = o_proj;
     if (total > (size_t)SATPILA_NOALLOC_SCRATCH_BYTES)
         return fail(SATPILA_ERR_INVALID_ARG, "sirt_run_noalloc: the problem needs " + std::to_string(total) +
                                                  " bytes of scratch, more than the static " +
                                                  std::to_string((size_t)SATPILA_NOALLOC_SCRATCH_BYTES));
+    // the projector's workspace (pixel chunks for few slices) when it fits
+    const bool chunk_ws = total + projector_ws_bytes(n_slices, p->U, p->B) <= (size_t)SATPILA_NOALLOC_SCRATCH_BYTES;
+    if (chunk_ws) total += projector_ws_bytes(n_slices, p->U, p->B);
     void* base = nullptr;
     int rc = noalloc_scratch(&base);
     if (rc != SATPILA_OK) return rc;
@@ -291,6 +298,7 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
     pa.n = p->n;
     pa.U = p->U;
     pa.B = p->B;
+    pa.ws = chunk_ws ? b + o_proj : nullptr;
     const float* w32 = p->d_w32;
     if (e == cudaSuccess && own_w) {
         ProjArgs fa = pa;
