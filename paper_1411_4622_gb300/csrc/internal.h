@@ -80,12 +80,11 @@ struct ProjArgs {
     const float* w;             // SIRT: factor matrix (float)
     double* part_sq;            // [item][U] per-angle sums of (P_c - P_m)^2
     float* part_drift;          // [item][U]
-    void* ws;                   // optional, projector_ws_bytes(items, U, B), zero when first
-                                // used (the projector leaves it zero): lets few images
-                                // split their pixels over more CTAs
+    void* ws;                   // optional, projector_ws_bytes(items, U, B, n) bytes: lets few
+                                // images split their pixels over more CTAs
     int chunks;                 // set with the plan
-    long long* acc_global;      // carved from ws when chunks > 1
-    int* fbits;
+    long long* partial;         // carved from ws when chunks > 1: [item][chunk][U][B] sums
+    float* max_parts;           // [item][32] partial max|f|
 };
 
 int projector_smem_bytes(int angles_per_group, int B);
@@ -94,8 +93,9 @@ int projector_smem_bytes(int angles_per_group, int B);
 // narrower groups.
 int projector_plan(int U, int B, int n, long long n_items, bool can_chunk, int* angles_per_group, int* n_groups,
                    int* lanes_log2, int* chunks);
-// Workspace that lets launch_projector split pixels into chunks.
-size_t projector_ws_bytes(long long n_items, int U, int B);
+// Workspace that lets launch_projector split the pixels of n_items n x n
+// images into chunks (0 when it would not).
+size_t projector_ws_bytes(long long n_items, int U, int B, int n);
 // Chooses the plan for n_items (filling a's group fields) and launches.
 cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s);
 // The largest B the projector takes (one angle per group in shared memory).

@@ -89,47 +89,43 @@ __device__ __forceinline__ void add_entry(long long* row, int k, const FixedSpli
     atomicAdd(reinterpret_cast<unsigned long long*>(&row[k]), (unsigned long long)t);
 }
 
-// Outputs of one angle row u from its fixed-point sums src[0..B), and the
-// row's sum of squares in a fixed order (lane partials over k, then a
-// butterfly), so that it does not depend on how the sums were formed.  clear:
-// leave src zero.
-__device__ __forceinline__ void finish_row(const ProjArgs& a, int item, int u, int F, long long* src, bool clear,
-                                           int lane) {
+// Outputs of cell (u, k) of image item from its fixed-point sum; returns
+// (P_c - P_m)^2 (RESYNC, SIRT; else 0) and, for RESYNC, the drift.
+__device__ __forceinline__ double cell_output(const ProjArgs& a, int item, int u, int k, long long raw, int F,
+                                              float* drift) {
     const int B = a.B;
-    double sq = 0.0;
-    float drift = 0.0f;
-    for (int k = lane; k < B; k += 32) {
-        const long long cell = (long long)u * B + k;
-        const long long raw = src[k];
-        if (clear) src[k] = 0;
-        const double val = ldexp((double)raw, -F);
-        switch (a.mode) {
-            case PROJ_FORWARD:
-                a.out64[(long long)item * a.out_stride + cell] = val;
-                break;
-            case PROJ_FACTOR:
-                a.out64[cell] = val;
-                a.out32[cell] = (float)val;
-                break;
-            case PROJ_RESYNC: {
-                const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
-                const float rf = (float)r;
-                const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
-                float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
-                if (a.drift) drift = fmaxf(drift, fabsf(rf - *dst));
-                *dst = rf;
-                sq += r * r;
-                break;
-            }
-            case PROJ_SIRT: {
-                const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
-                const float w = a.w[cell];
-                a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
-                sq += r * r;
-                break;
-            }
+    const long long cell = (long long)u * B + k;
+    const double val = ldexp((double)raw, -F);
+    switch (a.mode) {
+        case PROJ_FORWARD:
+            a.out64[(long long)item * a.out_stride + cell] = val;
+            return 0.0;
+        case PROJ_FACTOR:
+            a.out64[cell] = val;
+            a.out32[cell] = (float)val;
+            return 0.0;
+        case PROJ_RESYNC: {
+            const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
+            const float rf = (float)r;
+            const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
+            float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
+            if (a.drift) *drift = fabsf(rf - *dst);
+            *dst = rf;
+            return r * r;
+        }
+        default: {  // PROJ_SIRT
+            const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
+            const float w = a.w[cell];
+            a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
+            return r * r;
         }
     }
+}
+
+// A row's sum of squares and drift in a fixed order: lane partials over
+// k = lane, lane + 32, ... ascending, then a butterfly; lane 0 stores them.
+__device__ __forceinline__ void store_row_sums(const ProjArgs& a, int item, int u, double sq, float drift,
+                                               int lane) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -141,23 +137,60 @@ __device__ __forceinline__ void finish_row(const ProjArgs& a, int item, int u, i
     }
 }
 
-// Fraction bits of image item's sums: from a bound on |P| (every ray is at
+// Outputs of angle row u from its fixed-point sums src[0..B), one warp.
+__device__ __forceinline__ void finish_row(const ProjArgs& a, int item, int u, int F, const long long* src,
+                                           int lane) {
+    double sq = 0.0;
+    float drift = 0.0f;
+    for (int k = lane; k < a.B; k += 32) {
+        float d = 0.0f;
+        sq += cell_output(a, item, u, k, src[k], F, &d);
+        drift = fmaxf(drift, d);
+    }
+    store_row_sums(a, item, u, sq, drift, lane);
+}
+
+constexpr int kScaleParts = 32;  // blocks per image finding max|f| in chunked launches
+
+__device__ __forceinline__ int fraction_bits_of_max(const ProjArgs& a, float m) {
+    if (a.mode == PROJ_FACTOR) return fixed_point_bits(2.0 * (1.4142135623730951 * a.n + 2.0));
+    return fixed_point_bits(1.5 * (double)m * (1.4142135623730951 * a.n + 2.0));
+}
+
+// Fraction bits of image item's sums, from a bound on |P| (every ray is at
 // most sqrt(2)*n + 2 long).  All threads of the block must call it.
 __device__ int item_fraction_bits(const ProjArgs& a, int item, float* red) {
-    if (a.mode == PROJ_FACTOR) return fixed_point_bits(2.0 * (1.4142135623730951 * a.n + 2.0));
+    if (a.mode == PROJ_FACTOR) return fraction_bits_of_max(a, 0.0f);
     const float* img = a.img + (long long)item * a.img_stride;
     const long long P = (long long)a.n * a.n;
     float m = 0.0f;
     for (long long q = threadIdx.x; q < P; q += blockDim.x) m = fmaxf(m, fabsf(img[q]));
-    m = block_max(m, red);
-    return fixed_point_bits(1.5 * (double)m * (1.4142135623730951 * a.n + 2.0));
+    return fraction_bits_of_max(a, block_max(m, red));
 }
 
-// Chunked launches: the fraction bits of every image, once.
+// The same bits from the kScaleParts partial maxima of a chunked launch
+// (called by a whole warp).
+__device__ __forceinline__ int item_fraction_bits_parts(const ProjArgs& a, int item, int lane) {
+    float m = a.max_parts[(long long)item * kScaleParts + lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return fraction_bits_of_max(a, m);
+}
+
+// Chunked launches: max|f| of each image in kScaleParts pieces.
 __global__ void __launch_bounds__(kProjThreads) proj_scale_kernel(ProjArgs a) {
     __shared__ float red_f[kProjThreads];
-    const int F = item_fraction_bits(a, blockIdx.x, red_f);
-    if (threadIdx.x == 0) a.fbits[blockIdx.x] = F;
+    const int item = blockIdx.y, part = blockIdx.x;
+    const long long P = (long long)a.n * a.n;
+    const long long per = (P + kScaleParts - 1) / kScaleParts;
+    const long long q0 = part * per, q1 = min(P, q0 + per);
+    float m = 0.0f;
+    if (a.mode != PROJ_FACTOR) {
+        const float* img = a.img + (long long)item * a.img_stride;
+        for (long long q = q0 + threadIdx.x; q < q1; q += kProjThreads) m = fmaxf(m, fabsf(img[q]));
+    }
+    m = block_max(m, red_f);
+    if (threadIdx.x == 0) a.max_parts[(long long)item * kScaleParts + part] = m;
 }
 
 // One CTA per (group of 2^l angles, image, pixel chunk).  A warp takes
@@ -182,8 +215,18 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     const float* img = a.img ? a.img + (long long)item * a.img_stride : nullptr;
 
     for (int e = tid; e < A * B; e += kProjThreads) acc[e] = 0;
-    const int F = a.chunks > 1 ? a.fbits[item] : item_fraction_bits(a, item, red_f);
+    __shared__ int F_sh;
+    if (a.chunks > 1) {
+        if (warp == 0) {
+            const int f = item_fraction_bits_parts(a, item, lane);
+            if (lane == 0) F_sh = f;
+        }
+    } else {
+        const int f = item_fraction_bits(a, item, red_f);
+        if (tid == 0) F_sh = f;
+    }
     __syncthreads();
+    const int F = F_sh;
 
     // pixel indices fit in 32 bits (pila_build caps n * n at 2^30)
     const int Pi = a.n * a.n;
@@ -231,22 +274,54 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
     __syncthreads();
 
     if (a.chunks == 1) {
-        for (int r = warp; r < A; r += nwarps) finish_row(a, item, u0 + r, F, acc + r * B, false, lane);
+        for (int r = warp; r < A; r += nwarps) finish_row(a, item, u0 + r, F, acc + r * B, lane);
     } else {
-        // rows u0 .. u0 + A - 1 of the image are contiguous in acc_global
-        unsigned long long* dst =
-            reinterpret_cast<unsigned long long*>(a.acc_global + ((long long)item * a.U + u0) * B);
-        for (int e = tid; e < A * B; e += kProjThreads)
-            if (acc[e] != 0) atomicAdd(dst + e, (unsigned long long)acc[e]);
+        // the chunk's sums, rows u0 .. u0 + A - 1 (contiguous), into its own slice
+        long long* dst = a.partial + (((long long)item * a.chunks + chunk) * a.U + u0) * B;
+        for (int e = tid; e < A * B; e += kProjThreads) dst[e] = acc[e];
     }
 }
 
-// Chunked launches: one warp per angle row of an image.
-__global__ void __launch_bounds__(kProjThreads) proj_finish_kernel(ProjArgs a) {
+// Chunked launches, step 1: one thread per cell sums the chunks' slices
+// (exact integer adds), writes the outputs, and leaves the cell's square and
+// drift in slice 0 and 1 of the cell (read by step 2 only).
+__global__ void proj_finish_cells_kernel(ProjArgs a) {
     const int item = blockIdx.y;
-    const int u = blockIdx.x * (kProjThreads / 32) + (threadIdx.x >> 5);
+    const long long cells = (long long)a.U * a.B;
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int F_sh;
+    if (threadIdx.x < 32) {  // the whole first warp, before any thread leaves
+        const int f = item_fraction_bits_parts(a, item, threadIdx.x);
+        if (threadIdx.x == 0) F_sh = f;
+    }
+    __syncthreads();
+    if (cell >= cells) return;
+    long long* src = a.partial + (long long)item * a.chunks * cells + cell;
+    long long raw = 0;
+    for (int c = 0; c < a.chunks; ++c) raw += src[c * cells];
+    const int u = (int)(cell / a.B), k = (int)(cell - (long long)u * a.B);
+    float drift = 0.0f;
+    const double sq = cell_output(a, item, u, k, raw, F_sh, &drift);
+    src[0] = __double_as_longlong(sq);
+    src[cells] = (long long)__float_as_int(drift);
+}
+
+// Step 2: one warp per angle row, the row sums in the same fixed order as an
+// unchunked launch.
+constexpr int kFinishWarps = 4;
+__global__ void __launch_bounds__(32 * kFinishWarps) proj_finish_rows_kernel(ProjArgs a) {
+    const int item = blockIdx.y, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * kFinishWarps + (threadIdx.x >> 5);
     if (u >= a.U) return;
-    finish_row(a, item, u, a.fbits[item], a.acc_global + ((long long)item * a.U + u) * a.B, true, threadIdx.x & 31);
+    const long long cells = (long long)a.U * a.B;
+    const long long* src = a.partial + (long long)item * a.chunks * cells + (long long)u * a.B;
+    double sq = 0.0;
+    float drift = 0.0f;
+    for (int k = lane; k < a.B; k += 32) {
+        sq += __longlong_as_double(src[k]);
+        drift = fmaxf(drift, __int_as_float((int)src[cells + k]));
+    }
+    store_row_sums(a, item, u, sq, drift, lane);
 }
 
 // One warp per item: lane partials over u = lane, lane + 32, ... in order,
@@ -294,10 +369,11 @@ int projector_plan(int U, int B, int n, long long n_items, bool can_chunk, int* 
     long long G = (U + (1 << l) - 1) >> l;
     *chunks = 1;
     if (n_items * G < target) {
-        if (can_chunk) {
-            // split the pixels: chunks of at least 1024 pixels
-            const long long P = (long long)n * n;
-            *chunks = (int)std::max(1LL, std::min((target + n_items * G - 1) / (n_items * G), P / 1024));
+        const long long P = (long long)n * n;
+        if (can_chunk && P / 1024 >= 2) {
+            // split the pixels: chunks of at least 1024 pixels, several CTAs per SM
+            const long long want = 4 * target;
+            *chunks = (int)std::max(2LL, std::min((want + n_items * G - 1) / (n_items * G), P / 1024));
         } else {
             // narrower groups: the widest that still gives enough CTAs
             while (l > 0 && n_items * ((U + (1 << l) - 1) >> l) < target) --l;
@@ -310,9 +386,11 @@ int projector_plan(int U, int B, int n, long long n_items, bool can_chunk, int* 
     return SATPILA_OK;
 }
 
-size_t projector_ws_bytes(long long n_items, int U, int B) {
-    return round_up((size_t)n_items * U * B * sizeof(long long), 256) +
-           round_up((size_t)n_items * sizeof(int), 256);
+size_t projector_ws_bytes(long long n_items, int U, int B, int n) {
+    int A = 0, G = 0, l = 0, chunks = 1;
+    if (projector_plan(U, B, n, n_items, true, &A, &G, &l, &chunks) != SATPILA_OK || chunks <= 1) return 0;
+    return round_up((size_t)n_items * chunks * U * B * sizeof(long long), 256) +
+           round_up((size_t)n_items * kScaleParts * sizeof(float), 256);
 }
 
 // The projector's shared-memory limit, set once per device (before any
@@ -335,25 +413,27 @@ cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s) {
     if (projector_plan(a.U, a.B, a.n, n_items, a.ws != nullptr, &a.angles_per_group, &a.n_groups, &a.lanes_log2,
                        &a.chunks) != SATPILA_OK)
         return cudaErrorInvalidValue;
-    a.acc_global = nullptr;
-    a.fbits = nullptr;
+    a.partial = nullptr;
+    a.max_parts = nullptr;
     if (a.chunks > 1) {
-        a.acc_global = reinterpret_cast<long long*>(a.ws);
-        a.fbits = reinterpret_cast<int*>(reinterpret_cast<char*>(a.ws) +
-                                         round_up((size_t)n_items * a.U * a.B * sizeof(long long), 256));
+        a.partial = reinterpret_cast<long long*>(a.ws);
+        a.max_parts = reinterpret_cast<float*>(reinterpret_cast<char*>(a.ws) +
+                                               round_up((size_t)n_items * a.chunks * a.U * a.B * sizeof(long long), 256));
     }
     const int smem = projector_smem_bytes(a.angles_per_group, a.B);
     cudaError_t e = prepare_projector();
     if (e != cudaSuccess) return e;
     if (a.chunks > 1) {
-        proj_scale_kernel<<<n_items, kProjThreads, 0, s>>>(a);
+        proj_scale_kernel<<<dim3(kScaleParts, n_items), kProjThreads, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     projector_kernel<<<dim3(a.n_groups, n_items, a.chunks), kProjThreads, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.chunks > 1) {
-        constexpr int rows_per_block = kProjThreads / 32;
-        proj_finish_kernel<<<dim3((a.U + rows_per_block - 1) / rows_per_block, n_items), kProjThreads, 0, s>>>(a);
+        const long long cells = (long long)a.U * a.B;
+        proj_finish_cells_kernel<<<dim3((unsigned)((cells + 255) / 256), n_items), 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        proj_finish_rows_kernel<<<dim3((a.U + kFinishWarps - 1) / kFinishWarps, n_items), 32 * kFinishWarps, 0, s>>>(a);
         e = cudaGetLastError();
     }
     return e;
@@ -430,9 +510,7 @@ extern "C" int pila_forward(const satpila_pila* p, int32_t n_images, const float
     int A = 0, G = 0, l = 0, chunks = 1;
     // few images: a stream-ordered workspace lets their pixels spread over more CTAs
     if (projector_plan(p->U, p->B, p->n, n_images, true, &A, &G, &l, &chunks) == SATPILA_OK && chunks > 1) {
-        const size_t bytes = projector_ws_bytes(n_images, p->U, p->B);
-        e = cudaMallocAsync(&ws, bytes, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, bytes, s);
+        e = cudaMallocAsync(&ws, projector_ws_bytes(n_images, p->U, p->B, p->n), s);
         a.ws = ws;
     }
     if (e == cudaSuccess) e = launch_projector(a, n_images, s);

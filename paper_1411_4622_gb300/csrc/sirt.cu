@@ -122,11 +122,11 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     const size_t o_psq = o_corr + ((size_t)n_slices * cells * 4 + 255) / 256 * 256;
     const size_t o_cost = o_psq + ((size_t)n_slices * G * 8 + 255) / 256 * 256;
     const size_t o_proj = o_cost + ((size_t)n_slices * 8 + 255) / 256 * 256;
-    const size_t total = o_proj + projector_ws_bytes(n_slices, p->U, p->B);
+    const size_t proj_ws = projector_ws_bytes(n_slices, p->U, p->B, p->n);
+    const size_t total = o_proj + proj_ws;
     SP_CUDA(cudaMalloc(&ws, total));
     char* b = (char*)ws;
-    // the projector's workspace starts zero (and stays so between launches)
-    cudaError_t e = cudaMemsetAsync(b + o_proj, 0, total - o_proj, s);
+    cudaError_t e = cudaSuccess;
     if (e == cudaSuccess && !dev_s) {
         d_sino = (const float*)(b + o_sino);
         e = cudaMemcpyAsync((void*)d_sino, sino_meas, bytes_sino, cudaMemcpyHostToDevice, s);
@@ -155,7 +155,7 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     pa.resid_stride = cells;
     pa.w = p->d_w32;
     pa.part_sq = psq;
-    pa.ws = b + o_proj;
+    pa.ws = proj_ws ? b + o_proj : nullptr;
     ReduceArgs ra{};
     ra.n_items = n_slices;
     ra.n_rows = G;
@@ -279,8 +279,9 @@ extern "C" int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const f
                                                  " bytes of scratch, more than the static " +
                                                  std::to_string((size_t)SATPILA_NOALLOC_SCRATCH_BYTES));
     // the projector's workspace (pixel chunks for few slices) when it fits
-    const bool chunk_ws = total + projector_ws_bytes(n_slices, p->U, p->B) <= (size_t)SATPILA_NOALLOC_SCRATCH_BYTES;
-    if (chunk_ws) total += projector_ws_bytes(n_slices, p->U, p->B);
+    const size_t proj_ws = projector_ws_bytes(n_slices, p->U, p->B, p->n);
+    const bool chunk_ws = proj_ws > 0 && total + proj_ws <= (size_t)SATPILA_NOALLOC_SCRATCH_BYTES;
+    if (chunk_ws) total += proj_ws;
     void* base = nullptr;
     int rc = noalloc_scratch(&base);
     if (rc != SATPILA_OK) return rc;
