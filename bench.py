@@ -37,7 +37,9 @@ WORKLOAD = "batch128x512"
 PLAN_NAMES = {0: "rules", 1: "autotuned: windowed, band residual in shared memory",
               2: "autotuned: windowed, residual in global memory", 3: "autotuned: windowed hybrid",
               4: "autotuned: pipelined, 1 warp per chain", 5: "autotuned: pipelined, 2 warps per chain",
-              6: "autotuned: pipelined, 4 warps per chain"}
+              6: "autotuned: pipelined, 4 warps per chain",
+              7: "autotuned: windowed, 2 warps per chain, residual in global memory",
+              8: "autotuned: windowed, 4 warps per chain, residual in global memory"}
 METRIC = "SAT pixel-moves/s at equal final RMSE (batched vs plain); slice p50/p99 ms"
 UNIT = "pixel-moves/s"
 

@@ -143,6 +143,8 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
                                  Draw 2 + e is estimate e's value, draw 0 (e = 0) or
                                  2 + bome_k + e - 1 (e >= 1) picks its pixel; the trace records
                                  the chosen estimate's pixel.  Residual in global memory. */
+#define SAT_FLAG_WINDOW_GROUPS 16u /* with group_warps 2 or 4 (and no autotuning): the windowed
+                                 move on that many warps per chain, residual in global memory */
 
 typedef struct {
     int32_t pixel;     /* pixel index i*n + j */
@@ -192,9 +194,9 @@ typedef struct {
 } sat_stats;
 
 /* Launch layouts (sat_stats.plan).  They differ in how chains map onto the
- * GPU, not in the moves: a layout with one warp per chain uses the windowed
- * form of the move (exact in-window corrections), the pipelined layouts the
- * per-move form; both follow Eq. (7) to FP32 rounding. */
+ * GPU, not in the moves: the windowed layouts use the windowed form of the
+ * move (exact in-window corrections), the pipelined layouts the per-move
+ * form; both follow Eq. (7) to FP32 rounding. */
 #define SAT_PLAN_RULES 0         /* chosen by size rules (no autotuning) */
 #define SAT_PLAN_WINDOW_SMEM 1   /* one warp per chain, residual band in shared memory */
 #define SAT_PLAN_WINDOW_GLOBAL 2 /* one warp per chain, residual in global memory */
@@ -202,6 +204,8 @@ typedef struct {
 #define SAT_PLAN_PIPE_1 4        /* pipelined, 1 warp per chain */
 #define SAT_PLAN_PIPE_2 5        /* pipelined, 2 warps per chain */
 #define SAT_PLAN_PIPE_4 6        /* pipelined, 4 warps per chain */
+#define SAT_PLAN_WINDOW_G2 7     /* windowed, 2 warps per chain, residual in global memory */
+#define SAT_PLAN_WINDOW_G4 8     /* windowed, 4 warps per chain, residual in global memory */
 
 /*
  * Anneal n_chains independent slices that share one PILA.  Chain c reads its

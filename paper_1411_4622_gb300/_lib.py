@@ -19,8 +19,9 @@ PILA_F32, PILA_F16, PILA_U8 = 0, 1, 2
 SAT_SCHED_LINEAR, SAT_SCHED_GEOMETRIC, SAT_SCHED_CUBIC = 0, 1, 2
 SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
 SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID, SAT_FLAG_BOME_INDEPENDENT = 1, 2, 4, 8
+SAT_FLAG_WINDOW_GROUPS = 16
 (SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
- SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4) = range(7)
+ SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4) = range(9)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).

@@ -18,8 +18,9 @@ from ._lib import (PILA_F16, PILA_F32, PILA_U8, SAT_FLAG_AUTOTUNE, SAT_FLAG_BOME
                    SAT_RESIDENT_GLOBAL, SAT_RESIDENT_SMEM, SAT_SCHED_CUBIC, SAT_SCHED_GEOMETRIC,
                    SAT_SCHED_LINEAR, SIRT_SEQUENTIAL, SIRT_SIMULTANEOUS, SatpilaError)
 from ._lib import ERR_BUSY, ERR_INVALID_ARG, ERR_NOT_FOUND, ERR_PENDING  # noqa: F401
-from ._lib import (SAT_PLAN_PIPE_1, SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_RULES,  # noqa: F401
-                   SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_WINDOW_SMEM)
+from ._lib import (SAT_FLAG_WINDOW_GROUPS, SAT_PLAN_PIPE_1, SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4,  # noqa: F401
+                   SAT_PLAN_RULES, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4, SAT_PLAN_WINDOW_GLOBAL,
+                   SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_WINDOW_SMEM)
 
 TRACE_DTYPE = np.dtype([("pixel", "<i4"), ("cstar", "<i4"), ("accepted", "<i4"), ("pad", "<i4"),
                         ("dS", "<f4"), ("dC", "<f4"), ("fnew", "<f4"), ("pad2", "<f4")])

@@ -32,14 +32,17 @@ SweepFn sweep_kernel_f16_glob(int jmax, int kmax);
 SweepFn window_kernel(int rt, bool smem, int jmax, int kmax);
 SweepFn hybrid_kernel(int rt, int jmax, int kmax);
 SweepFn bome_kernel(bool f16, int jmax, int kmax);
+SweepFn window_group_kernel(int rt, int jmax, int kmax, int warps_per_chain);
 int bome_warps_per_cta();
 
 namespace {
 
-// kind: 0 pipelined, 1 windowed, 2 hybrid, 3 independent-pixel BoME; rt: the
-// table precision (one-byte tables are read by the windowed kernel only)
+// kind: 0 pipelined, 1 windowed, 2 hybrid, 3 independent-pixel BoME, 4 and 5
+// windowed on groups of 2 and 4 warps per chain; rt: the table precision
+// (one-byte tables are read by the one-warp windowed kernel only)
 SweepFn sweep_kernel(int rt, bool smem, int jmax, int kmax, int kind = 0) {
     if (kind == 1) return window_kernel(rt, smem, jmax, kmax);
+    if (kind == 4 || kind == 5) return smem ? nullptr : window_group_kernel(rt, jmax, kmax, kind == 4 ? 2 : 4);
     if (rt == PILA_U8) return nullptr;
     const bool f16 = rt == PILA_F16;
     if (kind == 2) return hybrid_kernel(rt, jmax, kmax);
@@ -196,6 +199,11 @@ size_t Plan::sweep_smem_bytes() const {
 }
 
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl) {
+    if (variant == PLAN_RULES && (prm->flags & SAT_FLAG_WINDOW_GROUPS)) {
+        if (prm->group_warps != 2 && prm->group_warps != 4)
+            return fail(SATPILA_ERR_INVALID_ARG, "sat_run: SAT_FLAG_WINDOW_GROUPS needs group_warps 2 or 4");
+        variant = prm->group_warps == 2 ? PLAN_WINDOW_G2 : PLAN_WINDOW_G4;
+    }
     const int rt = p->precision;
     const bool f16 = rt == PILA_F16;
     const int rpc = rt == PILA_U8 ? 4 : f16 ? 2 : 1;  // records per 16-byte chunk
@@ -252,6 +260,36 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
         pl->spt = n_chains <= slots ? window : 1;
         const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
         const long long want = (std::min<long long>(tasks, slots) + pl->warps - 1) / pl->warps;
+        pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
+        return SATPILA_OK;
+    }
+    // The windowed kernel on groups of 2 or 4 warps per chain (their lanes
+    // split the angles), residual in global memory: one gather round trip and
+    // one exchange of sums between the warps per window of moves.
+    if (variant == PLAN_WINDOW_G2 || variant == PLAN_WINDOW_G4) {
+        const int Wg = variant == PLAN_WINDOW_G2 ? 2 : 4;
+        if (rt == PILA_U8 || prm->residency == SAT_RESIDENT_SMEM || records_per_lane(Wg) > 4)
+            return fail(SATPILA_ERR_INVALID_ARG, "sat_run: no windowed group launch for this table");
+        const int jw = records_per_lane(Wg) <= 2 ? 2 : 4;
+        const int stage = 512 * Wg * (jw / rpc);
+        const size_t glob = align_up(group_ring_bytes(Wg) + (size_t)2 * kWin * stage, 128);
+        const int kmax = kmax_for(prm->bome_k);
+        const int groups = std::max(1, std::min(kSatMaxWarps / Wg, std::min(n_chains, (int)(maxopt / glob))));
+        pl->kind = Wg == 2 ? 4 : 5;
+        pl->smem = false;
+        pl->W = Wg;
+        pl->J = pl->jmax = jw;
+        pl->D = 4;
+        pl->stage_bytes = stage;
+        pl->group_smem = (int)glob;
+        pl->groups = groups;
+        pl->warps = groups * Wg;
+        int per_sm = sweep_blocks_per_sm(rt, false, pl->kind, jw, kmax, pl->warps, (size_t)groups * glob);
+        if (per_sm < 1) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: windowed group launch does not fit");
+        const long long slots = (long long)sms * per_sm * groups;
+        pl->spt = n_chains <= slots ? window : 1;
+        const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
+        const long long want = (std::min<long long>(tasks, slots) + groups - 1) / groups;
         pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
         return SATPILA_OK;
     }

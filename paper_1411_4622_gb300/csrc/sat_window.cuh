@@ -1,6 +1,8 @@
 // Windowed form of the annealing move for one warp per chain, with the
-// residual in shared memory or in global memory (identical arithmetic).
-// Windows of kWin = 2 moves; the notes below hold for any kWin dividing 4.
+// residual in shared memory or in global memory (identical arithmetic), or
+// for a group of WG = 2 or 4 warps per chain that split its angles, with the
+// residual in global memory.  Windows of kWin = 2 moves; the notes below hold
+// for any kWin dividing 4.
 //
 // Moves are still decided one after the other, each on the exact state left
 // by all earlier moves; what changes is how that state is read.  For a window
@@ -31,7 +33,7 @@ __device__ __forceinline__ void cell_share(int ki, float a0, float a1, int kj, f
     s1 = d == 0 ? a1 : (d == -1 ? a0 : 0.0f);
 }
 
-template <int RT, bool SMEM, int JMAX, int KMAX>
+template <int RT, bool SMEM, int JMAX, int KMAX, int WG = 1>
 __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupShared& G, const StageCtx& x,
                                                  float& S_hi, float& S_lo, unsigned long long& n_acc,
                                                  const int (&rowbase)[JMAX]) {
@@ -49,7 +51,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                 unsigned char* st = stage_of(w, j);
 #pragma unroll
                 for (int i = 0; i < rt_chunks_per_lane<RT, JMAX>(); ++i) {
-                    const int q = x.gl + 32 * i;
+                    const int q = x.gl + 32 * WG * i;
                     cp_async_16_pred(q < a.row_chunks, st + 16 * q, row + 16 * (q < a.row_chunks ? q : 0));
                 }
             }
@@ -109,7 +111,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
             Recs<JMAX> r;
-            rt_decode_stage<RT, JMAX>(stage_of(w, j), x.gl, 1, r);
+            rt_decode_stage<RT, JMAX>(stage_of(w, j), x.gl, WG, r);
 #pragma unroll
             for (int s = 0; s < JMAX; ++s) {
                 k[j][s] = r.k[s];
@@ -156,6 +158,26 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
             for (int e = 0; e < kWin + kPairs; ++e) red[e] += __shfl_xor_sync(0xffffffffu, red[e], o);
+        if constexpr (WG > 1) {
+            // each warp holds the sums over its own angles: add the warps'
+            // sums in warp order (the same order in every warp).  Slots
+            // alternate with the window parity; a warp can be at most one
+            // window ahead of the others, so a slot is never overwritten
+            // while another warp still reads it.
+            float* xr = G.part + (w & 1) * (4 * kMaxGroupWarps);
+            float mine = 0.0f;
+#pragma unroll
+            for (int e = 0; e < kWin + kPairs; ++e) mine = x.lane == e ? red[e] : mine;
+            if (x.lane < kWin + kPairs) xr[4 * x.wig + x.lane] = mine;
+            group_sync(x.gid, WG);
+#pragma unroll
+            for (int e = 0; e < kWin + kPairs; ++e) {
+                float t = xr[e];
+#pragma unroll
+                for (int q = 1; q < WG; ++q) t += xr[4 * q + e];
+                red[e] = t;
+            }
+        }
 
         // ---- decisions, in move order ----
         float df[kWin], fnew[kWin];
@@ -247,7 +269,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             const bool accept = live && (xs <= 0.0f || xm < 0.0f || xm * xm < rhs);
             df[j] = accept ? fcand[0] - f : 0.0f;
             fnew[j] = accept ? fcand[0] : f;
-            if (x.tracing && live && x.lane == 0) {
+            if (x.tracing && live && x.gl == 0) {
                 const float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
                 const float Cp = sqrtf(fmaxf(0.0f, fmaf(C, C, xs)));
                 const float den = Cp + C;
@@ -519,6 +541,102 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const Sat
         window_warp<RT, false, JMAX, KMAX>(a, smem + (size_t)ns * a.group_smem_bytes + (size_t)g * a.hybrid_glob_bytes,
                                             warp, lane);
     }
+}
+
+// Task loop of a chain group: WG warps that split the chain's angles (group
+// lane gl = lane + 32 * wig, named barrier 1 + grp), residual in global
+// memory.  Every warp takes every decision itself (the same sums, draws and
+// pixel values) and writes the same pixel values, so the warps exchange
+// only the window sums; the residual cells of an angle belong to one lane.
+template <int RT, int JMAX, int KMAX, int WG>
+__device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb, int grp, int wig, int lane) {
+    GroupShared G;
+    G.bar = reinterpret_cast<uint64_t*>(gb);
+    G.part = reinterpret_cast<float*>(gb + 64);
+    G.flags = reinterpret_cast<volatile int*>(gb + 192);
+    G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * kDrawRingBytes);
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * kDrawRingBytes + kDrawRing * 4);
+    G.stages = gb + group_ring_bytes(WG);
+    const int gl = lane + 32 * wig, gid = 1 + grp;
+
+    for (int e = gl; e < 2 * kWin * a.stage_bytes / 16; e += 32 * WG)
+        reinterpret_cast<uint4*>(G.stages)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (gl == 0)
+        for (int i = 0; i < 8; ++i) G.flags[i] = 0;
+    group_sync(gid, WG);
+
+    // Cell (u, k) of the residual: R[rowbase + k]; group lanes past the last
+    // angle address two dummy cells of their own after the rows.
+    int rowbase[JMAX];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const int u = rt_record_of<RT>(gl, WG, j);
+        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * gl;
+    }
+
+    for (;;) {
+        if (gl == 0) G.flags[0] = atomicAdd(a.task_counter, 1);
+        group_sync(gid, WG);
+        const int t = G.flags[0];
+        group_sync(gid, WG);
+        if (t >= a.n_tasks) break;
+        const int c = t % a.n_chains;
+        const int blk = t / a.n_chains;
+        const int s0 = a.sweep_begin + blk * a.sweeps_per_task;
+        const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
+        if (blk > 0) {
+            if (gl == 0) G.flags[2] = wait_progress(&a.progress[c], s0) ? 1 : 0;
+            group_sync(gid, WG);
+            const int ok = G.flags[2];
+            group_sync(gid, WG);
+            if (!ok) {
+                if (gl == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                break;
+            }
+        }
+        const double S = a.S[c];
+        float S_hi = (float)S;
+        float S_lo = -(float)(S - (double)S_hi);
+        unsigned long long n_acc = 0;
+        StageCtx x;
+        x.M = a.moves;
+        x.D = a.D;
+        x.W = WG;
+        x.wig = wig;
+        x.lane = lane;
+        x.gid = gid;
+        x.gl = gl;
+        x.R = a.resid + (long long)c * a.resid_floats;
+        x.img = a.img + (long long)c * a.img_stride;
+        const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
+        const int s_base = cc ? cc->stage0 : 0, s_total = cc ? cc->n_sweeps : a.n_sweeps_total;
+        const int sched = cc ? cc->schedule : a.schedule;
+        x.key = chain_key(cc ? cc->seed : a.seed + (unsigned long long)c);
+        x.tracing = a.trace != nullptr && c == a.trace_chain;
+        const double T0 = a.T0[c], TN = a.TN[c];
+        for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
+            x.s = s_base + s;
+            x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
+            run_stage_window<RT, false, JMAX, KMAX, WG>(a, G, x, S_hi, S_lo, n_acc, rowbase);
+            if (a.sweep_cost && gl == 0)
+                a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
+        }
+        if (gl == 0) {
+            a.S[c] = (double)S_hi - (double)S_lo;
+            a.accepted[c] += n_acc;
+        }
+        __threadfence();
+        group_sync(gid, WG);
+        if (gl == 0) st_release(&a.progress[c], s1);
+    }
+}
+
+template <int RT, int JMAX, int KMAX, int WG>
+__global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_group_kernel(const SatArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = warp / WG;
+    window_group<RT, JMAX, KMAX, WG>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG, lane);
 }
 
 }  // namespace satpila

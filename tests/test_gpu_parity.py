@@ -586,6 +586,41 @@ def test_window_angle_limit(api, U):
     api.pila_free(p)
 
 
+@pytest.mark.parametrize("W,U,prec", [(2, 180, 0), (4, 180, 1), (4, 360, 1), (2, 90, 1)])
+def test_window_groups_lockstep(api, W, U, prec):
+    """The windowed move on groups of 2 or 4 warps per chain (residual in
+    global memory; the warps exchange window sums): move by move against the
+    oracle (the FP16 table over binary16 lengths), with 2 and 4 record slots
+    per lane, and a chain in a batch equal to its run alone."""
+    n = 48
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    pm = synth.gaussian_noise(oracle.drt(synth.phantom(n, 8, 1006), U, B), 0.01, 2006).astype(np.float32)
+    img0 = synth.initial_image(n, 0.5, mask)
+    S, M = 2, 1500
+    fmt = oracle.LEN_EXACT if prec == api.PILA_F32 else oracle.LEN_BINARY16
+    p = api.pila_build(n, U, B, prec, mask=mask)
+    kw = dict(bome_k=8, t0=-1.0, tn=-1.0, seed=3006, moves_per_sweep=M, group_warps=W,
+              flags=api.SAT_FLAG_WINDOW_GROUPS)
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, **kw)
+    assert st["status"] == 0 and st["proposed"] == S * M
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=8, n_sweeps=S, seed=3006,
+                                 moves_per_sweep=M, mask=mask, length_format=fmt)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5, rep
+    # batch of 5 chains: chain 3 equals its run alone
+    sinos = np.stack([pm] * 5)
+    imgs = dev(np.stack([img0] * 5))
+    kwb = {k: v for k, v in kw.items() if k != "seed"}
+    stb = api.sat_run(p, dev(sinos), imgs, n_sweeps=S, seed=500, **kwb)
+    one = dev(img0[None])
+    st1 = api.sat_run(p, dev(pm[None]), one, n_sweeps=S, seed=503, **kwb)
+    assert np.array_equal(imgs.cpu().numpy()[3], one.cpu().numpy()[0])
+    assert stb[3]["accepted"] == st1[0]["accepted"]
+    api.pila_free(p)
+
+
 def test_hybrid_batch_matches_single_chains(api):
     """More chains than shared-memory slots: the batch runs on shared-memory
     and global-memory warps side by side, with chains moving between them
@@ -653,7 +688,7 @@ def test_autotune_picks_a_layout_and_is_repeatable(api):
         imgs = dev(img0)
         st = api.sat_run(p, dev(sinos), imgs, flags=api.SAT_FLAG_AUTOTUNE, **kw)
         assert all(s["status"] == 0 for s in st)
-        assert 1 <= st[0]["plan"] <= 6
+        assert 1 <= st[0]["plan"] <= 8
         outs.append((imgs.cpu().numpy(), [s["plan"] for s in st], [s["accepted"] for s in st]))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
     rule = dev(img0)
