@@ -34,12 +34,11 @@ sys.path.insert(0, ROOT)
 from paper_1411_4622_gb300 import shard, synth  # noqa: E402
 
 WORKLOAD = "batch128x512"
-PLAN_NAMES = {0: "rules", 1: "autotuned: windowed, band residual in shared memory",
-              2: "autotuned: windowed, residual in global memory", 3: "autotuned: windowed hybrid",
-              4: "autotuned: pipelined, 1 warp per chain", 5: "autotuned: pipelined, 2 warps per chain",
-              6: "autotuned: pipelined, 4 warps per chain",
-              7: "autotuned: windowed, 2 warps per chain, residual in global memory",
-              8: "autotuned: windowed, 4 warps per chain, residual in global memory"}
+PLAN_NAMES = {0: "independent-pixel BoME kernel", 1: "windowed, band residual in shared memory",
+              2: "windowed, residual in global memory", 3: "windowed hybrid",
+              4: "pipelined, 1 warp per chain", 5: "pipelined, 2 warps per chain",
+              6: "pipelined, 4 warps per chain", 7: "windowed, 2 warps per chain, residual in global memory",
+              8: "windowed, 4 warps per chain, residual in global memory"}
 METRIC = "SAT pixel-moves/s at equal final RMSE (batched vs plain); slice p50/p99 ms"
 UNIT = "pixel-moves/s"
 
@@ -141,9 +140,23 @@ class ClockSampler:
 
 KERNEL_SOURCES = {
     "sat_window_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window.cu"],
+    "sat_hybrid_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window.cu"],
+    "sat_window_group_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_group.cu"],
     "sat_sweep_kernel": ["common.cuh", "sat_sweep.cuh", "sat_f16_glob.cu", "sat_f16_smem.cu", "sat_f32_glob.cu",
                          "sat_f32_smem.cu"],
 }
+
+
+def launch_name(plan, flags):
+    """The launch layout a run used, and who chose it."""
+    who = "autotuned: " if flags & 2 else "requested: " if flags & 16 else "size rules: "
+    return who + PLAN_NAMES.get(plan, str(plan))
+
+
+# the sweep kernel each launch layout (sat_stats.plan) runs
+PLAN_KERNEL = {1: "sat_window_kernel", 2: "sat_window_kernel", 3: "sat_hybrid_kernel", 4: "sat_sweep_kernel",
+               5: "sat_sweep_kernel", 6: "sat_sweep_kernel", 7: "sat_window_group_kernel",
+               8: "sat_window_group_kernel"}
 
 
 def kernel_source_hash(kernel):
@@ -386,18 +399,20 @@ def run_precision(args):
     useful_bytes = row_bytes + 4.0 * E * (1.0 + acc) + 4.0 * (1.0 + acc)
     rate = moves / (sweep_ms / 1e3)
     achieved = sector_bytes * rate / 1e9
-    tpm = stored_traffic("sat_sweep_kernel", "precision512")
+    kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_sweep_kernel")
+    tpm = stored_traffic(kernel, "precision512")
     out = {"metric": "SAT pixel-moves/s, 512x512 slices (gather throughput)", "value": moves / (ms / 1e3),
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "precision512", "chains": C, "distinct_slices": distinct, "n": n, "angles": U,
                       "bins": B, "bome_k": K, "stages": S, "moves_per_stage": M, "pila": "f16",
-                      "l2": "flushed between timed steps (256 MB write)"},
+                      "l2": "flushed between timed steps (256 MB write)",
+                      "launch": launch_name(st[0]["plan"], args.flags)},
            "acceptance": acc, "sweep_moves_per_s": rate,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": tpm * moves if tpm is not None else None,
                         "traffic_frac": tpm * rate / 1e9 / peak if tpm is not None else None,
-                        "peak_kind": peak_kind, "kernel": "sat_sweep_kernel", "bytes_per_move": sector_bytes,
+                        "peak_kind": peak_kind, "kernel": kernel, "bytes_per_move": sector_bytes,
                         "bytes_per_move_useful": useful_bytes, "frac_useful": useful_bytes * rate / 1e9 / peak,
                         "accounting": "PILA row + one 32-byte sector per touched residual cell group, read and "
                                       "(times acceptance) written", "sweep_ms": sweep_ms},
@@ -736,7 +751,7 @@ def run_rows(args):
     M = int(mask.sum())
     chain = {"stages": stages, "moves_per_stage": M, "sweep_ms": st[0]["sweep_ms"],
              "ms_per_stage": st[0]["sweep_ms"] / stages, "moves_per_s": stages * M / (st[0]["sweep_ms"] / 1e3),
-             "launch": PLAN_NAMES.get(st[0]["plan"], str(st[0]["plan"])), "bome_k": cfg["bome_k"], "pila": "f16"}
+             "launch": launch_name(st[0]["plan"], kw["flags"]), "bome_k": cfg["bome_k"], "pila": "f16"}
     api.pila_free(p)
     api.pila_free(pf)
     out = {"metric": "SIRT-PILA iterations/s, 256x256 slice (180 angles, FP32 table)", "value": sirt["FP32"],
@@ -919,7 +934,7 @@ def main():
     E = info["entries"] / P
     bytes_per_move = info["row_records"] * info["record_bytes"] + 4 * E * (1 + acc) + 4 * (1 + acc)
     achieved = bytes_per_move * moves_per_step / (statistics.mean(sweep_ms) / 1e3) / 1e9
-    kernel = "sat_window_kernel"
+    kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_window_kernel")
     tpm = stored_traffic(kernel)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (tpm * moves_per_step) if tpm is not None else None, "peak_kind": peak_kind,
@@ -932,7 +947,7 @@ def main():
            "config": {"workload": WORKLOAD, "slices_per_gpu": slices, "n": n, "angles": U, "bins": B,
                       "bome_k": K, "stages": S, "moves_per_stage": M, "pila": args.pila,
                       "l2": "flushed between timed steps (256 MB write)",
-                      "launch": PLAN_NAMES.get(st[0]["plan"], str(st[0]["plan"])), "graph": True},
+                      "launch": launch_name(st[0]["plan"], args.flags), "graph": True},
            "evaluations_per_s": value * K, "acceptance": acc,
            "rmse": {"batched_mean": float(rmse_batched.mean())}, "plain": plain,
            "latency_ms": {"slice_p50": float(np.percentile(step_ms, 50)),

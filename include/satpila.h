@@ -189,7 +189,8 @@ typedef struct {
     double sweep_ms;          /* device time of the sweep kernels of this call (same for every chain):
                                  CUDA events on `stream` around each sweep launch (direct launches), or
                                  the device's global timer read just before and after it (graphs) */
-    int32_t plan;             /* SAT_PLAN_* the launches used */
+    int32_t plan;             /* SAT_PLAN_* layout the launches used (SAT_PLAN_RULES: the
+                                 independent-pixel BoME kernel) */
     int32_t pad;
 } sat_stats;
 
@@ -197,7 +198,7 @@ typedef struct {
  * GPU, not in the moves: the windowed layouts use the windowed form of the
  * move (exact in-window corrections), the pipelined layouts the per-move
  * form; both follow Eq. (7) to FP32 rounding. */
-#define SAT_PLAN_RULES 0         /* chosen by size rules (no autotuning) */
+#define SAT_PLAN_RULES 0         /* input: chosen by size rules (no autotuning) */
 #define SAT_PLAN_WINDOW_SMEM 1   /* one warp per chain, residual band in shared memory */
 #define SAT_PLAN_WINDOW_GLOBAL 2 /* one warp per chain, residual in global memory */
 #define SAT_PLAN_WINDOW_HYBRID 3 /* both kinds of warp in one launch */

@@ -172,38 +172,6 @@ __device__ __forceinline__ Entry2 decode_rec(const unsigned char* table, long lo
 
 // ---- exact fixed-point accumulation ------------------------------------------
 
-// round(a * b * 2^F) as a signed 64-bit integer, computed exactly on the
-// integer units: the two 24-bit significands are multiplied into a 48-bit
-// product and shifted by the combined exponent (round half away from zero).
-// The caller picks F so that the result cannot overflow.
-__device__ __forceinline__ long long fixed_product(float a, float b, int F) {
-    const uint32_t ba = __float_as_uint(a), bb = __float_as_uint(b);
-    const uint32_t ea = (ba >> 23) & 0xffu, eb = (bb >> 23) & 0xffu;
-    uint32_t ma = ba & 0x7fffffu, mb = bb & 0x7fffffu;
-    if ((ea | ma) == 0u || (eb | mb) == 0u) return 0;
-    int xa = -149, xb = -149;
-    if (ea) {
-        ma |= 0x800000u;
-        xa = (int)ea - 150;
-    }
-    if (eb) {
-        mb |= 0x800000u;
-        xb = (int)eb - 150;
-    }
-    const unsigned long long m = (unsigned long long)ma * (unsigned long long)mb;
-    const int e = xa + xb + F;
-    unsigned long long v;
-    if (e >= 0) {
-        v = m << e;
-    } else if (e > -64) {
-        const int sh = -e;
-        v = (m >> sh) + ((m >> (sh - 1)) & 1ull);
-    } else {
-        v = 0ull;
-    }
-    return ((ba ^ bb) >> 31) ? -(long long)v : (long long)v;
-}
-
 // Fraction bits F such that sum of |terms| <= bound stays below 2^61.
 __device__ __forceinline__ int fixed_point_bits(double bound) {
     if (!(bound > 0.0)) return 0;

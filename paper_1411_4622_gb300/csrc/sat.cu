@@ -193,6 +193,17 @@ __global__ void copy_f64_kernel(double* dst, const double* src, int n) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+int plan_code(const Plan& pl) {
+    switch (pl.kind) {
+        case 1: return pl.smem ? PLAN_WINDOW_SMEM : PLAN_WINDOW_GLOBAL;
+        case 2: return PLAN_WINDOW_HYBRID;
+        case 0: return pl.W == 1 ? PLAN_PIPE_1 : pl.W == 2 ? PLAN_PIPE_2 : PLAN_PIPE_4;
+        case 4: return PLAN_WINDOW_G2;
+        case 5: return PLAN_WINDOW_G4;
+        default: return PLAN_RULES;  // the independent-pixel BoME kernel
+    }
+}
+
 size_t Plan::sweep_smem_bytes() const {
     return kind == 2 ? (size_t)hybrid_smem_warps * group_smem + (size_t)(warps - hybrid_smem_warps) * hybrid_glob_bytes
                      : (size_t)groups * group_smem;
@@ -1041,7 +1052,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             st.t0_found = found[c];
             st.status = err_code;
             st.sweep_ms = sweep_ms;
-            st.plan = variant;
+            st.plan = variant != PLAN_RULES ? variant : plan_code(pl);
         }
     }
     if (err_code != 0) return fail(err_code, "sat_run: a device-side check failed");

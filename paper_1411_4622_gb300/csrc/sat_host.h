@@ -43,6 +43,10 @@ struct Plan {
     size_t sweep_smem_bytes() const;
 };
 
+// The SAT_PLAN_* code of a plan's launch layout (PLAN_RULES for the
+// independent-pixel BoME kernel, which has no other layout).
+int plan_code(const Plan& pl);
+
 // Launch plan for n_chains chains running `window` stages per sweep launch.
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl);
 

@@ -693,7 +693,7 @@ def test_autotune_picks_a_layout_and_is_repeatable(api):
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
     rule = dev(img0)
     st_r = api.sat_run(p, dev(sinos), rule, **kw)
-    assert st_r[0]["plan"] == 0
+    assert 1 <= st_r[0]["plan"] <= 8  # the layout the size rules chose
     r_tuned = np.mean([synth.rmse(outs[0][0][c], ph[c]) for c in range(C)])
     r_rule = np.mean([synth.rmse(rule.cpu().numpy()[c], ph[c]) for c in range(C)])
     assert abs(r_tuned - r_rule) <= 0.02 * r_rule
