@@ -64,6 +64,8 @@ def parse():
                          "rows: the other steps of the path (table build, forward projection, SIRT, one chain), "
                          "each timed alone")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="serve: arrival rate in requests/s (default: 80%% of the capacity measured on a burst)")
     ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
                     help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
     return ap.parse_args()
@@ -474,7 +476,7 @@ def run_serve(args):
         for x in tk:
             srv.wait(x)
         cap = sum(moves_of[:burst]) / (time.perf_counter() - t)
-        rate = 0.8 * cap / float(np.mean(moves_of))  # requests per second
+        rate = args.rate or 0.8 * cap / float(np.mean(moves_of))  # requests per second
         gaps = rng.exponential(1.0 / rate, size=nreq)
         clocks = ClockSampler(0)
         clocks.start()
@@ -500,7 +502,8 @@ def run_serve(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "serve", "requests": nreq, "sizes": [64, 128, 256, 512], "stages": 50,
                       "k": [1, 4, 8], "pila": "f16", "budget_gb": 120, "arrival": "poisson",
-                      "rate_per_s": rate, "capacity_moves_per_s": cap},
+                      "rate_per_s": rate, "rate_rule": "given" if args.rate else "80% of burst capacity",
+                      "capacity_moves_per_s": cap},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
            "failed": failed, "server": {k: info[k] for k in ("ticks", "bytes_peak", "geometries", "classes")},
            "clocks": clk}

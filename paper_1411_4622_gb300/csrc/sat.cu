@@ -276,7 +276,9 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     }
     // The windowed kernel on groups of 2 or 4 warps per chain (their lanes
     // split the angles), residual in global memory: one gather round trip and
-    // one exchange of sums between the warps per window of moves.
+    // one exchange of sums between the warps per window of moves.  (The size
+    // rules keep the pipelined kernel for wide tables: with it the serving
+    // engine's mixed launches gave lower request latency.)
     if (variant == PLAN_WINDOW_G2 || variant == PLAN_WINDOW_G4) {
         const int Wg = variant == PLAN_WINDOW_G2 ? 2 : 4;
         if (rt == PILA_U8 || prm->residency == SAT_RESIDENT_SMEM || records_per_lane(Wg) > 4)
