@@ -24,63 +24,75 @@
 namespace satpila {
 namespace {
 
+// One thread per (angle u, pixel p): threads of a block span consecutive
+// angles (coalesced record writes), blocks step through the pixels.  The
+// per-angle terms (a, b, half-width, plateau half-width, plateau height, a*b)
+// are the same FP64 expressions for every pixel, so they are formed once.
 __global__ void pila_build_kernel(unsigned char* table, int f16, int row_records, int n, int U, int B,
                                   const double* cs, const double* sn, unsigned long long* entries) {
-    const long long total = (long long)n * n * row_records;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int cnt = 0;
-    int kk[2] = {0, 0};
-    double ll[2] = {0.0, 0.0};
-    if (idx < total) {
-        const int p = (int)(idx / row_records), u = (int)(idx % row_records);
-        if (u < U) {
-            const double c = cs[u], s = sn[u];
-            const double a = fabs(c), b = fabs(s);
-            const int i = p / n, j = p % n;
-            const double x = (double)j - 0.5 * (n - 1), y = 0.5 * (n - 1) - (double)i;
-            const double sp = x * c + y * s;
-            const double half = 0.5 * (a + b), flat = 0.5 * fabs(a - b);
-            const double height = 1.0 / fmax(a, b), ab = a * b;
-            const double centre = 0.5 * (B - 1);
-            const double kfirst = ceil(sp - half + centre);
-            for (int t = 0; t < 2; ++t) {
-                const double kd = kfirst + t;
-                const double d = (kd - centre) - sp;
-                if (d < -half || d >= half) continue;
-                const double dist = fabs(d);
-                const double l = dist <= flat ? height : (half - dist) / ab;
-                if (!(l >= 1e-12)) continue;
-                if (kd < 0.0 || kd >= (double)B) continue;
-                kk[cnt] = (int)kd;
-                ll[cnt] = l;
-                ++cnt;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int P = n * n;  // at most 2^30
+    double c = 0.0, s = 0.0, half = 0.0, flat = 0.0, height = 0.0, ab = 0.0;
+    if (u < U) {
+        c = cs[u];
+        s = sn[u];
+        const double a = fabs(c), b = fabs(s);
+        half = 0.5 * (a + b);
+        flat = 0.5 * fabs(a - b);
+        height = 1.0 / fmax(a, b);
+        ab = a * b;
+    }
+    const double centre = 0.5 * (B - 1);
+    unsigned long long count = 0;
+    if (u < row_records) {
+        for (int p = blockIdx.y; p < P; p += gridDim.y) {
+            int cnt = 0;
+            int kk[2] = {0, 0};
+            double ll[2] = {0.0, 0.0};
+            if (u < U) {
+                const int i = p / n, j = p - i * n;
+                const double x = (double)j - 0.5 * (n - 1), y = 0.5 * (n - 1) - (double)i;
+                const double sp = x * c + y * s;
+                const double kfirst = ceil(sp - half + centre);
+                for (int t = 0; t < 2; ++t) {
+                    const double kd = kfirst + t;
+                    const double d = (kd - centre) - sp;
+                    if (d < -half || d >= half) continue;
+                    const double dist = fabs(d);
+                    const double l = dist <= flat ? height : (half - dist) / ab;
+                    if (!(l >= 1e-12)) continue;
+                    if (kd < 0.0 || kd >= (double)B) continue;
+                    kk[cnt] = (int)kd;
+                    ll[cnt] = l;
+                    ++cnt;
+                }
             }
-        }
-        if (cnt == 0) kk[0] = kk[1] = 0;
-        if (cnt == 1) kk[1] = kk[0];
-        if (f16 == PILA_U8) {
-            // lengths times 180, rounded (at most round(sqrt 2 * 180) = 255)
-            const uint32_t q0 = (uint32_t)fmin(255.0, rint(ll[0] * 180.0));
-            const uint32_t q1 = (uint32_t)fmin(255.0, rint(ll[1] * 180.0));
-            reinterpret_cast<uint32_t*>(table)[idx] = ((uint32_t)(uint16_t)kk[0]) | (q0 << 16) | (q1 << 24);
-            cnt = (q0 != 0u) + (q1 != 0u);
-        } else if (f16) {
-            const __half h0 = __double2half(ll[0]), h1 = __double2half(ll[1]);
-            const uint32_t bins = ((uint32_t)(uint16_t)kk[0]) | ((uint32_t)(uint16_t)kk[1] << 16);
-            const uint32_t lens = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-            reinterpret_cast<uint2*>(table)[idx] = make_uint2(bins, lens);
-            cnt = (__half2float(h0) != 0.0f) + (__half2float(h1) != 0.0f);
-        } else {
-            const float f0 = (float)ll[0], f1 = (float)ll[1];
-            reinterpret_cast<uint4*>(table)[idx] =
-                make_uint4((uint32_t)kk[0], (uint32_t)kk[1], __float_as_uint(f0), __float_as_uint(f1));
-            cnt = (f0 != 0.0f) + (f1 != 0.0f);
+            if (cnt == 0) kk[0] = kk[1] = 0;
+            if (cnt == 1) kk[1] = kk[0];
+            const long long idx = (long long)p * row_records + u;
+            if (f16 == PILA_U8) {
+                // lengths times 180, rounded (at most round(sqrt 2 * 180) = 255)
+                const uint32_t q0 = (uint32_t)fmin(255.0, rint(ll[0] * 180.0));
+                const uint32_t q1 = (uint32_t)fmin(255.0, rint(ll[1] * 180.0));
+                reinterpret_cast<uint32_t*>(table)[idx] = ((uint32_t)(uint16_t)kk[0]) | (q0 << 16) | (q1 << 24);
+                count += (q0 != 0u) + (q1 != 0u);
+            } else if (f16) {
+                const __half h0 = __double2half(ll[0]), h1 = __double2half(ll[1]);
+                const uint32_t bins = ((uint32_t)(uint16_t)kk[0]) | ((uint32_t)(uint16_t)kk[1] << 16);
+                const uint32_t lens = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+                reinterpret_cast<uint2*>(table)[idx] = make_uint2(bins, lens);
+                count += (__half2float(h0) != 0.0f) + (__half2float(h1) != 0.0f);
+            } else {
+                const float f0 = (float)ll[0], f1 = (float)ll[1];
+                reinterpret_cast<uint4*>(table)[idx] =
+                    make_uint4((uint32_t)kk[0], (uint32_t)kk[1], __float_as_uint(f0), __float_as_uint(f1));
+                count += (f0 != 0.0f) + (f1 != 0.0f);
+            }
         }
     }
     // warp-level count of non-empty entries
-    unsigned c = (unsigned)cnt;
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(entries, (unsigned long long)c);
+    for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
+    if ((threadIdx.x & 31) == 0 && count) atomicAdd(entries, count);
 }
 
 // Per pixel, the sum of its stored lengths squared (sum l^2 of Eq. (7)'s
@@ -100,24 +112,37 @@ __global__ void pila_hsum_kernel(const unsigned char* table, int f16, int row_re
 
 // Smallest and largest cell an annealing move can touch: over the records of
 // the reconstruction-space pixels, bin k0 and the cell k0 + 1 that the second
-// entry of a record addresses.
+// entry of a record addresses.  Threads span angles, blocks step through the
+// list; one pair of atomics per block.
 __global__ void pila_band_kernel(const unsigned char* table, int f16, int row_records, int U, const int32_t* list,
-                                 long long n_list, int* lohi) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                 int n_list, int* lohi) {
     int lo = 0x7fffffff, hi = -1;
-    if (idx < n_list * U) {
-        const long long rec = (long long)list[idx / U] * row_records + idx % U;
-        const Entry2 e = decode_rec(table, rec, f16);
-        lo = e.k0;
-        hi = e.k0 + 1;
-    }
+    for (int u = threadIdx.x; u < U; u += blockDim.x)
+        for (int q = blockIdx.x; q < n_list; q += gridDim.x) {
+            const Entry2 e = decode_rec(table, (long long)list[q] * row_records + u, f16);
+            lo = min(lo, e.k0);
+            hi = max(hi, e.k0 + 1);
+        }
     for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    if ((threadIdx.x & 31) == 0 && hi >= 0) {
-        atomicMin(&lohi[0], lo);
-        atomicMax(&lohi[1], hi);
+    __shared__ int red[2][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = lo;
+        red[1][warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = min(lo, red[0][w]);
+            hi = max(hi, red[1][w]);
+        }
+        if (hi >= 0) {
+            atomicMin(&lohi[0], lo);
+            atomicMax(&lohi[1], hi);
+        }
     }
 }
 
@@ -221,11 +246,10 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_entries + 1, band_init, sizeof(band_init), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        const long long total = P * p->row_records;
-        const int threads = 256;
-        const long long blocks = (total + threads - 1) / threads;
-        pila_build_kernel<<<(unsigned)blocks, threads, 0, s>>>(p->d_table, precision, p->row_records,
-                                                                p->n, p->U, p->B, p->d_cos, p->d_sin, d_entries);
+        const int threads = 128;
+        const dim3 grid((unsigned)((p->row_records + threads - 1) / threads), (unsigned)std::min<long long>(P, 8192));
+        pila_build_kernel<<<grid, threads, 0, s>>>(p->d_table, precision, p->row_records, p->n, p->U, p->B,
+                                                   p->d_cos, p->d_sin, d_entries);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -234,9 +258,9 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !list.empty()) {
-        const long long total = (long long)list.size() * p->U;
-        pila_band_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-            p->d_table, precision, p->row_records, p->U, p->d_list, (long long)list.size(),
+        const int threads = p->U >= 256 ? 256 : (p->U + 31) / 32 * 32;
+        pila_band_kernel<<<(unsigned)std::min<size_t>(list.size(), 4096), threads, 0, s>>>(
+            p->d_table, precision, p->row_records, p->U, p->d_list, (int)list.size(),
             reinterpret_cast<int*>(d_entries + 1));
         e = cudaGetLastError();
     }
