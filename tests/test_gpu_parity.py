@@ -457,6 +457,50 @@ def test_batched_workload_full_size_sampled_chains(api):
         assert np.all(final[c][mask == 0] == 0.0) and final[c].min() >= 0.0 and final[c].max() <= cfg["beta"]
 
 
+def test_precision_workload_full_size_sampled_chain(api):
+    """The 512^2 workload at full size, in the launch the benchmark times: 304
+    chains (2 distinct phantoms, Poisson noise at 1e5 photons), 360 angles,
+    725 bins, K = 8, T0 by Eq. (8), 200 stages of 2,058 moves, the FP16 table
+    and the autotuned layout.  A sampled chain is followed move by move (all
+    411,600 moves) by the oracle over the same binary16 lengths: decisions,
+    Eq. (7) sums and the new pixel values, and T0."""
+    cfg = synth.WORKLOADS["precision512"]
+    n, U, B, K, S = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"]
+    C, distinct = 304, 2
+    mask = synth.disk_mask(n)
+    M = int(mask.sum()) // 100
+    sinos = []
+    for i in range(distinct):
+        clean = oracle.drt(synth.phantom(n, cfg["ellipses"], synth.slice_seeds(i)[0]) * mask, U, B)
+        sinos.append(synth.poisson_noise(clean, cfg["noise"][1], synth.slice_seeds(i)[1]).astype(np.float32))
+    sinos = np.stack(sinos)
+    img0 = synth.initial_image(n, 0.5, mask).astype(np.float32)
+    seed0 = synth.slice_seeds(0)[2]
+    traced = int(np.random.default_rng(12).integers(C))
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    imgs = dev(np.broadcast_to(img0, (C, n, n)))
+    trace = torch.zeros(S * M * api.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    st = api.sat_run(p, dev(sinos[np.arange(C) % distinct]), imgs, bome_k=K, n_sweeps=S, moves_per_sweep=M,
+                     t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, flags=api.SAT_FLAG_AUTOTUNE,
+                     trace_chain=traced, trace=trace)
+    api.pila_free(p)
+    assert all(s["status"] == 0 and s["proposed"] == S * M for s in st)
+    tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
+    pm = sinos[traced % distinct]
+    t0, found = oracle.sat_t0(pm, img0, seed=seed0 + traced, mask=mask, length_format=oracle.LEN_BINARY16)
+    assert found == st[traced]["t0_found"] == 200
+    assert abs(st[traced]["t0"] - t0) <= 1e-4 * t0
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st[traced]["t0"], tn=st[traced]["tn"], bome_k=K, n_sweeps=S,
+                                 moves_per_sweep=M, seed=seed0 + traced, mask=mask,
+                                 length_format=oracle.LEN_BINARY16)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5 and rep["max_err_f"] <= 1e-5, rep
+    assert rep["near_ties"] <= 1e-3 * S * M, rep
+    final = imgs[traced].cpu().numpy()
+    assert np.all(final[mask == 0] == 0.0) and final.min() >= 0.0 and final.max() <= cfg["beta"]
+
+
 def test_resync_drift_bound_512(api):
     """One stage of the 512^2 precision workload shape (360 angles, 725
     bins, Poisson noise) with the residual in global memory: the
