@@ -112,7 +112,12 @@ int pila_export(const satpila_pila* p, int32_t* bins, float* lens, void* stream)
  * Forward projection through the PILA, i.e. the DRT of Eq. (1) with the
  * stored lengths: sino[i][u][k] = sum over pixels p of images[i][p] * l.
  * Accumulated exactly in 64-bit fixed point (order-independent, hence
- * deterministic) and returned as float64 [n_images][U][B].
+ * deterministic) and returned as float64 [n_images][U][B].  images and sino
+ * are host or device memory (host buffers make the call synchronous).  For
+ * few images the call takes a stream-ordered device workspace (n_images *
+ * chunks * U * B * 8 bytes, chunks <= 64) to split their pixels over more
+ * CTAs, released on `stream` when the work is done.
+ * Errors: INVALID_ARG (null pointers, B above the projector's limit), CUDA.
  */
 int pila_forward(const satpila_pila* p, int32_t n_images, const float* images, double* sino, void* stream);
 /*
@@ -385,7 +390,9 @@ typedef struct {
 /*
  * n_slices independent SIRT reconstructions sharing the PILA.  costs (host or
  * device, [n_slices][n_iter], may be NULL) receives Eq. (4) after each pass.
- * Synchronizes `stream` at its end.
+ * Allocates its device scratch (corrections, partial sums, and for few slices
+ * the projector's pixel-chunk slices) for the call.  Synchronizes `stream` at
+ * its end.
  */
 int sirt_run(const satpila_pila* p, int32_t n_slices, const float* sino_meas, float* images,
              const sirt_params* prm, double* costs, void* stream);
@@ -406,7 +413,9 @@ int sirt_run(const satpila_pila* p, int32_t n_slices, const float* sino_meas, fl
  *  - the call is asynchronous on `stream` and does not synchronize it;
  *  - a problem whose scratch (n_slices * U * B floats, partial sums, and the
  *    factor matrix when the PILA has not cached one) exceeds the array is
- *    rejected with SATPILA_ERR_INVALID_ARG;
+ *    rejected with SATPILA_ERR_INVALID_ARG; the projector's pixel-chunk
+ *    slices are used only when they fit beside it (results are the same
+ *    either way);
  *  - the first call on a device looks up the array's device address once,
  *    so make that first call before any stream capture begins;
  *  - all calls share the array: calls whose work overlaps on the GPU (other

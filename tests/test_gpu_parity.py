@@ -403,6 +403,29 @@ def test_sirt_vs_oracle(api, mode):
     api.pila_free(p)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sirt_full_size_256(api, mode):
+    """SIRT on the 256^2 SAT+SIRT configuration (180 angles, 363 bins, disk
+    space, Gaussian noise at 1%): one slice, so the simultaneous mode's
+    projections run split into pixel chunks; four iterations against the
+    oracle, images within 2e-5 and per-iteration costs within 1e-4."""
+    cfg = synth.WORKLOADS["sat256"]
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, cfg["ellipses"], synth.slice_seeds(0)[0]) * mask
+    pm = synth.gaussian_noise(oracle.drt(ph, U, B), cfg["noise"][1], synth.slice_seeds(0)[1]).astype(np.float32)
+    img0 = synth.initial_image(n, 0.5, mask)
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    img = dev(img0).reshape(1, n, n)
+    it = 4
+    costs = torch.zeros((1, it), dtype=torch.float64, device="cuda")
+    api.sirt_run(p, dev(pm).reshape(1, U, B), img, n_iter=it, mode=mode, costs=costs)
+    oimg, oc = oracle.sirt_run(pm, img0, it, mode=mode, mask=mask)
+    assert np.max(np.abs(img.cpu().numpy()[0] - oimg)) <= 2e-5 * max(1.0, np.max(np.abs(oimg)))
+    assert np.allclose(costs.cpu().numpy()[0], oc, rtol=1e-4)
+    api.pila_free(p)
+
+
 def test_batched_workload_full_size_sampled_chains(api):
     """The batched workload at full size, in the launch the benchmark times:
     512 chains of 128^2 slices (disk space, 120 angles, 181 bins), K = 4,
