@@ -67,3 +67,30 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.SatParams) == 88
     assert C.sizeof(_lib.PilaGeom) == 32
     assert C.sizeof(_lib.SatStats) == 88
+
+
+def header_constants():
+    """Every integer #define of include/satpila.h, evaluated."""
+    text = open(os.path.join(ROOT, "include", "satpila.h")).read()
+    out = {}
+    for m in re.finditer(r"^#define\s+(\w+)\s+(.+?)\s*(?:/\*.*)?$", text, flags=re.M):
+        expr = re.sub(r"(\d+)u\b", r"\1", m.group(2).strip())
+        if re.fullmatch(r"[\d\s()<>+\-*]+", expr):
+            out[m.group(1)] = eval(expr)
+    return out
+
+
+def test_binding_constants_match_header():
+    """The Python binding's constants are the header's values (a stale copy
+    would pass wrong flags or misread plans and status codes)."""
+    from paper_1411_4622_gb300 import _lib
+
+    h = header_constants()
+    assert len(h) >= 30
+    for name, value in h.items():
+        if name == "SATPILA_NOALLOC_SCRATCH_BYTES":
+            assert _lib.NOALLOC_SCRATCH_BYTES == value
+            continue
+        py = name[len("SATPILA_"):] if name.startswith("SATPILA_") else name
+        assert hasattr(_lib, py), name
+        assert getattr(_lib, py) == value, name
