@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kProjThreads) proj_scale_kernel(ProjArgs a) {
 // 32 >> l pixels of the chunk at a time, one per lane slot (a slot's lanes
 // are the group's angles); the slots walk far-apart parts of the chunk,
 // starting at different columns, so that lanes of one angle rarely add to the
-// same bin.  Two steps are loaded before either is added, to overlap their
+// same bin.  Four steps are loaded before any is added, to overlap their
 // loads.  With one chunk the CTA finishes its rows itself; with several it
 // adds its sums to the image's rows in acc_global (exact integer adds, so the
 // order does not matter) and proj_finish_kernel finishes them.
@@ -246,29 +246,28 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
         if (off >= L) off %= L;
         return c0 + ps * L + off;
     };
-    for (int b = warp; b < L; b += 2 * nwarps) {
-        const int b2 = b + nwarps;
-        const int q1 = pixel_of(b), q2 = b2 < L ? pixel_of(b2) : c1;
-        const bool v1 = on && q1 < c1, v2 = on && q2 < c1;
-        float f1 = 0.0f, f2 = 0.0f;
-        Entry2 e1{0, 0, 0.0f, 0.0f}, e2{0, 0, 0.0f, 0.0f};
-        if (v1) {
-            f1 = factor ? (a.mask[q1] ? 1.0f : 0.0f) : img[q1];
-            e1 = decode_rec(a.table, (long long)q1 * a.row_records + col, a.f16);
+    constexpr int kSteps = 4;  // pixel steps loaded before their adds
+    for (int b = warp; b < L; b += kSteps * nwarps) {
+        float f[kSteps];
+        Entry2 e[kSteps];
+#pragma unroll
+        for (int t = 0; t < kSteps; ++t) {
+            const int bt = b + t * nwarps;
+            const int q = bt < L ? pixel_of(bt) : c1;
+            f[t] = 0.0f;
+            e[t] = Entry2{0, 0, 0.0f, 0.0f};
+            if (on && q < c1) {
+                f[t] = factor ? (a.mask[q] ? 1.0f : 0.0f) : img[q];
+                e[t] = decode_rec(a.table, (long long)q * a.row_records + col, a.f16);
+            }
         }
-        if (v2) {
-            f2 = factor ? (a.mask[q2] ? 1.0f : 0.0f) : img[q2];
-            e2 = decode_rec(a.table, (long long)q2 * a.row_records + col, a.f16);
-        }
-        if (f1 != 0.0f) {
-            const FixedSplit s1 = fixed_split(f1);
-            if (e1.l0 != 0.0f) add_entry(row, e1.k0, s1, e1.l0, F, factor);
-            if (e1.l1 != 0.0f) add_entry(row, e1.k1, s1, e1.l1, F, factor);
-        }
-        if (f2 != 0.0f) {
-            const FixedSplit s2 = fixed_split(f2);
-            if (e2.l0 != 0.0f) add_entry(row, e2.k0, s2, e2.l0, F, factor);
-            if (e2.l1 != 0.0f) add_entry(row, e2.k1, s2, e2.l1, F, factor);
+#pragma unroll
+        for (int t = 0; t < kSteps; ++t) {
+            if (f[t] != 0.0f) {
+                const FixedSplit st = fixed_split(f[t]);
+                if (e[t].l0 != 0.0f) add_entry(row, e[t].k0, st, e[t].l0, F, factor);
+                if (e[t].l1 != 0.0f) add_entry(row, e[t].k1, st, e[t].l1, F, factor);
+            }
         }
     }
     __syncthreads();
