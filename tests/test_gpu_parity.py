@@ -261,6 +261,29 @@ def test_sat_final_rmse_plain64_vs_oracle(api):
     api.pila_free(p)
 
 
+def test_sat256_free_running_rmse_vs_oracle(api):
+    """The 256^2 SAT configuration in full (180 angles, 363 bins, disk space,
+    Gaussian noise at 1%, K = 8, T0 by Eq. (8), 100 stages of the whole
+    reconstruction space, FP32 table), free running on both sides: final RMSE
+    against the phantom and final Eq. (4) cost within 2% of the oracle's."""
+    cfg = synth.WORKLOADS["sat256"]
+    n, U, B, K, S = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"]
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, cfg["ellipses"], synth.slice_seeds(0)[0]) * mask
+    pm = synth.gaussian_noise(oracle.drt(ph, U, B), cfg["noise"][1], synth.slice_seeds(0)[1]).astype(np.float32)
+    img0 = synth.initial_image(n, 0.5, mask)
+    seed = synth.slice_seeds(0)[2]
+    p = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    img = dev(img0).reshape(1, n, n)
+    st = api.sat_run(p, dev(pm).reshape(1, U, B), img, bome_k=K, n_sweeps=S, t0=-1.0, tn=-1.0, seed=seed)
+    api.pila_free(p)
+    assert st[0]["status"] == 0
+    oimg, ost, _ = oracle.sat_run(pm, img0, bome_k=K, n_sweeps=S, seed=seed, mask=mask)
+    r_gpu, r_orc = synth.rmse(img.cpu().numpy()[0], ph, mask), synth.rmse(oimg, ph, mask)
+    assert abs(r_gpu - r_orc) <= 0.02 * r_orc, (r_gpu, r_orc)
+    assert abs(st[0]["final_cost"] - ost["final_cost_fresh"]) <= 0.02 * ost["final_cost_fresh"]
+
+
 def test_sat_u8_table(api):
     """The one-byte table of Sec. II-B (lengths q / 180): its forward
     projection is the exact sum of its stored lengths, the windowed kernel
