@@ -68,6 +68,12 @@ def parse():
                     help="serve: arrival rate in requests/s (default: 80%% of the capacity measured on a burst)")
     ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
                     help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
+    ap.add_argument("--tables", default="f16,f32", help="precision512: table precisions, comma separated")
+    ap.add_argument("--no-c4", action="store_true", help="default run: skip the 512^2 sub-object")
+    ap.add_argument("--no-serve", action="store_true", help="default run: skip the serving sub-object")
+    ap.add_argument("--serve-requests", type=int, default=200, help="default run: requests of the serving sub-object")
+    ap.add_argument("--serve-rate", type=float, default=7.0,
+                    help="default run: arrival rate of the serving sub-object (requests/s)")
     return ap.parse_args()
 
 
@@ -174,9 +180,10 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel, workload=WORKLOAD):
-    """DRAM bytes per move of `kernel` from the committed ncu summary, or None
-    when the summary is missing or was taken on different sources."""
+def stored_profile(kernel, workload=WORKLOAD, key="dram_bytes_per_move"):
+    """A per-move figure of `kernel` (DRAM bytes, warp instructions) from the
+    committed ncu summary, or None when the summary is missing, lacks it, or
+    was taken on different sources."""
     path = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
     try:
         kv = {}
@@ -186,9 +193,13 @@ def stored_traffic(kernel, workload=WORKLOAD):
                 kv[k.strip()] = v.strip().strip("`")
         if kv.get("source_sha") != kernel_source_hash(kernel):
             return None
-        return float(kv["dram_bytes_per_move"])
+        return float(kv[key])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def stored_traffic(kernel, workload=WORKLOAD):
+    return stored_profile(kernel, workload, "dram_bytes_per_move")
 
 
 def peaks():
@@ -198,6 +209,51 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def measure_peaks(api):
+    """Read rates of each memory level on this GPU, from the library's probes
+    (satpila_probe_read / satpila_probe_smem): the denominators of the
+    gathers' rooflines.  The PILA row is read as consecutive 16-byte chunks
+    (stream), the residual cells as one 32-byte sector per record at
+    scattered places (sector) or as scattered 4-byte shared-memory words.
+    L2: a 64 MB buffer (inside the 126 MB L2); HBM: a 4 GB buffer (32x L2),
+    sectors gathered by each warp inside its own 1 MiB region (as a chain's
+    warps gather inside its residual) and, for comparison, over the whole
+    buffer (then bound by address translation).  The HBM copy figure is
+    MEASURED_PEAKS.json's."""
+    import torch
+
+    copy, kind = peaks()
+    out = {"hbm_copy_gbs": copy, "hbm_copy_kind": kind}
+    buf = torch.ones(64 << 20, dtype=torch.uint8, device="cuda")
+    out["l2_stream_gbs"] = api.probe_read(buf, api.PROBE_STREAM, loads=1 << 30)
+    out["l2_sector_gbs"] = api.probe_read(buf, api.PROBE_SECTOR, loads=1 << 28)
+    del buf
+    buf = torch.ones(4 << 30, dtype=torch.uint8, device="cuda")
+    out["hbm_stream_gbs"] = api.probe_read(buf, api.PROBE_STREAM, loads=1 << 29)
+    # sectors gathered inside 1 MiB regions, one per warp: the residual of a
+    # 512^2 chain (360 rows of 728 cells) is 1.05 MB and its warps gather in it
+    out["hbm_sector_gbs"] = api.probe_read(buf, api.PROBE_SECTOR, loads=1 << 28, region_bytes=1 << 20)
+    out["hbm_sector_scatter_gbs"] = api.probe_read(buf, api.PROBE_SECTOR, loads=1 << 26)
+    del buf
+    torch.cuda.empty_cache()
+    out["smem_gbs"] = api.probe_smem(0, loads=1 << 33)
+    out["smem_random_gbs"] = api.probe_smem(1, loads=1 << 32)
+    out["how"] = ("satpila_probe_read/_smem: one untimed and one timed launch of 8 CTAs x 256 threads per SM, "
+                  "8 independent loads in flight per thread, L1 bypassed; CUDA events")
+    return out
+
+
+def issue_peak(clk):
+    """Warp instructions per second the SMs can issue: 4 schedulers per SM,
+    one instruction each per cycle, at the sampled SM clock (else the maximum,
+    2070 MHz)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    return sms * 4 * mhz * 1e6, sms, mhz
 
 
 _ORACLE_SLICES = {}
@@ -340,100 +396,117 @@ def timed_steps(args, step, stream, dist, local):
     return step_ms, stats, clocks.stop()
 
 
-def run_precision(args):
-    """The 512^2 configuration as a gather-throughput workload: C chains of
-    512x512 slices (8 distinct phantoms with 40 ellipses, Poisson noise at
-    1e5 photons, each chain its own seed), 360 angles, 725 bins, FP16 PILA,
-    K = 8, the whole 200-stage linear schedule from Eq. (8) with 1/100 of a
-    sweep per stage (the moves of every temperature, 2,058 per stage);
-    residual in global memory.  One step: PILA build, resync, Eq. (8), the
-    200 stages, final resync."""
+def precision_phantoms(cfg, distinct):
+    """Seeded 512^2 phantoms (40 ellipses, disk reconstruction space) and
+    their measured sinograms: the discrete model's projection through an FP32
+    table (FP64-grade sums), then Poisson noise at 1e5 photons per bin."""
     import torch
 
     from paper_1411_4622_gb300 import api
-    from paper_1411_4622_gb300 import build as libbuild
 
-    libbuild.build()
-    torch.cuda.set_device(0)
-    cfg = dict(synth.WORKLOADS["precision512"])
-    n, U, B, K, S = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"]
-    C = args.slices or 304
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
     mask = synth.disk_mask(n)
-    M = int(mask.sum()) // 100
-    distinct = min(8, C)
     ph = np.stack([synth.phantom(n, cfg["ellipses"], synth.slice_seeds(i)[0]) * mask for i in range(distinct)])
     pf = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
     clean = api.pila_forward(pf, torch.tensor(ph, dtype=torch.float32, device="cuda")).cpu().numpy()
     api.pila_free(pf)
     noisy = np.stack([synth.poisson_noise(clean[i], cfg["noise"][1], synth.slice_seeds(i)[1])
                       for i in range(distinct)]).astype(np.float32)
-    idx = np.arange(C) % distinct
+    return ph, noisy, mask
+
+
+def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2, warmup=1, flags=2,
+                     residency=0, group_warps=0):
+    """The 512^2 configuration as configured, on a bounded sample of its
+    schedule: C chains of 512x512 slices (8 distinct phantoms, each chain its
+    own seed), 360 angles, 725 bins, K = 8, M = every reconstruction-space
+    pixel per stage (205,887 moves), the FP64-grade resync after every stage
+    (a fresh forward projection replaces the incremental residual and the
+    drift is recorded), T0 by Eq. (8); `stages` stages of a linear schedule of
+    that length.  One step: table build, resync, Eq. (8), the stages with
+    their resyncs, final cost.  Per table precision: moves/s over the step
+    and in the sweep kernel, the sweep's bytes per move against the measured
+    HBM stream and sector-gather rates, the drift bound."""
+    import types
+
+    import torch
+
+    from paper_1411_4622_gb300 import api
+
+    cfg = dict(synth.WORKLOADS["precision512"])
+    n, U, B, K = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"]
+    distinct = min(8, chains)
+    ph, noisy, mask = precision_phantoms(cfg, distinct)
+    M = int(mask.sum())
+    idx = np.arange(chains) % distinct
     sino = torch.tensor(noisy[idx], device="cuda").contiguous()
-    init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * C), dtype=torch.float32, device="cuda")
+    pm_max = float(np.max(np.abs(noisy)))
+    init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * chains), dtype=torch.float32, device="cuda")
     images = init.clone()
     stream = torch.cuda.current_stream()
-    run_kw = dict(bome_k=K, n_sweeps=S, moves_per_sweep=M, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2],
-                  residency=args.residency, group_warps=args.group_warps, flags=args.flags)
-    info = {}
+    moves = chains * stages * M
+    out = {"workload": "precision512", "chains": chains, "distinct_slices": distinct, "n": n, "angles": U,
+           "bins": B, "bome_k": K, "moves_per_stage": M, "stages": stages, "resync_every": 1,
+           "sample": f"{stages} stages of full M (a linear schedule of {stages} stages from Eq. (8)'s T0; the "
+                     f"configured schedule has {cfg['n_sweeps']})",
+           "l2": "flushed between timed steps (256 MB write)", "steps": steps, "warmup": warmup, "tables": {}}
+    for t in tables:
+        prec = {"f16": api.PILA_F16, "f32": api.PILA_F32, "u8": api.PILA_U8}[t]
+        kw = dict(bome_k=K, n_sweeps=stages, moves_per_sweep=M, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2],
+                  resync_every=1, residency=residency, group_warps=group_warps, flags=flags)
+        info = {}
 
-    def step():
-        images.copy_(init)
-        p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
-        st = api.sat_run(p, sino, images, **run_kw)
-        if not info:
-            info.update(api.pila_info(p))
-        api.pila_free(p)
-        return st
+        def step():
+            images.copy_(init)
+            p = api.pila_build(n, U, B, prec, mask=mask)
+            st = api.sat_run(p, sino, images, **kw)
+            if not info:
+                info.update(api.pila_info(p))
+            api.pila_free(p)
+            return st
 
-    step_ms, stats, clk = timed_steps(args, step, stream, None, 0)
-    ms = statistics.mean(step_ms)
-    moves = C * S * M
-    st = stats[-1]
-    acc = sum(x["accepted"] for x in st) / max(1, sum(x["proposed"] for x in st))
-    sweep_ms = statistics.mean(x[0]["sweep_ms"] for x in stats)
-    peak, peak_kind = peaks()
-    E = info["entries"] / (n * n)
-    row_bytes = info["row_records"] * info["record_bytes"]
-    # one 32-byte sector per angle, two when a record's entries straddle a
-    # sector boundary (k0 = 7 mod 8: 1/8 of the records with two entries)
-    sectors = U * (1.0 + (E / U - 1.0) / 8.0)
-    sector_bytes = row_bytes + 32.0 * sectors * (1.0 + acc) + 8.0 * (1.0 + acc)
-    useful_bytes = row_bytes + 4.0 * E * (1.0 + acc) + 4.0 * (1.0 + acc)
-    rate = moves / (sweep_ms / 1e3)
-    achieved = sector_bytes * rate / 1e9
-    kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_sweep_kernel")
-    tpm = stored_traffic(kernel, "precision512")
-    out = {"metric": "SAT pixel-moves/s, 512x512 slices (gather throughput)", "value": moves / (ms / 1e3),
-           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "precision512", "chains": C, "distinct_slices": distinct, "n": n, "angles": U,
-                      "bins": B, "bome_k": K, "stages": S, "moves_per_stage": M, "pila": "f16",
-                      "l2": "flushed between timed steps (256 MB write)",
-                      "launch": launch_name(st[0]["plan"], args.flags)},
-           "acceptance": acc, "sweep_moves_per_s": rate,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": tpm * moves if tpm is not None else None,
-                        "traffic_frac": tpm * rate / 1e9 / peak if tpm is not None else None,
-                        "peak_kind": peak_kind, "kernel": kernel, "bytes_per_move": sector_bytes,
-                        "bytes_per_move_useful": useful_bytes, "frac_useful": useful_bytes * rate / 1e9 / peak,
-                        "accounting": "PILA row + one 32-byte sector per touched residual cell group, read and "
-                                      "(times acceptance) written", "sweep_ms": sweep_ms},
-           "clocks": clk, "gpu_launches": args.steps * (1 + 1 + 1 + 2 + 2 + 1 + 3 + 1)}
-    print(json.dumps(out))
+        step_ms, stats, clk = timed_steps(types.SimpleNamespace(warmup=warmup, steps=steps), step, stream, None, 0)
+        ms = statistics.mean(step_ms)
+        st = stats[-1]
+        acc = sum(x["accepted"] for x in st) / max(1, sum(x["proposed"] for x in st))
+        sweep_ms = statistics.mean(x[0]["sweep_ms"] for x in stats)
+        rate = moves / (sweep_ms / 1e3)
+        E = info["entries"] / (n * n)
+        row_bytes = info["row_records"] * info["record_bytes"]
+        # one 32-byte sector per angle, two when a record's entries straddle a
+        # sector boundary (k0 = 7 mod 8: 1/8 of the records with two entries)
+        sectors = U * (1.0 + (E / U - 1.0) / 8.0)
+        sector_resid = 32.0 * sectors * (1.0 + acc) + 8.0 * (1.0 + acc)
+        useful = row_bytes + 4.0 * E * (1.0 + acc) + 4.0 * (1.0 + acc)
+        # seconds of memory time per move at the probe rates: rows streamed,
+        # residual sectors gathered
+        t_row = row_bytes / (pk["hbm_stream_gbs"] * 1e9)
+        t_sec = sector_resid / (pk["hbm_sector_gbs"] * 1e9)
+        kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_sweep_kernel")
+        tpm = stored_traffic(kernel, "precision512")
+        achieved = (row_bytes + sector_resid) * rate / 1e9
+        peak_eff = (row_bytes + sector_resid) / (t_row + t_sec) / 1e9
+        out["tables"][t] = {
+            "moves_per_s": moves / (ms / 1e3), "sweep_moves_per_s": rate, "ms_per_step": ms, "sweep_ms": sweep_ms,
+            "other_ms": ms - sweep_ms, "acceptance": acc, "table_bytes": info["table_bytes"],
+            "launch": launch_name(st[0]["plan"], flags),
+            "drift_max_rel": max(x["max_resync_drift"] for x in st) / pm_max,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_eff, "unit": "GB/s",
+                         "frac": achieved / peak_eff, "kernel": kernel,
+                         "bytes_per_move": row_bytes + sector_resid, "row_bytes": row_bytes,
+                         "sector_bytes": sector_resid, "useful_bytes_per_move": useful,
+                         "peak_rule": "rows at the HBM stream rate, residual sectors at the HBM sector-gather rate",
+                         "frac_rows": row_bytes * rate / 1e9 / pk["hbm_stream_gbs"],
+                         "frac_sectors": sector_resid * rate / 1e9 / pk["hbm_sector_gbs"],
+                         "traffic": tpm * chains * stages * M if tpm is not None else None,
+                         "traffic_over_sector_bytes": tpm / (row_bytes + sector_resid) if tpm is not None else None},
+            "clocks": clk}
+    return out
 
 
-def run_serve(args):
-    """The serving workload: a Poisson stream of requests, sizes uniform over
-    {64, 128, 256, 512}^2, angles uniform in [N/2, N], 2 floor(N/sqrt 2) + 1
-    bins, Gaussian (1% of max) or Poisson (1e5) noise with probability 1/2,
-    K uniform over {1, 4, 8}, 50 stages each, FP16 PILA, disk reconstruction
-    space, under a 120 GB device budget.  The arrival rate is 80% of the
-    capacity measured on a closed burst of up to 400 requests of the mix.  Reported: moves/s
-    over the stream and per-request latency (submit to result) p50/p99."""
-    # one hardware work queue per stream for up to 32 streams (the default 8
-    # makes classes' launches wait behind unrelated long ones); read when the
-    # CUDA context is created, so set before the first CUDA call
-    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+def run_precision(args):
+    """--workload precision512: the 512^2 configuration as configured
+    (resync every stage, full M), FP16 and FP32 tables; one JSON line."""
     import torch
 
     from paper_1411_4622_gb300 import api
@@ -441,8 +514,37 @@ def run_serve(args):
 
     libbuild.build()
     torch.cuda.set_device(0)
-    rng = np.random.default_rng(7)
-    nreq = args.requests
+    pk = measure_peaks(api)
+    sub = precision_sample(pk, chains=args.slices or 304, stages=args.sweeps or 2, steps=args.steps,
+                           warmup=args.warmup, flags=args.flags, residency=args.residency,
+                           group_warps=args.group_warps, tables=tuple(args.tables.split(",")))
+    main = sub["tables"][sub_first(sub)]
+    out = {"metric": "SAT pixel-moves/s, 512x512 slices, resync every stage", "value": main["moves_per_s"],
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {k: v for k, v in sub.items() if k != "tables"}, "tables": sub["tables"],
+           "roofline": main["roofline"], "peaks": pk, "clocks": main["clocks"]}
+    print(json.dumps(out))
+
+
+def sub_first(sub):
+    return next(iter(sub["tables"]))
+
+
+def serve_stream(nreq, rate=None, burst=400, seed=7):
+    """The serving workload: a Poisson stream of nreq requests, sizes uniform
+    over {64, 128, 256, 512}^2, angles uniform in [N/2, N], 2 floor(N/sqrt 2)
+    + 1 bins, Gaussian (1% of max) or Poisson (1e5) noise with probability
+    1/2, K uniform over {1, 4, 8}, 50 stages each, FP16 PILA, disk
+    reconstruction space, under a 120 GB (1.2e11 bytes) device budget.  The
+    arrival rate is `rate` requests/s, else 80% of the capacity measured on a
+    closed burst of the first `burst` requests.  Returns moves/s over the
+    stream and per-request latency (submit to result) p50/p99."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+
+    rng = np.random.default_rng(seed)
     sizes = rng.choice([64, 128, 256, 512], size=nreq)
     angles = np.array([rng.integers(s // 2, s + 1) for s in sizes])
     noise = rng.integers(0, 2, size=nreq)
@@ -468,15 +570,18 @@ def run_serve(args):
         reqs.append(dict(sino=sn, n=s, precision=api.PILA_F16, mask=masks[s], bome_k=int(ks[i]), n_sweeps=50,
                          seed=20000 + i, t0=-1.0, tn=-1.0))
     moves_of = [50 * int(masks[r["n"]].sum()) for r in reqs]
-    with api.Server(stages_per_tick=5, mem_budget=120 << 30) as srv:
-        # capacity: a closed burst of the first requests
-        burst = min(400, nreq)
-        t = time.perf_counter()
-        tk = [srv.submit(**reqs[i]) for i in range(burst)]
-        for x in tk:
-            srv.wait(x)
-        cap = sum(moves_of[:burst]) / (time.perf_counter() - t)
-        rate = args.rate or 0.8 * cap / float(np.mean(moves_of))  # requests per second
+    budget = 120 * 10**9
+    cap = None
+    with api.Server(stages_per_tick=5, mem_budget=budget) as srv:
+        if rate is None:
+            # capacity: a closed burst of the first requests
+            nb = min(burst, nreq)
+            t = time.perf_counter()
+            tk = [srv.submit(**reqs[i]) for i in range(nb)]
+            for x in tk:
+                srv.wait(x)
+            cap = sum(moves_of[:nb]) / (time.perf_counter() - t)
+            rate = 0.8 * cap / float(np.mean(moves_of))  # requests per second
         gaps = rng.exponential(1.0 / rate, size=nreq)
         clocks = ClockSampler(0)
         clocks.start()
@@ -497,16 +602,31 @@ def run_serve(args):
         wall = time.perf_counter() - t0
         clk = clocks.stop()
         info = srv.info()
-    out = {"metric": "SAT pixel-moves/s, served request stream; request p50/p99 ms", "value": done_moves / wall,
-           "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True,
+    return {"moves_per_s": done_moves / wall, "wall_ms": wall * 1e3, "requests": nreq,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "rate_per_s": rate, "capacity_moves_per_s": cap, "failed": failed,
+            "config": {"sizes": [64, 128, 256, 512], "stages": 50, "k": [1, 4, 8], "pila": "f16",
+                       "budget_bytes": budget, "arrival": "poisson", "geometries": len(sinos)},
+            "server": {k: info[k] for k in ("ticks", "bytes_peak", "geometries", "classes")}, "clocks": clk}
+
+
+def run_serve(args):
+    """--workload serve: the whole request stream (default 2000 requests),
+    arrival rate given or 80% of the burst capacity; one JSON line."""
+    import torch
+
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    r = serve_stream(args.requests, args.rate)
+    out = {"metric": "SAT pixel-moves/s, served request stream; request p50/p99 ms", "value": r["moves_per_s"],
+           "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": r["wall_ms"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "serve", "requests": nreq, "sizes": [64, 128, 256, 512], "stages": 50,
-                      "k": [1, 4, 8], "pila": "f16", "budget_gb": 120, "arrival": "poisson",
-                      "rate_per_s": rate, "rate_rule": "given" if args.rate else "80% of burst capacity",
-                      "capacity_moves_per_s": cap},
-           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-           "failed": failed, "server": {k: info[k] for k in ("ticks", "bytes_peak", "geometries", "classes")},
-           "clocks": clk}
+           "config": dict(workload="serve", requests=args.requests, rate_per_s=r["rate_per_s"],
+                          rate_rule="given" if args.rate else "80% of burst capacity",
+                          capacity_moves_per_s=r["capacity_moves_per_s"], **r["config"]),
+           "latency_ms": r["latency_ms"], "failed": r["failed"], "server": r["server"], "clocks": r["clocks"]}
     print(json.dumps(out))
 
 
@@ -823,6 +943,10 @@ def run_fbp(args):
 
 def main():
     args = parse()
+    # one hardware work queue per stream for up to 32 streams (the serving
+    # engine runs each class on its own stream); read when the CUDA context is
+    # created, so set before the first CUDA call
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.workload == "precision512":
         return run_precision(args)
     if args.workload == "serve":
@@ -855,6 +979,7 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pk = measure_peaks(api)
     n, U, B, K, S = cfg["n"], cfg["n_angles"], cfg["n_bins"], cfg["bome_k"], cfg["n_sweeps"]
     first, slices = shard.slice_range(rank, cfg["slices"])
     phantoms, mask = make_slices(cfg, first, slices)
@@ -932,17 +1057,52 @@ def main():
            "h2d_bytes_per_step": int(sino_h.numel() * 4 + img_h.numel() * 4),
            "d2h_bytes_per_step": int(img_h.numel() * 4)}
 
-    # Roofline of the sweep kernel (algorithmic bytes per move).
-    peak, peak_kind = peaks()
+    # Roofline of the sweep kernel: each class of its algorithmic bytes per
+    # move against the measured rate of the level it is read from.  The PILA
+    # row (consecutive 16-byte chunks) comes from L2 when the table fits there
+    # (from HBM otherwise); the residual cells come from shared memory (the
+    # windowed band) as scattered 4-byte words, or else as 32-byte sectors
+    # from L2; the image words from L2.  The bound is the level with the
+    # largest fraction; the issue rate is reported beside it (the move is a
+    # sequential chain: one warp per scheduler).
     E = info["entries"] / P
-    bytes_per_move = info["row_records"] * info["record_bytes"] + 4 * E * (1 + acc) + 4 * (1 + acc)
-    achieved = bytes_per_move * moves_per_step / (statistics.mean(sweep_ms) / 1e3) / 1e9
+    sweep_s = statistics.mean(sweep_ms) / 1e3
+    rate = moves_per_step / sweep_s
+    row_bytes = info["row_records"] * info["record_bytes"]
+    resid_bytes = 4 * E * (1 + acc)
+    img_bytes = 4 * (1 + acc)
     kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_window_kernel")
+    smem_resid = st[0]["plan"] in (1, 3)
+    table_in_l2 = info["table_bytes"] < 64e6
+    levels = {
+        "table_rows": {"level": "l2" if table_in_l2 else "hbm", "bytes_per_move": row_bytes,
+                       "achieved": row_bytes * rate / 1e9,
+                       "peak": pk["l2_stream_gbs"] if table_in_l2 else pk["hbm_stream_gbs"], "pattern": "stream"},
+        "residual": ({"level": "smem", "bytes_per_move": resid_bytes, "achieved": resid_bytes * rate / 1e9,
+                      "peak": pk["smem_random_gbs"], "pattern": "scattered 4-byte words"} if smem_resid else
+                     {"level": "l2", "bytes_per_move": 32 * E * (1 + acc),
+                      "achieved": 32 * E * (1 + acc) * rate / 1e9, "peak": pk["l2_sector_gbs"],
+                      "pattern": "32-byte sectors"}),
+        "image": {"level": "l2", "bytes_per_move": 32 * (1 + acc), "achieved": 32 * (1 + acc) * rate / 1e9,
+                  "peak": pk["l2_sector_gbs"], "pattern": "32-byte sectors"},
+    }
+    for v in levels.values():
+        v["frac"] = v["achieved"] / v["peak"]
+    top = max(levels, key=lambda k: levels[k]["frac"])
     tpm = stored_traffic(kernel)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": (tpm * moves_per_step) if tpm is not None else None, "peak_kind": peak_kind,
-            "kernel": kernel, "bytes_per_move": bytes_per_move, "sweep_ms": statistics.mean(sweep_ms),
-            "launches_per_step": 1}
+    ipm = stored_profile(kernel, WORKLOAD, "inst_per_move")
+    ipk, sms, mhz = issue_peak(clk)
+    roof = {"bound": levels[top]["level"], "achieved": levels[top]["achieved"], "peak": levels[top]["peak"],
+            "unit": "GB/s", "frac": levels[top]["frac"], "bytes": top,
+            "traffic": (tpm * moves_per_step) if tpm is not None else None,
+            "peak_kind": "measured (satpila_probe_*, this run)", "kernel": kernel,
+            "bytes_per_move": row_bytes + resid_bytes + img_bytes, "sweep_ms": sweep_s * 1e3,
+            "launches_per_step": 1, "levels": levels,
+            "issue": {"inst_per_move": ipm, "achieved": ipm * rate if ipm else None, "peak": ipk,
+                      "unit": "warp instructions/s", "frac": ipm * rate / ipk if ipm else None,
+                      "peak_rule": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz, one instruction per cycle each",
+                      "note": "one warp per chain and 3-4 chains per SM: at most one warp per scheduler, so "
+                              "dependent instructions are not hidden (latency-bound)"}}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -956,13 +1116,19 @@ def main():
            "latency_ms": {"slice_p50": float(np.percentile(step_ms, 50)),
                           "slice_p99": float(np.percentile(step_ms, 99)),
                           "note": "every slice of a step completes with the step's one launch"},
-           "e2e": e2e, "roofline": roof, "clocks": clk,
+           "e2e": e2e, "roofline": roof, "peaks": pk, "clocks": clk,
            # per step: PILA records, per-pixel sums, residual band, 2 resync
            # projections, 2 reductions, Eq. (8), the sweep between two timer
            # stamps, one copy (the sat_run part as one CUDA graph)
            "gpu_launches": args.steps * (1 + 1 + 1 + 2 + 2 + 1 + 3 + 1)}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(cfg)
+    # the other two configurations measured beside the headline (rank 0 only)
+    if world == 1 and not args.no_c4:
+        out["precision512"] = precision_sample(pk)
+    if world == 1 and not args.no_serve:
+        r = serve_stream(args.serve_requests, args.serve_rate)
+        out["serve"] = dict(r, metric="SAT pixel-moves/s over a served request stream; request p50/p99 ms")
     api.pila_free(pf)
     if rank == 0:
         print(json.dumps(out))

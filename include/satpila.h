@@ -253,7 +253,7 @@ typedef struct {
                                 with the FP64-grade resync, so a request behaves as sat_run with
                                 resync_every = stages_per_tick; 0: 5 */
     int32_t queue_limit;     /* waiting requests beyond which submit returns SATPILA_ERR_BUSY; 0: 65536 */
-    uint64_t mem_budget;     /* device bytes for tables and chain state; 0: 120 GiB; capped at the
+    uint64_t mem_budget;     /* device bytes for tables and chain state; 0: 120 GB (1.2e11 bytes); capped at the
                                 device's free memory less 2 GiB */
 } sat_server_cfg;
 
@@ -403,9 +403,10 @@ int sirt_run(const satpila_pila* p, int32_t n_slices, const float* sino_meas, fl
 /*
  * sirt_run without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
- * during the call, for instance code running while a stream is captured into
- * a CUDA graph, processes confined to a memory budget fixed at start-up, or
- * hosts whose own allocator owns the device.  Instead of allocating scratch,
+ * during the call, for instance processes confined to a memory budget fixed
+ * at start-up, hosts whose own allocator has reserved the device's memory,
+ * or real-time loops that cannot afford the device-wide synchronisation a
+ * cudaMalloc/cudaFree pair may cause.  Instead of allocating scratch,
  * it works in one statically sized array of this library
  * (SATPILA_NOALLOC_SCRATCH_BYTES; every GPU that loads the library keeps it
  * until the process exits).  Same arguments and results as sirt_run, except:
@@ -423,6 +424,38 @@ int sirt_run(const satpila_pila* p, int32_t n_slices, const float* sino_meas, fl
  */
 int sirt_run_noalloc(const satpila_pila* p, int32_t n_slices, const float* sino_meas, float* images,
                      const sirt_params* prm, double* costs, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Memory-level probes.  No counterpart in the paper: they measure, on the    */
+/* running GPU, the read rates that bound the move's gathers (its roofline):  */
+/* the PILA row is read as consecutive 16-byte chunks, the residual cells as  */
+/* one 32-byte sector per record at scattered places.                         */
+/* ------------------------------------------------------------------------ */
+
+#define SATPILA_PROBE_STREAM 0 /* consecutive 16-byte loads, whole lines per warp */
+#define SATPILA_PROBE_SECTOR 1 /* one 32-byte sector at a pseudo-random place per load */
+
+/*
+ * Read rate over buf (device memory, 16-byte aligned, bytes >= 4096): about
+ * `loads` loads of the given kind from every SM, bypassing L1, timed with
+ * CUDA events on `stream` after one untimed pass.  A buffer that fits in L2
+ * measures L2; one many times larger than L2 measures HBM.  For
+ * SATPILA_PROBE_SECTOR each warp gathers inside one region of region_bytes
+ * (warp w in region w mod (bytes / region_bytes); 0: the whole buffer, at
+ * most 2^32 sectors), as a chain's warps gather inside its own residual.
+ * *gbs = bytes / s / 1e9, counting 32 bytes per sector load (the unit the
+ * memory moves) and 16 per stream load.  buf is only read.  Synchronizes
+ * `stream`.  Errors: INVALID_ARG (host pointer, sizes, kind), CUDA.
+ */
+int satpila_probe_read(const void* buf, uint64_t bytes, int32_t kind, uint64_t region_bytes, uint64_t loads,
+                       double* gbs, void* stream);
+/*
+ * Shared-memory 4-byte load rate summed over all SMs (about `loads` loads):
+ * kind 0 conflict-free (lane i reads bank i), kind 1 pseudo-random words of a
+ * 32 KB array per CTA (the pattern of residual cells at scattered bins).
+ * *gbs = 4 * loads / s / 1e9.  Synchronizes `stream`.
+ */
+int satpila_probe_smem(int32_t kind, uint64_t loads, double* gbs, void* stream);
 
 #ifdef __cplusplus
 }

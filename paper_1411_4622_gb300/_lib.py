@@ -23,12 +23,13 @@ SAT_FLAG_WINDOW_GROUPS = 16
 (SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
  SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4) = range(9)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
+PROBE_STREAM, PROBE_SECTOR = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["satpila_last_error", "satpila_version", "pila_build", "pila_free", "pila_info", "pila_export",
            "pila_forward", "pila_sirt_factor", "sat_run", "sat_server_create", "sat_server_submit", "sat_server_poll",
            "sat_server_wait", "sat_server_info", "sat_server_destroy", "drt_bilinear", "sat_drt_run", "fbp", "fbp_prior", "sirt_run",
-           "sirt_run_noalloc"]
+           "sirt_run_noalloc", "satpila_probe_read", "satpila_probe_smem"]
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -127,6 +128,8 @@ def load():
         lib.fbp_prior.argtypes = [C.c_int32, C.c_int32, V, C.c_float, V, V, V, V]
         lib.sirt_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
         lib.sirt_run_noalloc.argtypes = [V, C.c_int32, V, V, C.POINTER(SirtParams), V, V]
+        lib.satpila_probe_read.argtypes = [V, C.c_uint64, C.c_int32, C.c_uint64, C.c_uint64, C.POINTER(C.c_double), V]
+        lib.satpila_probe_smem.argtypes = [C.c_int32, C.c_uint64, C.POINTER(C.c_double), V]
         for name in EXPORTS:
             if name not in ("satpila_last_error", "satpila_version"):
                 getattr(lib, name).restype = C.c_int

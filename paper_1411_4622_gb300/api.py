@@ -21,6 +21,7 @@ from ._lib import ERR_BUSY, ERR_INVALID_ARG, ERR_NOT_FOUND, ERR_PENDING  # noqa:
 from ._lib import (SAT_FLAG_WINDOW_GROUPS, SAT_PLAN_PIPE_1, SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4,  # noqa: F401
                    SAT_PLAN_RULES, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4, SAT_PLAN_WINDOW_GLOBAL,
                    SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_WINDOW_SMEM)
+from ._lib import PROBE_SECTOR, PROBE_STREAM  # noqa: F401
 
 TRACE_DTYPE = np.dtype([("pixel", "<i4"), ("cstar", "<i4"), ("accepted", "<i4"), ("pad", "<i4"),
                         ("dS", "<f4"), ("dC", "<f4"), ("fnew", "<f4"), ("pad2", "<f4")])
@@ -317,3 +318,24 @@ def sirt_run_noalloc(p: Pila, sino_meas, images, *, n_iter=1, mode=SIRT_SIMULTAN
     prm = L.SirtParams(int(n_iter), int(mode), float(relax), 0)
     L.check(L.load().sirt_run_noalloc(p.handle, n_sl, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
                                       C.byref(prm), _ptr(costs, np.float64), _stream(stream)))
+
+
+def probe_read(buf, kind, loads=1 << 28, region_bytes=0, stream=None) -> float:
+    """Read rate (GB/s) over a device tensor: kind PROBE_STREAM
+    (consecutive 16-byte loads) or PROBE_SECTOR (one 32-byte sector at a
+    pseudo-random place per load, each warp inside its own region of
+    region_bytes; 0: the whole buffer)."""
+    if not _is_tensor(buf):
+        raise TypeError("probe_read takes a device tensor")
+    g = C.c_double()
+    L.check(L.load().satpila_probe_read(_ptr(buf), int(buf.numel() * buf.element_size()), int(kind),
+                                        int(region_bytes), int(loads), C.byref(g), _stream(stream)))
+    return g.value
+
+
+def probe_smem(kind, loads=1 << 30, stream=None) -> float:
+    """Shared-memory 4-byte load rate (GB/s, all SMs): kind 0 conflict-free,
+    1 pseudo-random words."""
+    g = C.c_double()
+    L.check(L.load().satpila_probe_smem(int(kind), int(loads), C.byref(g), _stream(stream)))
+    return g.value

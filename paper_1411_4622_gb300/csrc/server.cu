@@ -907,7 +907,7 @@ extern "C" int sat_server_create(const sat_server_cfg* cfg, satpila_server** out
     if (e != cudaSuccess) return cuda_fail(e, "sat_server_create");
     const uint64_t headroom = 2ull << 30;
     const uint64_t avail = free_b > headroom ? free_b - headroom : free_b / 2;
-    if (c.mem_budget == 0) c.mem_budget = 120ull << 30;
+    if (c.mem_budget == 0) c.mem_budget = 120000000000ull;  // 120 GB (10^9 bytes each)
     c.mem_budget = std::min<uint64_t>(c.mem_budget, avail);
     auto* s = new satpila_server();
     s->cfg = c;

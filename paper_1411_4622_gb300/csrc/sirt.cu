@@ -210,11 +210,11 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
 
 // ---- SIRT without any allocation -------------------------------------------
 //
-// For callers that must not allocate device memory during the call: code
-// that runs while a stream is being captured into a CUDA graph (where an
-// allocation would be invalid), processes that run inside a fixed memory
-// budget handed to them at start-up, and hosts whose own allocator owns all
-// device memory.  The scratch that sirt_run allocates per call lives instead
+// For callers that must not allocate device memory during the call:
+// processes that run inside a fixed memory budget handed to them at
+// start-up, hosts whose own allocator has reserved all device memory, and
+// loops that cannot take the device-wide synchronisation an allocation or
+// release may cause.  The scratch that sirt_run allocates per call lives instead
 // in one statically sized device array of this library, which every GPU that
 // loads the library keeps for the life of the process.
 

@@ -56,6 +56,9 @@ def test_host_side_argument_checks(lib):
     sp = _lib.SirtParams(1, 5, 1.0, 0)
     assert lib.sirt_run(None, 1, None, None, C.byref(sp), None, None) == _lib.ERR_INVALID_ARG
     assert lib.pila_free(None) == 0
+    g = C.c_double()
+    assert lib.satpila_probe_read(None, 1 << 20, 0, 0, 1, C.byref(g), None) == _lib.ERR_INVALID_ARG
+    assert lib.satpila_probe_smem(5, 1, C.byref(g), None) == _lib.ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header():

@@ -199,6 +199,36 @@ def test_sat_lockstep_plain64(api, W):
     api.pila_free(p)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("layout", ["window", "pipelined2", "window_groups4"])
+def test_sat_schedules_lockstep(api, schedule, layout):
+    """The geometric (8b) and cubic (9) schedules of Sec. III-C on the plain
+    64^2 workload (90 angles, K = 4): every move of 20 stages compared with
+    the oracle, on the windowed, pipelined and grouped-window kernels."""
+    cfg, n, U, B, ph, pm = _plain64()
+    img0 = np.full((n, n), 0.5)
+    p = api.pila_build(n, U, B, api.PILA_F32)
+    S, M = cfg["n_sweeps"], n * n
+    t0, tn = 1e-2, 1e-5
+    kw = {"window": dict(residency=1), "pipelined2": dict(group_warps=2),
+          "window_groups4": dict(group_warps=4, flags=api.SAT_FLAG_WINDOW_GROUPS)}[layout]
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, bome_k=4, t0=t0, tn=tn, seed=3100 + schedule,
+                              schedule=schedule, resync_every=5, **kw)
+    assert st["status"] == 0 and st["proposed"] == S * M
+    assert st["plan"] == {"window": api.SAT_PLAN_WINDOW_SMEM, "pipelined2": api.SAT_PLAN_PIPE_2,
+                          "window_groups4": api.SAT_PLAN_WINDOW_G4}[layout]
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=4, n_sweeps=S, seed=3100 + schedule,
+                                 schedule=schedule)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5 and rep["max_err_dC"] <= 1e-5, rep
+    assert rep["near_ties"] <= 1e-3 * S * M, rep
+    # uphill moves were decided at the stage temperatures (the oracle takes
+    # them from its own closed forms, so a wrong temperature is a mismatch)
+    assert np.count_nonzero((tr["accepted"] == 1) & (tr["dC"] > 0)) > 0
+    api.pila_free(p)
+
+
 @pytest.mark.parametrize("K,res,W", [(8, 0, 0), (8, 2, 1), (32, 2, 4), (3, 0, 2)])
 def test_sat_lockstep_bome_with_mask(api, K, res, W):
     """256^2-geometry slice (180 angles, 363 bins) with the disk reconstruction

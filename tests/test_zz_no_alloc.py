@@ -1,6 +1,6 @@
 """sirt_run_noalloc: SIRT for callers that cannot allocate device memory
-during the call (stream capture, fixed memory budgets, hosts that own the
-allocator).  It works in the library's static device scratch; here it must
+during the call (fixed memory budgets, hosts whose allocator has reserved the
+device, loops that cannot take an allocation's synchronisation).  It works in the library's static device scratch; here it must
 give sirt_run's results on two calls in a row (the scratch keeps the previous
 call's contents), both when the table has no cached factor matrix (it is then
 built inside the scratch) and when it has one."""
