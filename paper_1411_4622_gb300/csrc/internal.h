@@ -27,6 +27,14 @@ struct satpila_pila {
     // Residual band: every cell an annealing move can touch (bins k and k + 1
     // of each record of a reconstruction-space pixel) has band_lo <= bin <= band_hi.
     int band_lo = 0, band_hi = 0;
+    // Ray-major index of the table, read by the ray-driven projector: the
+    // entries of ray (u, k) are d_ray_ent[d_ray_off[u*B + k] .. d_ray_off[u*B + k + 1]),
+    // each {pixel, the stored length decoded to float32 bits}, ascending pixel
+    // (rays longer than the sort's capacity keep their build order).  NULL
+    // when not built (the pixel-driven projector is used instead).
+    uint32_t* d_ray_off = nullptr;  // [U*B + 1]
+    uint2* d_ray_ent = nullptr;     // [entries]
+    int64_t ray_bytes = 0;
     // Tables built for the serving engine come from a stream-ordered memory
     // pool (no device-wide synchronisation on allocation or release).
     cudaMemPool_t pool = nullptr;
@@ -36,8 +44,10 @@ struct satpila_pila {
 namespace satpila {
 
 // pila_build with its allocations taken from `pool` in the order of stream s
-// (pool == NULL: ordinary allocations, as pila_build).
-int pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s, cudaMemPool_t pool, satpila_pila** out);
+// (pool == NULL: ordinary allocations, as pila_build); ray_index: also build
+// the ray-major index of the ray-driven projector.
+int pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s, cudaMemPool_t pool, satpila_pila** out,
+                  bool ray_index = true);
 
 // Thread-local last-error message.
 void set_error(const std::string& msg);
@@ -82,6 +92,11 @@ struct ProjArgs {
     float* part_drift;          // [item][U]
     void* ws;                   // optional, projector_ws_bytes(items, U, B, n) bytes: lets few
                                 // images split their pixels over more CTAs
+    const uint32_t* ray_off;    // ray-major index of the table (satpila_pila::d_ray_off), or NULL
+    const uint2* ray_ent;
+    void* ray_ws;               // ray_ws_bytes(items, U, B, n) bytes: with the index, selects the
+                                // ray-driven projector (else the pixel-driven one runs)
+    float* timg;                // carved from ray_ws: images transposed to [group][P][32]
     int chunks;                 // set with the plan
     long long* partial;         // carved from ws when chunks > 1: [item][chunk][U][B] sums
     float* max_parts;           // [item][32] partial max|f|
@@ -96,6 +111,14 @@ int projector_plan(int U, int B, int n, long long n_items, bool can_chunk, int* 
 // Workspace that lets launch_projector split the pixels of n_items n x n
 // images into chunks (0 when it would not).
 size_t projector_ws_bytes(long long n_items, int U, int B, int n);
+// Workspace of the ray-driven projector for n_items n x n images.
+size_t ray_ws_bytes(long long n_items, int U, int B, int n);
+// True when SATPILA_PROJECTOR=pixel asks for the pixel-driven projector.
+bool projector_forced_pixel();
+// Fills the ray-driven projector's fields of a from p (index) and ws.
+void use_ray_projector(ProjArgs& a, const satpila_pila* p, void* ws);
+// Builds p's ray-major index on stream s (allocations from pool when given).
+int build_ray_index(satpila_pila* p, cudaStream_t s, cudaMemPool_t pool);
 // Chooses the plan for n_items (filling a's group fields) and launches.
 cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s);
 // The largest B the projector takes (one angle per group in shared memory).

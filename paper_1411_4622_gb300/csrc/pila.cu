@@ -170,7 +170,7 @@ extern "C" int pila_build(const pila_geom* g, int32_t precision, void* stream, s
 }
 
 int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t stream, cudaMemPool_t pool,
-                           satpila_pila** out) {
+                           satpila_pila** out, bool ray_index) {
     if (!g || !out) return fail(SATPILA_ERR_INVALID_ARG, "pila_build: null argument");
     *out = nullptr;
     if (g->n < 1 || g->n_angles < 1 || g->n_bins < 1)
@@ -279,6 +279,13 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
     if (list.empty() || band[1] < band[0]) band[0] = 0, band[1] = 1;
     p->band_lo = std::max(0, band[0]);
     p->band_hi = std::min(p->B, band[1]);
+    if (ray_index) {
+        const int rc = build_ray_index(p, s, pool);
+        if (rc != SATPILA_OK) {
+            const std::string msg = satpila_last_error();
+            return cleanup(rc, msg);
+        }
+    }
     *out = p;
     return SATPILA_OK;
 }
@@ -286,7 +293,7 @@ int satpila::pila_build_in(const pila_geom* g, int32_t precision, cudaStream_t s
 extern "C" int pila_free(satpila_pila* p) {
     if (!p) return SATPILA_OK;
     sat_cache_purge(p);
-    void* bufs[] = {p->d_table, p->d_list, p->d_mask, p->d_cos, p->d_sin, p->d_hsum};
+    void* bufs[] = {p->d_table, p->d_list, p->d_mask, p->d_cos, p->d_sin, p->d_hsum, p->d_ray_off, p->d_ray_ent};
     for (void* b : bufs) {
         if (!b) continue;
         if (p->pool) cudaFreeAsync(b, p->alloc_stream);

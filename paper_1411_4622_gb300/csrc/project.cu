@@ -15,7 +15,8 @@
 // The fraction bits are chosen per image from max|f| so nothing overflows.
 #include <algorithm>
 #include <cmath>
-
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -90,7 +91,9 @@ __device__ __forceinline__ void add_entry(long long* row, int k, const FixedSpli
 }
 
 // Outputs of cell (u, k) of image item from its fixed-point sum; returns
-// (P_c - P_m)^2 (RESYNC, SIRT; else 0) and, for RESYNC, the drift.
+// P_c - P_m (RESYNC, SIRT; else 0), whose square the row sums add with one
+// rounding (an explicit fused multiply-add, the same in every path), and,
+// for RESYNC, the drift.
 __device__ __forceinline__ double cell_output(const ProjArgs& a, int item, int u, int k, long long raw, int F,
                                               float* drift) {
     const int B = a.B;
@@ -111,13 +114,13 @@ __device__ __forceinline__ double cell_output(const ProjArgs& a, int item, int u
             float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
             if (a.drift) *drift = fabsf(rf - *dst);
             *dst = rf;
-            return r * r;
+            return r;
         }
         default: {  // PROJ_SIRT
             const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
             const float w = a.w[cell];
             a.resid[(long long)item * a.resid_stride + cell] = w > 0.0f ? (float)(-r / (double)w) : 0.0f;
-            return r * r;
+            return r;
         }
     }
 }
@@ -144,7 +147,8 @@ __device__ __forceinline__ void finish_row(const ProjArgs& a, int item, int u, i
     float drift = 0.0f;
     for (int k = lane; k < a.B; k += 32) {
         float d = 0.0f;
-        sq += cell_output(a, item, u, k, src[k], F, &d);
+        const double r = cell_output(a, item, u, k, src[k], F, &d);
+        sq = __fma_rn(r, r, sq);
         drift = fmaxf(drift, d);
     }
     store_row_sums(a, item, u, sq, drift, lane);
@@ -282,8 +286,8 @@ __global__ void __launch_bounds__(kProjThreads) projector_kernel(ProjArgs a) {
 }
 
 // Chunked launches, step 1: one thread per cell sums the chunks' slices
-// (exact integer adds), writes the outputs, and leaves the cell's square and
-// drift in slice 0 and 1 of the cell (read by step 2 only).
+// (exact integer adds), writes the outputs, and leaves the cell's residual
+// and drift in slice 0 and 1 of the cell (read by step 2 only).
 __global__ void proj_finish_cells_kernel(ProjArgs a) {
     const int item = blockIdx.y;
     const long long cells = (long long)a.U * a.B;
@@ -300,8 +304,8 @@ __global__ void proj_finish_cells_kernel(ProjArgs a) {
     for (int c = 0; c < a.chunks; ++c) raw += src[c * cells];
     const int u = (int)(cell / a.B), k = (int)(cell - (long long)u * a.B);
     float drift = 0.0f;
-    const double sq = cell_output(a, item, u, k, raw, F_sh, &drift);
-    src[0] = __double_as_longlong(sq);
+    const double r = cell_output(a, item, u, k, raw, F_sh, &drift);
+    src[0] = __double_as_longlong(r);
     src[cells] = (long long)__float_as_int(drift);
 }
 
@@ -317,10 +321,158 @@ __global__ void __launch_bounds__(32 * kFinishWarps) proj_finish_rows_kernel(Pro
     double sq = 0.0;
     float drift = 0.0f;
     for (int k = lane; k < a.B; k += 32) {
-        sq += __longlong_as_double(src[k]);
+        const double r = __longlong_as_double(src[k]);
+        sq = __fma_rn(r, r, sq);
         drift = fmaxf(drift, __int_as_float((int)src[cells + k]));
     }
     store_row_sums(a, item, u, sq, drift, lane);
+}
+
+// ---- ray-driven projector ---------------------------------------------------
+//
+// With the table's ray-major index (rays.cu) a forward projection sums along
+// rays, so each sum stays in a register: no shared accumulators, no atomics.
+// The terms are the same exact fixed-point products as above (the fraction
+// bits F of an image come from the same bound), and integer addition is
+// associative, so every sum is bit-identical to the pixel-driven
+// projector's.  The sums go to a workspace [item][U][B] and finish_rows_kernel
+// forms the outputs and the per-angle sums of squares with finish_row, the
+// function (and so the order) of the unchunked pixel-driven launch.
+//
+// Many images: a block of 4 warps takes 4 consecutive angles of one group of
+// 32 images and 32 consecutive bins (the four warps' rays cross nearly the
+// same pixels, so their image loads share L1 lines); lane = image.  The
+// images are first transposed to [group][P][32], so that one pixel's values
+// for the 32 images are one 128-byte line.  Few images: one warp per
+// (image, ray), lanes over the ray's entries, a butterfly of the sums.
+
+constexpr int kImageLanesMin = 24;  // images from which the image-lanes form runs
+constexpr int kRowWarps = 4;        // angles per block of ray_rows_kernel
+constexpr int kRowBins = 32;        // bins per block of ray_rows_kernel
+constexpr int kRowUnroll = 8;       // index entries loaded before their terms
+
+// 64-bit right shift by s, 0 for s >= 64 (PTX clamps the shift amount).
+__device__ __forceinline__ unsigned long long shr_clamp(unsigned long long x, uint32_t s) {
+    unsigned long long r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+
+// fixed_mul(fixed_split(f), l, F) from the bits of f and l, with
+// ebias = F - 300: the term's exponent is (max(ef, 1) - 150) + (el - 150) + F
+// = max(ef, 1) + el + ebias.  Equal to fixed_mul: for
+// e >= 0 the product shifted left, else rounded half away from zero; e <= 14
+// always (every term is below 2^61 and a product of normal significands is
+// at least 2^46), so (m << 15) >> (14 - e) = floor(m 2^(e+1)) never loses a
+// high bit, and shifts of 64 or more give 0.
+__device__ __forceinline__ long long fixed_term_bits(uint32_t bf, uint32_t bl, int ebias) {
+    const uint32_t ef = (bf >> 23) & 0xffu;
+    const uint32_t mf = (bf & 0x7fffffu) | (ef ? 0x800000u : 0u);
+    const int e = (int)max(ef, 1u) + (int)((bl >> 23) & 0xffu) + ebias;
+    const unsigned long long m = (unsigned long long)mf * (unsigned long long)((bl & 0x7fffffu) | 0x800000u);
+    const unsigned long long t = shr_clamp(m << 15, (uint32_t)(14 - e));
+    const unsigned long long v = (t + 1ull) >> 1;
+    return (bf >> 31) ? -(long long)v : (long long)v;
+}
+
+__device__ __forceinline__ long long fixed_term(float f, float l, int F) {
+    return fixed_term_bits(__float_as_uint(f), __float_as_uint(l), F - 300);
+}
+
+// T[g][p][lane] = image (32 g + lane) at pixel p, 0 past the last image.
+__global__ void transpose_images_kernel(const ProjArgs a, int n_items, long long P) {
+    __shared__ float tile[32][33];
+    const int g = blockIdx.y;
+    const long long p0 = (long long)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += 8) {
+        const int item = g * 32 + r;
+        const long long p = p0 + tx;
+        tile[r][tx] = (item < n_items && p < P) ? a.img[(long long)item * a.img_stride + p] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const long long p = p0 + r;
+        if (p < P) a.timg[((long long)g * P + p) * 32 + tx] = tile[tx][r];
+    }
+}
+
+// Block (group g, bin chunk c, angle quad q), g slowest so that the blocks
+// running at once share one group's transposed images in L2; warp w takes
+// angle 4q + w, bins 32c .. 32c + 31, lane = image.
+__global__ void __launch_bounds__(32 * kRowWarps) ray_rows_kernel(const ProjArgs a, int n_items, int quads,
+                                                                  int chunks) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long blk = blockIdx.x;
+    const int g = (int)(blk / ((long long)chunks * quads));
+    const int rem = (int)(blk - (long long)g * chunks * quads);
+    const int c = rem / quads, u = (rem - c * quads) * kRowWarps + warp;
+    if (u >= a.U) return;
+    const int item = g * 32 + lane;
+    float m = 0.0f;
+    if (item < n_items)
+        for (int q = 0; q < kScaleParts; ++q) m = fmaxf(m, a.max_parts[(long long)item * kScaleParts + q]);
+    const int ebias = fraction_bits_of_max(a, m) - 300;  // the lane's image's F, as fixed_term folds it
+    const long long P = (long long)a.n * a.n;
+    const float* T = a.timg + (long long)g * P * 32 + lane;
+    const uint32_t* off = a.ray_off + (long long)u * a.B;
+    long long* out = a.partial + ((long long)item * a.U + u) * a.B;
+    const int k0 = c * kRowBins, k1 = min(a.B, k0 + kRowBins);
+    uint32_t e1 = off[k0];
+    for (int k = k0; k < k1; ++k) {
+        uint32_t e = e1;
+        e1 = off[k + 1];
+        long long acc = 0;
+        for (; e + kRowUnroll <= e1; e += kRowUnroll) {
+            uint2 en[kRowUnroll];
+            float f[kRowUnroll];
+#pragma unroll
+            for (int j = 0; j < kRowUnroll; ++j) en[j] = a.ray_ent[e + j];
+#pragma unroll
+            for (int j = 0; j < kRowUnroll; ++j) f[j] = T[(long long)en[j].x * 32];
+#pragma unroll
+            for (int j = 0; j < kRowUnroll; ++j) acc += fixed_term_bits(__float_as_uint(f[j]), en[j].y, ebias);
+        }
+        for (; e < e1; ++e) {
+            const uint2 en = a.ray_ent[e];
+            acc += fixed_term_bits(__float_as_uint(T[(long long)en.x * 32]), en.y, ebias);
+        }
+        if (item < n_items) out[k] = acc;
+    }
+}
+
+// One warp per (image, ray), image-major; lanes over the ray's entries.
+__global__ void __launch_bounds__(256) ray_cells_kernel(const ProjArgs a, int n_items) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long rays = (long long)a.U * a.B;
+    if (w >= rays * n_items) return;
+    const int item = (int)(w / rays);
+    const long long ray = w - (long long)item * rays;
+    const int F = item_fraction_bits_parts(a, item, lane);
+    const bool factor = a.mode == PROJ_FACTOR;
+    const float* img = factor ? nullptr : a.img + (long long)item * a.img_stride;
+    long long acc = 0;
+    const uint32_t e1 = a.ray_off[ray + 1];
+    for (uint32_t e = a.ray_off[ray] + lane; e < e1; e += 32) {
+        const uint2 en = a.ray_ent[e];
+        const float l = __uint_as_float(en.y);
+        const float f = factor ? (a.mask[en.x] ? l : 0.0f) : img[en.x];
+        acc += fixed_term(f, l, F);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.partial[(long long)item * rays + ray] = acc;
+}
+
+// One warp per (image, angle row): outputs and row sums from the sums.
+constexpr int kRowsPerBlock = 4;
+__global__ void __launch_bounds__(32 * kRowsPerBlock) finish_rows_kernel(const ProjArgs a, int n_items) {
+    const int item = blockIdx.y, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * kRowsPerBlock + (threadIdx.x >> 5);
+    if (u >= a.U || item >= n_items) return;
+    const int F = item_fraction_bits_parts(a, item, lane);
+    finish_row(a, item, u, F, a.partial + ((long long)item * a.U + u) * a.B, lane);
 }
 
 // One warp per item: lane partials over u = lane, lane + 32, ... in order,
@@ -407,8 +559,63 @@ cudaError_t prepare_projector() {
     return e;
 }
 
+// [item][U][B] sums, the transposed images (many images), the max|f| parts.
+size_t ray_ws_bytes(long long n_items, int U, int B, int n) {
+    const long long P = (long long)n * n, cells = (long long)U * B;
+    const size_t timg = n_items >= kImageLanesMin ? (size_t)((n_items + 31) / 32) * P * 32 * sizeof(float) : 0;
+    return round_up((size_t)n_items * cells * sizeof(long long), 256) + round_up(timg, 256) +
+           round_up((size_t)n_items * kScaleParts * sizeof(float), 256);
+}
+
+// SATPILA_PROJECTOR=pixel in the environment selects the pixel-driven
+// projector wherever the ray-driven one could run (to compare the two).
+bool projector_forced_pixel() {
+    const char* v = std::getenv("SATPILA_PROJECTOR");
+    return v && std::strcmp(v, "pixel") == 0;
+}
+
+void use_ray_projector(ProjArgs& a, const satpila_pila* p, void* ws) {
+    a.ray_off = p->d_ray_off;
+    a.ray_ent = p->d_ray_ent;
+    a.ray_ws = p->d_ray_off ? ws : nullptr;
+}
+
+namespace {
+
+cudaError_t launch_ray_projector(ProjArgs& a, int n_items, cudaStream_t s) {
+    const long long P = (long long)a.n * a.n, cells = (long long)a.U * a.B;
+    const bool lanes_are_images = n_items >= kImageLanesMin;
+    const size_t sums = round_up((size_t)n_items * cells * sizeof(long long), 256);
+    const size_t timg = lanes_are_images ? round_up((size_t)((n_items + 31) / 32) * P * 32 * sizeof(float), 256) : 0;
+    char* ws = static_cast<char*>(a.ray_ws);
+    a.partial = reinterpret_cast<long long*>(ws);
+    a.timg = reinterpret_cast<float*>(ws + sums);
+    a.max_parts = reinterpret_cast<float*>(ws + sums + timg);
+    cudaError_t e;
+    proj_scale_kernel<<<dim3(kScaleParts, n_items), kProjThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (lanes_are_images) {
+        const int groups = (n_items + 31) / 32;
+        transpose_images_kernel<<<dim3((unsigned)((P + 31) / 32), groups), dim3(32, 8), 0, s>>>(a, n_items, P);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int quads = (a.U + kRowWarps - 1) / kRowWarps, chunks = (a.B + kRowBins - 1) / kRowBins;
+        const long long blocks = (long long)groups * chunks * quads;
+        ray_rows_kernel<<<(unsigned)blocks, 32 * kRowWarps, 0, s>>>(a, n_items, quads, chunks);
+    } else {
+        const long long warps = cells * n_items;
+        ray_cells_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a, n_items);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    finish_rows_kernel<<<dim3((a.U + kRowsPerBlock - 1) / kRowsPerBlock, n_items), 32 * kRowsPerBlock, 0, s>>>(
+        a, n_items);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_projector(ProjArgs& a, int n_items, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
+    if (a.ray_off && a.ray_ent && a.ray_ws && !projector_forced_pixel()) return launch_ray_projector(a, n_items, s);
     if (projector_plan(a.U, a.B, a.n, n_items, a.ws != nullptr, &a.angles_per_group, &a.n_groups, &a.lanes_log2,
                        &a.chunks) != SATPILA_OK)
         return cudaErrorInvalidValue;
@@ -462,7 +669,15 @@ int ensure_factor(satpila_pila* p, cudaStream_t s) {
     a.mask = p->d_mask;
     a.out64 = p->d_w64;
     a.out32 = p->d_w32;
-    SP_CUDA(launch_projector(a, 1, s));
+    void* ws = nullptr;
+    if (p->d_ray_off) SP_CUDA(cudaMallocAsync(&ws, ray_ws_bytes(1, p->U, p->B, p->n), s));
+    use_ray_projector(a, p, ws);
+    cudaError_t e = launch_projector(a, 1, s);
+    if (ws) {
+        const cudaError_t ef = cudaFreeAsync(ws, s);
+        if (e == cudaSuccess) e = ef;
+    }
+    SP_CUDA(e);
     return SATPILA_OK;
 }
 
@@ -507,8 +722,12 @@ extern "C" int pila_forward(const satpila_pila* p, int32_t n_images, const float
     cudaError_t e = cudaSuccess;
     void* ws = nullptr;
     int A = 0, G = 0, l = 0, chunks = 1;
-    // few images: a stream-ordered workspace lets their pixels spread over more CTAs
-    if (projector_plan(p->U, p->B, p->n, n_images, true, &A, &G, &l, &chunks) == SATPILA_OK && chunks > 1) {
+    if (p->d_ray_off && !projector_forced_pixel()) {
+        // the ray-driven projector's workspace, stream-ordered
+        e = cudaMallocAsync(&ws, ray_ws_bytes(n_images, p->U, p->B, p->n), s);
+        use_ray_projector(a, p, ws);
+    } else if (projector_plan(p->U, p->B, p->n, n_images, true, &A, &G, &l, &chunks) == SATPILA_OK && chunks > 1) {
+        // few images: a stream-ordered workspace lets their pixels spread over more CTAs
         e = cudaMallocAsync(&ws, projector_ws_bytes(n_images, p->U, p->B, p->n), s);
         a.ws = ws;
     }

@@ -240,6 +240,10 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->band_floats = (long long)p->U * pl->band_pitch + 64;
     if (p->B > projector_max_bins()) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many bins");
     pl->proj_G = p->U;  // per-angle partial sums of the resync, per chain
+    pl->geo_n = p->n;
+    pl->geo_U = p->U;
+    pl->geo_B = p->B;
+    pl->rays = p->d_ray_off != nullptr;
     pl->variant = variant;
     // Sec. III-B as written (an independent pixel per estimate): its own
     // kernel, one warp per chain, residual in global memory.
@@ -426,7 +430,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
 namespace {
 
 struct BatchLayout {
-    size_t resid, S, T0, TN, found, acc, prog, claim, err, psq, pdr, dmax, c0, cF, Sinc, bytes;
+    size_t resid, S, T0, TN, found, acc, prog, claim, err, psq, pdr, dmax, c0, cF, Sinc, rayws, bytes;
 };
 
 BatchLayout batch_layout(const Plan& pl, long long cap) {
@@ -453,6 +457,7 @@ BatchLayout batch_layout(const Plan& pl, long long cap) {
     L.c0 = carve(n * 8);
     L.cF = carve(n * 8);
     L.Sinc = carve(n * 8);
+    L.rayws = carve(pl.rays ? ray_ws_bytes(cap, pl.geo_U, pl.geo_B, pl.geo_n) : 0);
     L.bytes = off;
     return L;
 }
@@ -479,6 +484,7 @@ void batch_carve(void* base, const Plan& pl, long long cap, BatchDev* b) {
     b->cost0 = (double*)(c + L.c0);
     b->costF = (double*)(c + L.cF);
     b->S_inc = (double*)(c + L.Sinc);
+    b->proj_ws = pl.rays ? (void*)(c + L.rayws) : nullptr;
 }
 
 cudaError_t prepare_launches(const satpila_pila* p, const Plan& pl, int bome_k) {
@@ -512,6 +518,7 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
     pa.resid_pitch = pl.pitch;
     pa.part_sq = b.part_sq + (long long)c0 * G;
     pa.part_drift = b.part_drift + (long long)c0 * G;
+    if (b.proj_ws) use_ray_projector(pa, p, b.proj_ws);
     cudaError_t e = launch_projector(pa, nc, q);
     if (e != cudaSuccess) return e;
     ReduceArgs ra{};

@@ -39,6 +39,8 @@ struct Plan {
     long long band_floats = 0;   // shared-memory residual of a windowed warp
     int spt = 1;                 // stages per task
     int proj_G = 0;              // resync partial sums per chain (one per angle: U)
+    int geo_n = 0, geo_U = 0, geo_B = 0;  // the table's geometry
+    bool rays = false;           // the table has a ray-major index: resyncs run the ray-driven projector
     int variant = PLAN_RULES;
     size_t sweep_smem_bytes() const;
 };
@@ -69,6 +71,7 @@ struct BatchDev {
     double* cost0 = nullptr;       // Eq. (4) cost at the start
     double* costF = nullptr;       // Eq. (4) cost after the latest resync
     double* S_inc = nullptr;       // incremental S before the latest resync
+    void* proj_ws = nullptr;       // ray-driven projector's workspace (ray_ws_bytes for the capacity), or NULL
     const ChainCtl* ctl = nullptr; // per-chain control or NULL
     double* sweep_cost = nullptr;
     sat_trace_rec* trace = nullptr;

@@ -236,7 +236,9 @@ Geometry* satpila_server::geometry_for(const Request& r, size_t budget_left) {
     pg.angles_rad = r.angles.empty() ? nullptr : r.angles.data();
     pg.mask = r.mask.empty() ? nullptr : r.mask.data();
     satpila_pila* p = nullptr;
-    if (pila_build_in(&pg, r.precision, build_stream, pool, &p) != SATPILA_OK) return nullptr;
+    // no ray index: tables are what bounds the engine's memory (its resyncs
+    // take the pixel-driven projector)
+    if (pila_build_in(&pg, r.precision, build_stream, pool, &p, false) != SATPILA_OK) return nullptr;
     auto g = std::make_unique<Geometry>();
     g->key = std::move(key);
     g->p = p;

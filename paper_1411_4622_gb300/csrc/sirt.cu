@@ -122,7 +122,8 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     const size_t o_psq = o_corr + ((size_t)n_slices * cells * 4 + 255) / 256 * 256;
     const size_t o_cost = o_psq + ((size_t)n_slices * G * 8 + 255) / 256 * 256;
     const size_t o_proj = o_cost + ((size_t)n_slices * 8 + 255) / 256 * 256;
-    const size_t proj_ws = projector_ws_bytes(n_slices, p->U, p->B, p->n);
+    const bool rays = p->d_ray_off && !projector_forced_pixel();
+    const size_t proj_ws = rays ? ray_ws_bytes(n_slices, p->U, p->B, p->n) : projector_ws_bytes(n_slices, p->U, p->B, p->n);
     const size_t total = o_proj + proj_ws;
     SP_CUDA(cudaMalloc(&ws, total));
     char* b = (char*)ws;
@@ -155,7 +156,8 @@ extern "C" int sirt_run(const satpila_pila* p_const, int32_t n_slices, const flo
     pa.resid_stride = cells;
     pa.w = p->d_w32;
     pa.part_sq = psq;
-    pa.ws = proj_ws ? b + o_proj : nullptr;
+    if (rays) use_ray_projector(pa, p, b + o_proj);
+    else pa.ws = proj_ws ? b + o_proj : nullptr;
     ReduceArgs ra{};
     ra.n_items = n_slices;
     ra.n_rows = G;

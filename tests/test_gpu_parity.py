@@ -150,6 +150,80 @@ def test_forward_projection(api):
     api.pila_free(p)
 
 
+class _pixel_projector:
+    """Selects the pixel-driven projector for the calls inside the block."""
+
+    def __enter__(self):
+        import os
+
+        os.environ["SATPILA_PROJECTOR"] = "pixel"
+
+    def __exit__(self, *exc):
+        import os
+
+        os.environ.pop("SATPILA_PROJECTOR", None)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("n,U,B,items", [(64, 90, 91, 1), (48, 40, 69, 3), (37, 45, 53, 24), (50, 33, 71, 45),
+                                          (128, 120, 181, 64)])
+def test_ray_projector_bit_identical_to_pixel_projector(api, prec, n, U, B, items):
+    """The ray-driven projector (ray-major index, sums in registers) adds the
+    same exact fixed-point terms as the pixel-driven one: projections equal
+    to the bit, in the entry-lanes form (few images) and the image-lanes form
+    (24 and more; ragged last group), with zero and negative pixels."""
+    rng = np.random.default_rng(n + U + items)
+    img = rng.random((items, n, n)).astype(np.float32)
+    img[:, :3, :] = 0.0
+    img[0, n // 2, :] = -0.25
+    p = api.pila_build(n, U, B, prec)
+    got = api.pila_forward(p, dev(img)).cpu().numpy()
+    with _pixel_projector():
+        ref = api.pila_forward(p, dev(img)).cpu().numpy()
+    assert np.array_equal(got, ref)
+    api.pila_free(p)
+
+
+@pytest.mark.parametrize("chains", [5, 30])
+def test_ray_projector_resync_and_sirt_bit_identical(api, chains):
+    """Annealing with a resync after every stage, and SIRT, give bit-identical
+    images, costs and drifts with either projector (the per-angle sums of
+    squares are formed in the same fixed order)."""
+    n, U = 48, 60
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    sinos = np.stack([oracle.drt(synth.phantom(n, 6, 70 + i) * mask, U, B) for i in range(chains)]).astype(np.float32)
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * chains).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    kw = dict(bome_k=4, n_sweeps=4, t0=-1.0, tn=-1.0, seed=91, resync_every=1, flags=api.SAT_FLAG_NO_GRAPH)
+    a = dev(img0)
+    st_a = api.sat_run(p, dev(sinos), a, **kw)
+    with _pixel_projector():
+        b = dev(img0)
+        st_b = api.sat_run(p, dev(sinos), b, **kw)
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    for x, y in zip(st_a, st_b):
+        for k in ("t0", "initial_cost", "final_cost", "final_cost_incremental", "max_resync_drift", "accepted"):
+            assert x[k] == y[k], k
+    sa, ca = dev(img0[:3]), torch.zeros((3, 5), dtype=torch.float64, device="cuda")
+    api.sirt_run(p, dev(sinos[:3]), sa, n_iter=5, costs=ca)
+    with _pixel_projector():
+        sb, cb = dev(img0[:3]), torch.zeros((3, 5), dtype=torch.float64, device="cuda")
+        api.sirt_run(p, dev(sinos[:3]), sb, n_iter=5, costs=cb)
+    assert np.array_equal(sa.cpu().numpy(), sb.cpu().numpy())
+    assert np.array_equal(ca.cpu().numpy(), cb.cpu().numpy())
+    # the SIRT factor matrix of a fresh table, built either way
+    q = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+    w_ray = api.pila_sirt_factor(q)
+    api.pila_free(q)
+    with _pixel_projector():
+        q = api.pila_build(n, U, B, api.PILA_F32, mask=mask)
+        w_pix = api.pila_sirt_factor(q)
+        api.pila_free(q)
+    assert np.array_equal(w_ray, w_pix)
+    api.pila_free(p)
+
+
 def test_sirt_factor(api):
     n, U = 48, 30
     B = synth.bins_for(n)
