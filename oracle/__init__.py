@@ -28,15 +28,17 @@ LEN_EXACT, LEN_BINARY16, LEN_BYTE180 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so from the C++ sources with g++ (portable flags)."""
+    """Compile liboracle.so from the C++ sources with g++ (portable flags;
+    no fused multiply-add contraction, so every FP64 expression is evaluated
+    as written, with the same roundings on every host)."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     hdr = os.path.join(_HERE, "oracle.h")
     if not force and os.path.exists(_LIB_PATH):
         newest = max(os.path.getmtime(p) for p in srcs + [hdr])
-        if os.path.getmtime(_LIB_PATH) >= newest:
+        if os.path.getmtime(_LIB_PATH) >= max(newest, os.path.getmtime(__file__)):
             return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp] + srcs
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + srcs
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
