@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
     ap.add_argument("--flags", type=int, default=2,
                     help="SAT_FLAG_* bits for the batched run (default 2: the autotuner picks the launch layout)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "precision512", "serve", "bome", "drt", "fbp", "rows"],
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "precision512", "precision512-rmse", "serve", "bome", "drt", "fbp", "rows"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
                          "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
                          "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A); "
@@ -69,6 +70,9 @@ def parse():
     ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
                     help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
     ap.add_argument("--tables", default="f16,f32", help="precision512: table precisions, comma separated")
+    ap.add_argument("--part", default="both", choices=["both", "gpu", "oracle"],
+                    help="precision512-rmse: run the GPU side, the oracle side (no GPU needed) or both")
+    ap.add_argument("--oracle-chains", type=int, default=4, help="precision512-rmse: chains the oracle follows")
     ap.add_argument("--no-c4", action="store_true", help="default run: skip the 512^2 sub-object")
     ap.add_argument("--no-serve", action="store_true", help="default run: skip the serving sub-object")
     ap.add_argument("--serve-requests", type=int, default=200, help="default run: requests of the serving sub-object")
@@ -527,6 +531,119 @@ def run_precision(args):
     print(json.dumps(out))
 
 
+def _c4_problem(i):
+    """Slice i of the 512^2 configuration for the oracle comparison: phantom
+    (40 ellipses, disk reconstruction space), the oracle's FP64 Siddon DRT of
+    it, Poisson noise at 1e5 photons, rounded to float32 (the values both
+    sides read)."""
+    import oracle
+
+    cfg = synth.WORKLOADS["precision512"]
+    n, U, B = cfg["n"], cfg["n_angles"], cfg["n_bins"]
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, cfg["ellipses"], synth.slice_seeds(i)[0]) * mask
+    pm = synth.poisson_noise(oracle.drt(ph, U, B), cfg["noise"][1], synth.slice_seeds(i)[1]).astype(np.float32)
+    return ph, pm, mask
+
+
+def _c4_oracle_chain(job):
+    """Worker: the FP64 oracle over chain c's whole schedule (lengths exact or
+    rounded to binary16 as the FP16 table stores them); final RMSE against
+    the phantom on the reconstruction space."""
+    import oracle
+
+    c, slice_idx, seed, stages, fmt = job
+    ph, pm, mask = _c4_problem(slice_idx)
+    cfg = synth.WORKLOADS["precision512"]
+    t = time.perf_counter()
+    img, st, _ = oracle.sat_run(pm.astype(np.float64), synth.initial_image(cfg["n"], 0.5, mask), n_sweeps=stages,
+                                bome_k=cfg["bome_k"], mask=mask, seed=seed, beta=cfg["beta"], length_format=fmt)
+    return {"chain": c, "slice": slice_idx, "length_format": ["exact", "binary16", "byte180"][fmt],
+            "rmse": float(synth.rmse(img, ph, mask)), "final_cost": st["final_cost_fresh"], "t0": st["t0"],
+            "accepted": st["accepted"], "seconds": time.perf_counter() - t}
+
+
+def run_precision_rmse(args):
+    """The 512^2 configuration in full, with its errors against the FP64
+    oracle: C chains (slice c mod 8, seed 3000 + c), 200 stages of full M,
+    K = 8, resync after every stage, T0 by Eq. (8), on the FP16 and the FP32
+    table; final RMSE against the phantom per chain, drift per resync.  The
+    oracle runs the first chains over the same schedule with exact lengths
+    and with the binary16 lengths of the FP16 table (one process per chain).
+    --part gpu / oracle runs one side (the oracle needs no GPU)."""
+    cfg = synth.WORKLOADS["precision512"]
+    n, K = cfg["n"], cfg["bome_k"]
+    S = args.sweeps or cfg["n_sweeps"]
+    C = args.slices or 16
+    n_or = min(C, args.oracle_chains)
+    seed0 = synth.slice_seeds(0)[2]
+    out = {"metric": "final RMSE against the phantom, 512x512, GPU (FP16 / FP32 table) and FP64 oracle",
+           "unit": "rmse", "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "precision512-rmse", "chains": C, "distinct_slices": min(8, C), "n": n,
+                      "angles": cfg["n_angles"], "bins": cfg["n_bins"], "bome_k": K, "stages": S,
+                      "moves_per_stage": "all reconstruction-space pixels", "resync_every": 1,
+                      "oracle_chains": n_or, "sinogram": "oracle FP64 Siddon DRT + Poisson 1e5, as float32"}}
+    import multiprocessing as mp
+
+    pool = None
+    if args.part in ("both", "oracle") and n_or > 0:
+        import oracle
+
+        oracle.build()
+        jobs = [(c, c % 8, seed0 + c, S, fmt) for fmt in (0, 1) for c in range(n_or)]
+        pool = mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1))
+        pending = pool.map_async(_c4_oracle_chain, jobs, chunksize=1)
+    if args.part in ("both", "gpu"):
+        import torch
+
+        from paper_1411_4622_gb300 import api
+        from paper_1411_4622_gb300 import build as libbuild
+
+        libbuild.build()
+        torch.cuda.set_device(0)
+        distinct = min(8, C)
+        probs = [_c4_problem(i) for i in range(distinct)]
+        mask = probs[0][2]
+        M = int(mask.sum())
+        sino = torch.tensor(np.stack([probs[c % distinct][1] for c in range(C)]), device="cuda").contiguous()
+        init = torch.tensor(np.stack([synth.initial_image(n, 0.5, mask)] * C), dtype=torch.float32, device="cuda")
+        pm_max = max(float(np.max(np.abs(p[1]))) for p in probs)
+        out["gpu"] = {}
+        for name, prec in (("f16", api.PILA_F16), ("f32", api.PILA_F32)):
+            p = api.pila_build(n, cfg["n_angles"], cfg["n_bins"], prec, mask=mask)
+            img = init.clone()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st = api.sat_run(p, sino, img, bome_k=K, n_sweeps=S, t0=-1.0, tn=-1.0, seed=seed0, resync_every=1,
+                             flags=api.SAT_FLAG_AUTOTUNE)
+            wall = time.perf_counter() - t
+            api.pila_free(p)
+            final = img.cpu().numpy()
+            rm = [float(synth.rmse(final[c], probs[c % distinct][0], mask)) for c in range(C)]
+            out["gpu"][name] = {"rmse": rm, "rmse_mean": float(np.mean(rm)),
+                                "final_cost": [x["final_cost"] for x in st], "t0": [x["t0"] for x in st],
+                                "drift_max_rel": max(x["max_resync_drift"] for x in st) / pm_max,
+                                "moves_per_s": C * S * M / wall, "sweep_ms": st[0]["sweep_ms"], "wall_s": wall,
+                                "launch": launch_name(st[0]["plan"], api.SAT_FLAG_AUTOTUNE)}
+        g16, g32 = out["gpu"]["f16"]["rmse"], out["gpu"]["f32"]["rmse"]
+        out["f16_vs_f32_rel"] = [abs(a - b) / b for a, b in zip(g16, g32)]
+    if pool is not None:
+        res = pending.get()
+        pool.close()
+        pool.join()
+        out["oracle"] = res
+        ex = {r["chain"]: r["rmse"] for r in res if r["length_format"] == "exact"}
+        b16 = {r["chain"]: r["rmse"] for r in res if r["length_format"] == "binary16"}
+        out["oracle_rmse_exact"] = [ex[c] for c in sorted(ex)]
+        out["oracle_rmse_binary16"] = [b16[c] for c in sorted(b16)]
+        if "gpu" in out:
+            for name in ("f16", "f32"):
+                g = out["gpu"][name]["rmse"]
+                out["gpu"][name]["vs_oracle_exact_rel"] = [abs(g[c] - ex[c]) / ex[c] for c in sorted(ex)]
+                out["gpu"][name]["vs_oracle_binary16_rel"] = [abs(g[c] - b16[c]) / b16[c] for c in sorted(b16)]
+    print(json.dumps(out))
+
+
 def sub_first(sub):
     return next(iter(sub["tables"]))
 
@@ -949,6 +1066,8 @@ def main():
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.workload == "precision512":
         return run_precision(args)
+    if args.workload == "precision512-rmse":
+        return run_precision_rmse(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.workload == "bome":

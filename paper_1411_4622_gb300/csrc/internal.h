@@ -97,6 +97,7 @@ struct ProjArgs {
     void* ray_ws;               // ray_ws_bytes(items, U, B, n) bytes: with the index, selects the
                                 // ray-driven projector (else the pixel-driven one runs)
     float* timg;                // carved from ray_ws: images transposed to [group][P][32]
+    int* neg_group;             // carved from ray_ws: 1 for a group of 32 images holding a negative value
     int chunks;                 // set with the plan
     long long* partial;         // carved from ws when chunks > 1: [item][chunk][U][B] sums
     float* max_parts;           // [item][32] partial max|f|

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(32 * kFinishWarps) proj_finish_rows_kernel(Pro
 constexpr int kImageLanesMin = 24;  // images from which the image-lanes form runs
 constexpr int kRowWarps = 4;        // angles per block of ray_rows_kernel
 constexpr int kRowBins = 32;        // bins per block of ray_rows_kernel
-constexpr int kRowUnroll = 8;       // index entries loaded before their terms
+constexpr int kRowUnroll = 16;      // index entries loaded before their terms
 
 // 64-bit right shift by s, 0 for s >= 64 (PTX clamps the shift amount).
 __device__ __forceinline__ unsigned long long shr_clamp(unsigned long long x, uint32_t s) {
@@ -375,25 +375,71 @@ __device__ __forceinline__ long long fixed_term_bits(uint32_t bf, uint32_t bl, i
     return (bf >> 31) ? -(long long)v : (long long)v;
 }
 
+// The same term for a non-negative image value (its sign bit clear) of an
+// image whose F is at most 124: the hidden bit is set even for a zero or
+// subnormal f (ef = 0), but its exponent ef + el + ebias is then at most
+// 127 + 124 - 300 = -49 (l < 2), and a product below 2^48 times 2^-49 rounds
+// to 0, which is what the exact form gives for such f.
+__device__ __forceinline__ long long fixed_term_nonneg(uint32_t bf, uint32_t bl, int ebias) {
+    const int e = (int)(bf >> 23) + (int)(bl >> 23) + ebias;
+    const unsigned long long m =
+        (unsigned long long)((bf & 0x7fffffu) | 0x800000u) * (unsigned long long)((bl & 0x7fffffu) | 0x800000u);
+    const unsigned long long t = shr_clamp(m << 15, (uint32_t)(14 - e));
+    return (long long)((t + 1ull) >> 1);
+}
+
 __device__ __forceinline__ long long fixed_term(float f, float l, int F) {
     return fixed_term_bits(__float_as_uint(f), __float_as_uint(l), F - 300);
 }
 
-// T[g][p][lane] = image (32 g + lane) at pixel p, 0 past the last image.
+// T[g][p][lane] = image (32 g + lane) at pixel p (-0 as +0: the same term),
+// 0 past the last image; neg_group[g] = 1 if the group holds a negative value.
 __global__ void transpose_images_kernel(const ProjArgs a, int n_items, long long P) {
     __shared__ float tile[32][33];
     const int g = blockIdx.y;
     const long long p0 = (long long)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
+    bool neg = false;
     for (int r = ty; r < 32; r += 8) {
         const int item = g * 32 + r;
         const long long p = p0 + tx;
-        tile[r][tx] = (item < n_items && p < P) ? a.img[(long long)item * a.img_stride + p] : 0.0f;
+        const float v = (item < n_items && p < P) ? __fadd_rn(a.img[(long long)item * a.img_stride + p], 0.0f) : 0.0f;
+        neg = neg || v < 0.0f;
+        tile[r][tx] = v;
     }
-    __syncthreads();
+    if (__syncthreads_or(neg) && tx == 0 && ty == 0) atomicOr(&a.neg_group[g], 1);
     for (int r = ty; r < 32; r += 8) {
         const long long p = p0 + r;
         if (p < P) a.timg[((long long)g * P + p) * 32 + tx] = tile[tx][r];
+    }
+}
+
+// The warp's rays: bins k0 .. k1-1 of angle row `off`, lane = image.
+template <bool NONNEG>
+__device__ __forceinline__ void ray_rows_sum(const ProjArgs& a, const float* T, const uint32_t* off, int k0, int k1,
+                                             int ebias, long long* out, bool live) {
+    uint32_t e1 = off[k0];
+    for (int k = k0; k < k1; ++k) {
+        uint32_t e = e1;
+        e1 = off[k + 1];
+        long long acc = 0;
+        for (; e + kRowUnroll <= e1; e += kRowUnroll) {
+            uint2 en[kRowUnroll];
+            uint32_t f[kRowUnroll];
+#pragma unroll
+            for (int j = 0; j < kRowUnroll; ++j) en[j] = a.ray_ent[e + j];
+#pragma unroll
+            for (int j = 0; j < kRowUnroll; ++j) f[j] = __float_as_uint(T[(long long)en[j].x * 32]);
+#pragma unroll
+            for (int j = 0; j < kRowUnroll; ++j)
+                acc += NONNEG ? fixed_term_nonneg(f[j], en[j].y, ebias) : fixed_term_bits(f[j], en[j].y, ebias);
+        }
+        for (; e < e1; ++e) {
+            const uint2 en = a.ray_ent[e];
+            const uint32_t f = __float_as_uint(T[(long long)en.x * 32]);
+            acc += NONNEG ? fixed_term_nonneg(f, en.y, ebias) : fixed_term_bits(f, en.y, ebias);
+        }
+        if (live) out[k] = acc;
     }
 }
 
@@ -412,33 +458,19 @@ __global__ void __launch_bounds__(32 * kRowWarps) ray_rows_kernel(const ProjArgs
     float m = 0.0f;
     if (item < n_items)
         for (int q = 0; q < kScaleParts; ++q) m = fmaxf(m, a.max_parts[(long long)item * kScaleParts + q]);
-    const int ebias = fraction_bits_of_max(a, m) - 300;  // the lane's image's F, as fixed_term folds it
+    const int F = fraction_bits_of_max(a, m);
+    const int ebias = F - 300;  // the lane's image's F, as fixed_term folds it
     const long long P = (long long)a.n * a.n;
     const float* T = a.timg + (long long)g * P * 32 + lane;
     const uint32_t* off = a.ray_off + (long long)u * a.B;
     long long* out = a.partial + ((long long)item * a.U + u) * a.B;
     const int k0 = c * kRowBins, k1 = min(a.B, k0 + kRowBins);
-    uint32_t e1 = off[k0];
-    for (int k = k0; k < k1; ++k) {
-        uint32_t e = e1;
-        e1 = off[k + 1];
-        long long acc = 0;
-        for (; e + kRowUnroll <= e1; e += kRowUnroll) {
-            uint2 en[kRowUnroll];
-            float f[kRowUnroll];
-#pragma unroll
-            for (int j = 0; j < kRowUnroll; ++j) en[j] = a.ray_ent[e + j];
-#pragma unroll
-            for (int j = 0; j < kRowUnroll; ++j) f[j] = T[(long long)en[j].x * 32];
-#pragma unroll
-            for (int j = 0; j < kRowUnroll; ++j) acc += fixed_term_bits(__float_as_uint(f[j]), en[j].y, ebias);
-        }
-        for (; e < e1; ++e) {
-            const uint2 en = a.ray_ent[e];
-            acc += fixed_term_bits(__float_as_uint(T[(long long)en.x * 32]), en.y, ebias);
-        }
-        if (item < n_items) out[k] = acc;
-    }
+    const bool live = item < n_items;
+    // the short form needs every lane's image free of negative values and F <= 124
+    if (__all_sync(0xffffffffu, F <= 124) && a.neg_group[g] == 0)
+        ray_rows_sum<true>(a, T, off, k0, k1, ebias, out, live);
+    else
+        ray_rows_sum<false>(a, T, off, k0, k1, ebias, out, live);
 }
 
 // One warp per (image, ray), image-major; lanes over the ray's entries.
@@ -559,12 +591,14 @@ cudaError_t prepare_projector() {
     return e;
 }
 
-// [item][U][B] sums, the transposed images (many images), the max|f| parts.
+// [item][U][B] sums, the transposed images and a flag per group (many
+// images), the max|f| parts.
 size_t ray_ws_bytes(long long n_items, int U, int B, int n) {
     const long long P = (long long)n * n, cells = (long long)U * B;
-    const size_t timg = n_items >= kImageLanesMin ? (size_t)((n_items + 31) / 32) * P * 32 * sizeof(float) : 0;
+    const long long groups = (n_items + 31) / 32;
+    const size_t timg = n_items >= kImageLanesMin ? (size_t)groups * P * 32 * sizeof(float) : 0;
     return round_up((size_t)n_items * cells * sizeof(long long), 256) + round_up(timg, 256) +
-           round_up((size_t)n_items * kScaleParts * sizeof(float), 256);
+           round_up((size_t)n_items * kScaleParts * sizeof(float), 256) + round_up((size_t)groups * sizeof(int), 256);
 }
 
 // SATPILA_PROJECTOR=pixel in the environment selects the pixel-driven
@@ -588,14 +622,16 @@ cudaError_t launch_ray_projector(ProjArgs& a, int n_items, cudaStream_t s) {
     const size_t sums = round_up((size_t)n_items * cells * sizeof(long long), 256);
     const size_t timg = lanes_are_images ? round_up((size_t)((n_items + 31) / 32) * P * 32 * sizeof(float), 256) : 0;
     char* ws = static_cast<char*>(a.ray_ws);
+    const int groups = (n_items + 31) / 32;
     a.partial = reinterpret_cast<long long*>(ws);
     a.timg = reinterpret_cast<float*>(ws + sums);
     a.max_parts = reinterpret_cast<float*>(ws + sums + timg);
+    a.neg_group = reinterpret_cast<int*>(ws + sums + timg + round_up((size_t)n_items * kScaleParts * sizeof(float), 256));
     cudaError_t e;
     proj_scale_kernel<<<dim3(kScaleParts, n_items), kProjThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (lanes_are_images) {
-        const int groups = (n_items + 31) / 32;
+        if ((e = cudaMemsetAsync(a.neg_group, 0, (size_t)groups * sizeof(int), s)) != cudaSuccess) return e;
         transpose_images_kernel<<<dim3((unsigned)((P + 31) / 32), groups), dim3(32, 8), 0, s>>>(a, n_items, P);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int quads = (a.U + kRowWarps - 1) / kRowWarps, chunks = (a.B + kRowBins - 1) / kRowBins;
