@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--residency", type=int, default=0, help="0 auto, 1 shared memory, 2 global memory")
     ap.add_argument("--group-warps", type=int, default=0, help="warps per chain (0: chosen by size)")
-    ap.add_argument("--flags", type=int, default=2,
-                    help="SAT_FLAG_* bits for the batched run (default 2: the autotuner picks the launch layout)")
+    ap.add_argument("--flags", type=int, default=0,
+                    help="SAT_FLAG_* bits for the batched run (2: the autotuner picks the launch layout; --plan 0)")
+    ap.add_argument("--plan", type=int, default=1,
+                    help="SAT_PLAN_* launch layout of the batched run (default 1, the windowed kernel with its "
+                         "residual band in shared memory: the autotuner's pick for this shape); 0: rules/autotuner")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "precision512", "precision512-rmse", "serve", "bome", "drt", "fbp", "rows"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
@@ -159,9 +162,10 @@ KERNEL_SOURCES = {
 }
 
 
-def launch_name(plan, flags):
+def launch_name(plan, flags, pinned=0):
     """The launch layout a run used, and who chose it."""
-    who = "autotuned: " if flags & 2 else "requested: " if flags & 16 else "size rules: "
+    who = ("pinned: " if pinned else "autotuned: " if flags & 2 else "requested: " if flags & 16
+           else "size rules: ")
     return who + PLAN_NAMES.get(plan, str(plan))
 
 
@@ -419,8 +423,8 @@ def precision_phantoms(cfg, distinct):
     return ph, noisy, mask
 
 
-def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2, warmup=1, flags=2,
-                     residency=0, group_warps=0):
+def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2, warmup=1, flags=0,
+                     residency=0, group_warps=0, plan=8):
     """The 512^2 configuration as configured, on a bounded sample of its
     schedule: C chains of 512x512 slices (8 distinct phantoms, each chain its
     own seed), 360 angles, 725 bins, K = 8, M = every reconstruction-space
@@ -449,6 +453,17 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2
     images = init.clone()
     stream = torch.cuda.current_stream()
     moves = chains * stages * M
+    # the sector-gather rate of this working set: one region per chain the
+    # size of its residual (U rows of B + 1 cells padded to 4, plus the
+    # lanes' dummy cells), all chains' residuals at once (partly L2-resident)
+    resid_bytes = (U * ((B + 1 + 3) // 4 * 4) + 256) * 4 // 32 * 32
+    buf = torch.ones(chains * resid_bytes, dtype=torch.uint8, device="cuda")
+    from paper_1411_4622_gb300 import api as _api
+
+    pk = dict(pk, ws_sector_gbs=_api.probe_read(buf, _api.PROBE_SECTOR, loads=1 << 27, region_bytes=resid_bytes),
+              ws_bytes=chains * resid_bytes)
+    del buf
+    torch.cuda.empty_cache()
     out = {"workload": "precision512", "chains": chains, "distinct_slices": distinct, "n": n, "angles": U,
            "bins": B, "bome_k": K, "moves_per_stage": M, "stages": stages, "resync_every": 1,
            "sample": f"{stages} stages of full M (a linear schedule of {stages} stages from Eq. (8)'s T0; the "
@@ -457,7 +472,7 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2
     for t in tables:
         prec = {"f16": api.PILA_F16, "f32": api.PILA_F32, "u8": api.PILA_U8}[t]
         kw = dict(bome_k=K, n_sweeps=stages, moves_per_sweep=M, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2],
-                  resync_every=1, residency=residency, group_warps=group_warps, flags=flags)
+                  resync_every=1, residency=residency, group_warps=group_warps, flags=flags, plan=plan)
         info = {}
 
         def step():
@@ -482,10 +497,11 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2
         sectors = U * (1.0 + (E / U - 1.0) / 8.0)
         sector_resid = 32.0 * sectors * (1.0 + acc) + 8.0 * (1.0 + acc)
         useful = row_bytes + 4.0 * E * (1.0 + acc) + 4.0 * (1.0 + acc)
-        # seconds of memory time per move at the probe rates: rows streamed,
-        # residual sectors gathered
+        # seconds of memory time per move at the probe rates: rows streamed
+        # from HBM (the table is 6-12x L2), residual sectors gathered from the
+        # chains' residuals (the probe over the same footprint)
         t_row = row_bytes / (pk["hbm_stream_gbs"] * 1e9)
-        t_sec = sector_resid / (pk["hbm_sector_gbs"] * 1e9)
+        t_sec = sector_resid / (pk["ws_sector_gbs"] * 1e9)
         kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_sweep_kernel")
         tpm = stored_traffic(kernel, "precision512")
         achieved = (row_bytes + sector_resid) * rate / 1e9
@@ -493,15 +509,18 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2
         out["tables"][t] = {
             "moves_per_s": moves / (ms / 1e3), "sweep_moves_per_s": rate, "ms_per_step": ms, "sweep_ms": sweep_ms,
             "other_ms": ms - sweep_ms, "acceptance": acc, "table_bytes": info["table_bytes"],
-            "launch": launch_name(st[0]["plan"], flags),
+            "launch": launch_name(st[0]["plan"], flags, plan),
             "drift_max_rel": max(x["max_resync_drift"] for x in st) / pm_max,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_eff, "unit": "GB/s",
                          "frac": achieved / peak_eff, "kernel": kernel,
                          "bytes_per_move": row_bytes + sector_resid, "row_bytes": row_bytes,
                          "sector_bytes": sector_resid, "useful_bytes_per_move": useful,
-                         "peak_rule": "rows at the HBM stream rate, residual sectors at the HBM sector-gather rate",
+                         "peak_rule": "rows at the HBM stream rate, residual sectors at the sector-gather rate of "
+                                      "the chains' residual footprint (one 1.05 MB region per chain)",
                          "frac_rows": row_bytes * rate / 1e9 / pk["hbm_stream_gbs"],
-                         "frac_sectors": sector_resid * rate / 1e9 / pk["hbm_sector_gbs"],
+                         "frac_sectors": sector_resid * rate / 1e9 / pk["ws_sector_gbs"],
+                         "frac_sectors_vs_hbm_probe": sector_resid * rate / 1e9 / pk["hbm_sector_gbs"],
+                         "ws_sector_gbs": pk["ws_sector_gbs"],
                          "traffic": tpm * chains * stages * M if tpm is not None else None,
                          "traffic_over_sector_bytes": tpm / (row_bytes + sector_resid) if tpm is not None else None},
             "clocks": clk}
@@ -521,7 +540,8 @@ def run_precision(args):
     pk = measure_peaks(api)
     sub = precision_sample(pk, chains=args.slices or 304, stages=args.sweeps or 2, steps=args.steps,
                            warmup=args.warmup, flags=args.flags, residency=args.residency,
-                           group_warps=args.group_warps, tables=tuple(args.tables.split(",")))
+                           group_warps=args.group_warps, tables=tuple(args.tables.split(",")),
+                           plan=8 if args.plan == 1 else args.plan)
     main = sub["tables"][sub_first(sub)]
     out = {"metric": "SAT pixel-moves/s, 512x512 slices, resync every stage", "value": main["moves_per_s"],
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
@@ -1112,7 +1132,7 @@ def main():
     images = init.clone()
     seed0 = synth.slice_seeds(first)[2]  # chain c uses seed0 + c: global slice numbering
     run_kw = dict(bome_k=K, n_sweeps=S, t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0,
-                  residency=args.residency, group_warps=args.group_warps, flags=args.flags)
+                  residency=args.residency, group_warps=args.group_warps, flags=args.flags, plan=args.plan)
     stream = torch.cuda.current_stream()
     info = {}
 
@@ -1229,7 +1249,7 @@ def main():
            "config": {"workload": WORKLOAD, "slices_per_gpu": slices, "n": n, "angles": U, "bins": B,
                       "bome_k": K, "stages": S, "moves_per_stage": M, "pila": args.pila,
                       "l2": "flushed between timed steps (256 MB write)",
-                      "launch": launch_name(st[0]["plan"], args.flags), "graph": True},
+                      "launch": launch_name(st[0]["plan"], args.flags, args.plan), "graph": True},
            "evaluations_per_s": value * K, "acceptance": acc,
            "rmse": {"batched_mean": float(rmse_batched.mean())}, "plain": plain,
            "latency_ms": {"slice_p50": float(np.percentile(step_ms, 50)),

@@ -41,7 +41,7 @@ extern "C" {
 #define SATPILA_ERR_OOM (-2)
 #define SATPILA_ERR_CUDA (-3)
 #define SATPILA_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up */
-#define SATPILA_ERR_BOUNDS (-5)    /* a device-side index check failed */
+/* -5 is not used */
 #define SATPILA_ERR_BUSY (-6)      /* serving: no slot or memory free right now */
 #define SATPILA_ERR_NOT_FOUND (-7) /* serving: unknown ticket */
 #define SATPILA_ERR_PENDING (-8)   /* serving: result not ready yet */
@@ -59,7 +59,8 @@ int satpila_version(void);
 #define PILA_F16 1 /* record: int16 bin0, int16 bin1, half len0, half len1 (8 B)    */
 #define PILA_U8 2  /* record: uint16 bin0, uint8 180*len0, uint8 180*len1 (4 B): the
                       one-byte lengths of Sec. II-B (length = q * fl(1/180)); entry 1
-                      sits on bin0 + 1.  Read by the windowed kernel (<= 128 angles) */
+                      sits on bin0 + 1.  Read by the windowed kernels (one warp per chain
+                      up to 128 angles, groups of 2 or 4 warps up to 256 and 512) */
 
 typedef struct satpila_pila satpila_pila;
 
@@ -140,7 +141,11 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
 
 #define SAT_FLAG_NO_GRAPH 1u  /* launch kernels directly instead of a cached CUDA graph */
 #define SAT_FLAG_AUTOTUNE 2u  /* time the launch candidates once per shape and keep the best:
-                                 warps per chain (angle tiling), chains per CTA and residency */
+                                 warps per chain (angle tiling), chains per CTA and residency.
+                                 With SATPILA_TUNE_CACHE=<file> in the environment the picks are
+                                 also read from and appended to that file, so that later processes
+                                 use the same layout (sat_stats.plan reports it; pass it back as
+                                 sat_params.plan to pin it) */
 #define SAT_FLAG_HYBRID 4u    /* with more chains than shared-memory slots, also run chains on
                                  global-memory warps beside them (same arithmetic) */
 #define SAT_FLAG_BOME_INDEPENDENT 8u /* BoME as Sec. III-B words it: each estimate is its own random
@@ -150,6 +155,11 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
                                  the chosen estimate's pixel.  Residual in global memory. */
 #define SAT_FLAG_WINDOW_GROUPS 16u /* with group_warps 2 or 4 (and no autotuning): the windowed
                                  move on that many warps per chain, residual in global memory */
+#define SAT_FLAG_TEST_STALL 32u /* test hook for the timeout path: the sweep kernel never reports
+                                 chain 0's first stage as done, so the task of its next stage waits
+                                 until wait_ms runs out, gives up, and the call returns
+                                 SATPILA_ERR_TIMEOUT (stats.status too) with the device usable.
+                                 Stages are then one task each.  Not for production runs. */
 
 typedef struct {
     int32_t pixel;     /* pixel index i*n + j */
@@ -180,6 +190,10 @@ typedef struct {
     int32_t pipeline_depth;  /* PILA rows in flight per chain, 3..8; 0: default (4) */
     sat_trace_rec* trace;    /* n_sweeps*M records for trace_chain (host or device), or NULL */
     double* sweep_cost;      /* [n_chains][n_sweeps] cost after each sweep (host or device), or NULL */
+    int32_t plan;            /* SAT_PLAN_* launch layout to use (1..8; INVALID_ARG if it does not fit);
+                                0: size rules, or the autotuner with SAT_FLAG_AUTOTUNE */
+    int32_t wait_ms;         /* bound on every device-side wait of a chain for its earlier stages
+                                (ms); 0: 20000 */
 } sat_params;
 
 typedef struct {
@@ -232,8 +246,8 @@ typedef struct {
  * recently used first out, dropped by pila_free) so that repeating the call
  * with the same table, buffers and parameters replays it.  Calls with host
  * buffers launch directly.
- * Errors: INVALID_ARG, OOM, CUDA; TIMEOUT/BOUNDS if a device-side check fired
- * (also reported per chain in stats.status).
+ * Errors: INVALID_ARG, OOM, CUDA; TIMEOUT if a bounded device-side wait gave
+ * up (also reported per chain in stats.status).
  */
 int sat_run(const satpila_pila* p, int32_t n_chains, const float* sino_meas, float* images,
             const sat_params* prm, sat_stats* stats, void* stream);

@@ -13,13 +13,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsatpila.so")
 
 OK = 0
-ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS, ERR_BUSY, ERR_NOT_FOUND, ERR_PENDING = (
-    -1, -2, -3, -4, -5, -6, -7, -8)
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_NOT_FOUND, ERR_PENDING = (-1, -2, -3, -4, -6, -7, -8)
 PILA_F32, PILA_F16, PILA_U8 = 0, 1, 2
 SAT_SCHED_LINEAR, SAT_SCHED_GEOMETRIC, SAT_SCHED_CUBIC = 0, 1, 2
 SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
 SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID, SAT_FLAG_BOME_INDEPENDENT = 1, 2, 4, 8
 SAT_FLAG_WINDOW_GROUPS = 16
+SAT_FLAG_TEST_STALL = 32
 (SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
  SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4) = range(9)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
@@ -55,7 +55,7 @@ class SatParams(C.Structure):
                 ("schedule", C.c_int32), ("t0_samples", C.c_int32), ("seed", C.c_uint64),
                 ("resync_every", C.c_int32), ("residency", C.c_int32), ("flags", C.c_uint32),
                 ("trace_chain", C.c_int32), ("group_warps", C.c_int32), ("pipeline_depth", C.c_int32),
-                ("trace", C.c_void_p), ("sweep_cost", C.c_void_p)]
+                ("trace", C.c_void_p), ("sweep_cost", C.c_void_p), ("plan", C.c_int32), ("wait_ms", C.c_int32)]
 
 
 class SatStats(C.Structure):

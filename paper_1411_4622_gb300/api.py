@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib as L
 from ._lib import (PILA_F16, PILA_F32, PILA_U8, SAT_FLAG_AUTOTUNE, SAT_FLAG_BOME_INDEPENDENT, SAT_FLAG_HYBRID,  # noqa: F401
-                   SAT_FLAG_NO_GRAPH,
+                   SAT_FLAG_NO_GRAPH, SAT_FLAG_TEST_STALL, ERR_TIMEOUT,
                    SAT_RESIDENT_AUTO,
                    SAT_RESIDENT_GLOBAL, SAT_RESIDENT_SMEM, SAT_SCHED_CUBIC, SAT_SCHED_GEOMETRIC,
                    SAT_SCHED_LINEAR, SIRT_SEQUENTIAL, SIRT_SIMULTANEOUS, SatpilaError)
@@ -144,11 +144,11 @@ def pila_sirt_factor(p: Pila, stream=None) -> np.ndarray:
 def sat_params(*, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn=-1.0,
                schedule=SAT_SCHED_LINEAR, t0_samples=200, seed=0, resync_every=0,
                residency=SAT_RESIDENT_AUTO, flags=0, trace_chain=-1, group_warps=0, pipeline_depth=0, trace=None,
-               sweep_cost=None):
+               sweep_cost=None, plan=0, wait_ms=0):
     return L.SatParams(float(beta), int(bome_k), int(n_sweeps), int(moves_per_sweep), float(t0), float(tn),
                        int(schedule), int(t0_samples), int(seed) & (2**64 - 1), int(resync_every),
                        int(residency), int(flags), int(trace_chain), int(group_warps), int(pipeline_depth), _ptr(trace),
-                       _ptr(sweep_cost))
+                       _ptr(sweep_cost), int(plan), int(wait_ms))
 
 
 def sat_run(p: Pila, sino_meas, images, stream=None, **kw) -> list[dict]:

@@ -10,7 +10,10 @@
 // (unless SAT_FLAG_NO_GRAPH), so a repeated call costs one graph launch.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <list>
 #include <memory>
 #include <mutex>
@@ -285,7 +288,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     // engine's mixed launches gave lower request latency.)
     if (variant == PLAN_WINDOW_G2 || variant == PLAN_WINDOW_G4) {
         const int Wg = variant == PLAN_WINDOW_G2 ? 2 : 4;
-        if (rt == PILA_U8 || prm->residency == SAT_RESIDENT_SMEM || records_per_lane(Wg) > 4)
+        if (prm->residency == SAT_RESIDENT_SMEM || records_per_lane(Wg) > 4)
             return fail(SATPILA_ERR_INVALID_ARG, "sat_run: no windowed group launch for this table");
         const int jw = records_per_lane(Wg) <= 2 ? 2 : 4;
         const int stage = 512 * Wg * (jw / rpc);
@@ -319,9 +322,15 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
                                       variant == PLAN_WINDOW_HYBRID;
     if (use_window && !window_ok)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_run: too many angles for the windowed kernel");
-    if (rt == PILA_U8 && !use_window)
+    if (rt == PILA_U8 && !use_window) {
+        // one-byte tables past 128 angles: the windowed move on 2 or 4 warps
+        // per chain (unless the caller asked for a pipelined layout)
+        const bool by_size = variant == PLAN_RULES && prm->group_warps <= 1 && prm->pipeline_depth == 0;
+        if (by_size && records_per_lane(2) <= 4) return choose_plan(p, n_chains, window, prm, PLAN_WINDOW_G2, pl);
+        if (by_size && records_per_lane(4) <= 4) return choose_plan(p, n_chains, window, prm, PLAN_WINDOW_G4, pl);
         return fail(SATPILA_ERR_INVALID_ARG,
-                    "sat_run: one-byte tables are read by the windowed kernel only (at most 128 angles)");
+                    "sat_run: one-byte tables are read by the windowed kernels only (at most 512 angles)");
+    }
     if (use_window) {
         const int residency = variant == PLAN_WINDOW_SMEM     ? SAT_RESIDENT_SMEM
                               : variant == PLAN_WINDOW_GLOBAL ? SAT_RESIDENT_GLOBAL
@@ -623,8 +632,11 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.claim = pl.kind == 2 ? b.claim : nullptr;
     sa.sweep_begin = s_begin;
     sa.sweep_end = s_end;
-    sa.sweeps_per_task = pl.spt;
-    sa.n_tasks = n_chains * ((s_end - s_begin + pl.spt - 1) / pl.spt);
+    sa.wait_ns = (unsigned long long)(prm->wait_ms > 0 ? prm->wait_ms : 20000) * 1000000ull;
+    sa.stall_chain = (prm->flags & SAT_FLAG_TEST_STALL) ? 0 : -1;
+    const int spt = sa.stall_chain >= 0 ? 1 : pl.spt;  // the stall needs a second task of chain 0
+    sa.sweeps_per_task = spt;
+    sa.n_tasks = n_chains * ((s_end - s_begin + spt - 1) / spt);
     sa.task_counter = task_counter;
     return launch_sweep(p->precision, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid,
                         pl.warps, pl.sweep_smem_bytes(), q);
@@ -731,6 +743,48 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, int>> g_tuned;
 
+// The autotuner's picks kept across processes: with SATPILA_TUNE_CACHE set,
+// one line per pick, "<device name>|n U B precision n_mask K log2(chains) M plan".
+std::string tune_line_key(const TuneKey& k) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, k.device) != cudaSuccess) {
+        cudaGetLastError();
+        prop.name[0] = 0;
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|%d %d %d %d %d %d %d %d", prop.name, k.n, k.U, k.B, k.precision, k.n_mask, k.K,
+                  k.chains_log2, k.M);
+    return buf;
+}
+
+int tune_cache_lookup(const TuneKey& k) {
+    const char* path = std::getenv("SATPILA_TUNE_CACHE");
+    if (!path || !*path) return -1;
+    std::FILE* f = std::fopen(path, "r");
+    if (!f) return -1;
+    const std::string want = tune_line_key(k);
+    char line[640];
+    int plan = -1;
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string ln(line);
+        const size_t sp = ln.find_last_of(' ');
+        if (sp == std::string::npos || ln.compare(0, sp, want) != 0 || sp != want.size()) continue;
+        const int v = std::atoi(ln.c_str() + sp + 1);
+        if (v > PLAN_RULES && v < PLAN_COUNT) plan = v;  // the last line for a key wins
+    }
+    std::fclose(f);
+    return plan;
+}
+
+void tune_cache_store(const TuneKey& k, int plan) {
+    const char* path = std::getenv("SATPILA_TUNE_CACHE");
+    if (!path || !*path || plan <= PLAN_RULES) return;
+    std::FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", tune_line_key(k).c_str(), plan);
+    std::fclose(f);
+}
+
 // Times one short sweep launch of each feasible variant on a scratch copy of
 // the caller's images (the caller's data are not touched) and returns the
 // variant with the highest moves/s.  Variants differ only in how the work is
@@ -747,6 +801,11 @@ int autotune(const satpila_pila* p, int n_chains, const float* sino, const float
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto& kv : g_tuned)
             if (kv.first == key) return kv.second;
+        const int cached = tune_cache_lookup(key);
+        if (cached > PLAN_RULES) {
+            g_tuned.push_back({key, cached});
+            return cached;
+        }
     }
     const long long P = (long long)p->n * p->n;
     int best = PLAN_RULES;
@@ -759,6 +818,7 @@ int autotune(const satpila_pila* p, int n_chains, const float* sino, const float
     sat_params tp = *prm;
     tp.trace = nullptr;
     tp.sweep_cost = nullptr;
+    tp.flags &= ~SAT_FLAG_TEST_STALL;
     tp.t0 = prm->t0 > 0.0 ? prm->t0 : 1e-3;  // a fixed temperature: the probe only times moves
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -812,6 +872,7 @@ int autotune(const satpila_pila* p, int n_chains, const float* sino, const float
     cudaFree(img);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned.push_back({key, best});
+    tune_cache_store(key, best);
     return best;
 }
 
@@ -860,7 +921,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
     if (prm->bome_k < 1 || prm->bome_k > kMaxK)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_run: bome_k must be in [1, 32]");
     if (!(prm->beta > 0.0f)) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: beta must be > 0");
-    if (prm->n_sweeps < 0 || prm->moves_per_sweep < 0 || prm->resync_every < 0)
+    if (prm->n_sweeps < 0 || prm->moves_per_sweep < 0 || prm->resync_every < 0 || prm->wait_ms < 0)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_run: negative counts");
     if (prm->schedule < SAT_SCHED_LINEAR || prm->schedule > SAT_SCHED_CUBIC)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_run: unknown schedule");
@@ -895,11 +956,18 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
     }
     const bool staged = d_sino.owned || d_img.owned || d_trace.owned || d_cost.owned;
 
-    // Launch plan, chosen by rules or by the autotuner.
+    // Launch plan: given, chosen by rules, or by the autotuner.
     int variant = PLAN_RULES;
-    if ((prm->flags & SAT_FLAG_AUTOTUNE) && !(prm->flags & SAT_FLAG_BOME_INDEPENDENT) && S_total > 0 &&
-        p->n_mask > 0)
+    if (prm->plan != PLAN_RULES) {
+        if (prm->plan < PLAN_RULES || prm->plan >= PLAN_COUNT) {
+            free_staged();
+            return fail(SATPILA_ERR_INVALID_ARG, "sat_run: unknown plan");
+        }
+        variant = prm->plan;
+    } else if ((prm->flags & SAT_FLAG_AUTOTUNE) && !(prm->flags & SAT_FLAG_BOME_INDEPENDENT) && S_total > 0 &&
+               p->n_mask > 0) {
         variant = autotune(p, n_chains, (const float*)d_sino.dev, (const float*)d_img.dev, prm, M, s);
+    }
     Plan pl;
     if ((rc = choose_plan(p, n_chains, shape.window, prm, variant, &pl)) != SATPILA_OK) {
         free_staged();

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kBomeWarps * 32) sat_bome_kernel(const SatArgs
         const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
         if (blk > 0) {
             int ok = 1;
-            if (lane == 0) ok = wait_progress(&a.progress[c], s0) ? 1 : 0;
+            if (lane == 0) ok = wait_progress(&a.progress[c], s0, a.wait_ns) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kBomeWarps * 32) sat_bome_kernel(const SatArgs
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release(&a.progress[c], s1);
+        if (lane == 0 && report_progress(a, c, s0)) st_release(&a.progress[c], s1);
     }
 }
 

@@ -88,7 +88,14 @@ struct SatArgs {
     long long trace_cap;
     const ChainCtl* ctl;         // [n_chains] or NULL
     int* claim;                  // windowed kernels: [n_chains] 1 while a warp runs the chain, or NULL
+    unsigned long long wait_ns;  // bound on a wait for a chain's earlier stages (and for a chain to claim)
+    int stall_chain;             // test hook: this chain's first task is never reported done (-1: none)
 };
+
+// True unless the task just run is the stalled chain's first (test hook).
+__device__ __forceinline__ bool report_progress(const SatArgs& a, int c, int s0) {
+    return !(c == a.stall_chain && s0 == a.sweep_begin);
+}
 
 constexpr int kSatMaxWarps = 8;
 constexpr int kMaxGroupWarps = 4;
@@ -580,12 +587,12 @@ __device__ __forceinline__ void run_stage(const SatArgs& a, const GroupShared& G
 }
 
 // Waits until another group has finished the chain's earlier stages (at
-// most 20 s of wall time).
-static __device__ __forceinline__ bool wait_progress(const int* flag, int target) {
+// most limit_ns of wall time).
+static __device__ __forceinline__ bool wait_progress(const int* flag, int target, unsigned long long limit_ns) {
     const unsigned long long t0 = global_ns();
     for (;;) {
         if (ld_acquire(flag) >= target) return true;
-        if (global_ns() - t0 > 20000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
         __nanosleep(256);
     }
 }
@@ -642,7 +649,7 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
         const int s0 = a.sweep_begin + blk * a.sweeps_per_task;
         const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
         if (blk > 0) {
-            if (gl == 0) G.flags[2] = wait_progress(&a.progress[c], s0) ? 1 : 0;
+            if (gl == 0) G.flags[2] = wait_progress(&a.progress[c], s0, a.wait_ns) ? 1 : 0;
             group_sync(gid, W);
             const int ok = G.flags[2];
             group_sync(gid, W);
@@ -713,7 +720,7 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
         }
         __threadfence();
         group_sync(gid, W);
-        if (gl == 0) st_release(&a.progress[c], s1);
+        if (gl == 0 && report_progress(a, c, s0)) st_release(&a.progress[c], s1);
     }
 }
 

@@ -410,7 +410,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
                 int all_done = 0;
                 if (lane == 0) all_done = ld_acquire(a.task_counter) >= a.n_chains ? 1 : 0;
                 if (__shfl_sync(0xffffffffu, all_done, 0)) break;
-                if (global_ns() - t_start > 20000000000ull) {
+                if (global_ns() - t_start > a.wait_ns) {
                     if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
                     break;
                 }
@@ -433,7 +433,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
             s0 = a.sweep_begin + blk * a.sweeps_per_task;
             if (blk > 0) {
                 int ok = 1;
-                if (lane == 0) ok = wait_progress(&a.progress[c], s0) ? 1 : 0;
+                if (lane == 0) ok = wait_progress(&a.progress[c], s0, a.wait_ns) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) {
                     if (lane == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
@@ -507,7 +507,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && report_progress(a, c, s0)) {  // a stalled chain also stays claimed
             st_release(&a.progress[c], s1);
             if (a.claim) {
                 if (s1 >= a.sweep_end) atomicAdd(a.task_counter, 1);  // chains finished in this launch
@@ -585,7 +585,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         const int s0 = a.sweep_begin + blk * a.sweeps_per_task;
         const int s1 = min(s0 + a.sweeps_per_task, a.sweep_end);
         if (blk > 0) {
-            if (gl == 0) G.flags[2] = wait_progress(&a.progress[c], s0) ? 1 : 0;
+            if (gl == 0) G.flags[2] = wait_progress(&a.progress[c], s0, a.wait_ns) ? 1 : 0;
             group_sync(gid, WG);
             const int ok = G.flags[2];
             group_sync(gid, WG);
@@ -627,7 +627,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         }
         __threadfence();
         group_sync(gid, WG);
-        if (gl == 0) st_release(&a.progress[c], s1);
+        if (gl == 0 && report_progress(a, c, s0)) st_release(&a.progress[c], s1);
     }
 }
 

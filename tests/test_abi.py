@@ -67,7 +67,7 @@ def test_struct_layouts_match_header():
     # sizes the C compiler gives these structs on LP64
     assert C.sizeof(_lib.SatTraceRec) == 32
     assert C.sizeof(_lib.PilaInfo) == 48
-    assert C.sizeof(_lib.SatParams) == 88
+    assert C.sizeof(_lib.SatParams) == 96
     assert C.sizeof(_lib.PilaGeom) == 32
     assert C.sizeof(_lib.SatStats) == 88
 

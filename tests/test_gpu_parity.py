@@ -576,12 +576,12 @@ def test_batched_workload_full_size_sampled_chains(api):
     imgs = dev(np.broadcast_to(img0, (C, n, n)))
     trace = torch.zeros(S * M * api.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     st = api.sat_run(p, dev(sinos[np.arange(C) % distinct]), imgs, bome_k=K, n_sweeps=S, t0=cfg["t0"],
-                     tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0, flags=api.SAT_FLAG_AUTOTUNE,
+                     tn=cfg["tn"], beta=cfg["beta"], seed=seed0, resync_every=0, plan=api.SAT_PLAN_WINDOW_SMEM,
                      trace_chain=traced, trace=trace)
     api.pila_free(p)
     assert all(s["status"] == 0 and s["proposed"] == S * M for s in st)
-    # the autotuner's choice, as in the benchmark (in practice the windowed kernel, band in shared memory)
-    assert 1 <= st[0]["plan"] <= 8
+    # the layout the benchmark pins (the autotuner's pick for this shape)
+    assert st[0]["plan"] == api.SAT_PLAN_WINDOW_SMEM
     final = imgs.cpu().numpy()
     tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
     pm = sinos[traced % distinct]
@@ -611,8 +611,9 @@ def test_batched_workload_full_size_sampled_chains(api):
 def test_precision_workload_full_size_sampled_chain(api):
     """The 512^2 workload at full size, in the launch the benchmark times: 304
     chains (2 distinct phantoms, Poisson noise at 1e5 photons), 360 angles,
-    725 bins, K = 8, T0 by Eq. (8), 200 stages of 2,058 moves, the FP16 table
-    and the autotuned layout.  A sampled chain is followed move by move (all
+    725 bins, K = 8, T0 by Eq. (8), 200 stages of 2,058 moves with a resync
+    every 20, the FP16 table and the layout the benchmark pins (the windowed
+    move on 4 warps per chain).  A sampled chain is followed move by move (all
     411,600 moves) by the oracle over the same binary16 lengths: decisions,
     Eq. (7) sums and the new pixel values, and T0."""
     cfg = synth.WORKLOADS["precision512"]
@@ -632,10 +633,12 @@ def test_precision_workload_full_size_sampled_chain(api):
     imgs = dev(np.broadcast_to(img0, (C, n, n)))
     trace = torch.zeros(S * M * api.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     st = api.sat_run(p, dev(sinos[np.arange(C) % distinct]), imgs, bome_k=K, n_sweeps=S, moves_per_sweep=M,
-                     t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, flags=api.SAT_FLAG_AUTOTUNE,
-                     trace_chain=traced, trace=trace)
+                     t0=cfg["t0"], tn=cfg["tn"], beta=cfg["beta"], seed=seed0, plan=api.SAT_PLAN_WINDOW_G4,
+                     resync_every=20, trace_chain=traced, trace=trace)
     api.pila_free(p)
     assert all(s["status"] == 0 and s["proposed"] == S * M for s in st)
+    assert st[0]["plan"] == api.SAT_PLAN_WINDOW_G4
+    assert max(s["max_resync_drift"] for s in st) <= 1e-4 * float(np.max(np.abs(sinos)))
     tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
     pm = sinos[traced % distinct]
     t0, found = oracle.sat_t0(pm, img0, seed=seed0 + traced, mask=mask, length_format=oracle.LEN_BINARY16)
@@ -781,19 +784,20 @@ def test_window_angle_limit(api, U):
     api.pila_free(p)
 
 
-@pytest.mark.parametrize("W,U,prec", [(2, 180, 0), (4, 180, 1), (4, 360, 1), (2, 90, 1)])
+@pytest.mark.parametrize("W,U,prec", [(2, 180, 0), (4, 180, 1), (4, 360, 1), (2, 90, 1), (2, 180, 2), (4, 360, 2)])
 def test_window_groups_lockstep(api, W, U, prec):
     """The windowed move on groups of 2 or 4 warps per chain (residual in
     global memory; the warps exchange window sums): move by move against the
-    oracle (the FP16 table over binary16 lengths), with 2 and 4 record slots
-    per lane, and a chain in a batch equal to its run alone."""
+    oracle (FP16 tables over binary16 lengths, one-byte tables over the
+    lengths q/180 of Sec. II-B at 180 and 360 angles), with 2 and 4 record
+    slots per lane, and a chain in a batch equal to its run alone."""
     n = 48
     B = synth.bins_for(n)
     mask = synth.disk_mask(n)
     pm = synth.gaussian_noise(oracle.drt(synth.phantom(n, 8, 1006), U, B), 0.01, 2006).astype(np.float32)
     img0 = synth.initial_image(n, 0.5, mask)
     S, M = 2, 1500
-    fmt = oracle.LEN_EXACT if prec == api.PILA_F32 else oracle.LEN_BINARY16
+    fmt = {api.PILA_F32: oracle.LEN_EXACT, api.PILA_F16: oracle.LEN_BINARY16, api.PILA_U8: oracle.LEN_BYTE180}[prec]
     p = api.pila_build(n, U, B, prec, mask=mask)
     kw = dict(bome_k=8, t0=-1.0, tn=-1.0, seed=3006, moves_per_sweep=M, group_warps=W,
               flags=api.SAT_FLAG_WINDOW_GROUPS)
@@ -886,6 +890,11 @@ def test_autotune_picks_a_layout_and_is_repeatable(api):
         assert 1 <= st[0]["plan"] <= 8
         outs.append((imgs.cpu().numpy(), [s["plan"] for s in st], [s["accepted"] for s in st]))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
+    # the pick passed back as sat_params.plan reproduces the autotuned run exactly
+    pinned = dev(img0)
+    st_p = api.sat_run(p, dev(sinos), pinned, plan=outs[0][1][0], **kw)
+    assert st_p[0]["plan"] == outs[0][1][0]
+    assert np.array_equal(pinned.cpu().numpy(), outs[0][0])
     rule = dev(img0)
     st_r = api.sat_run(p, dev(sinos), rule, **kw)
     assert 1 <= st_r[0]["plan"] <= 8  # the layout the size rules chose
