@@ -154,9 +154,10 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {
-    "sat_window_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window.cu"],
-    "sat_hybrid_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window.cu"],
-    "sat_window_group_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_group.cu"],
+    "sat_window_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_inst.cuh", "sat_window.cu"],
+    "sat_hybrid_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_inst.cuh", "sat_window.cu"],
+    "sat_window_group_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_inst.cuh",
+                                "sat_window_group.cu"],
     "sat_sweep_kernel": ["common.cuh", "sat_sweep.cuh", "sat_f16_glob.cu", "sat_f16_smem.cu", "sat_f32_glob.cu",
                          "sat_f32_smem.cu"],
 }

@@ -155,6 +155,8 @@ int pila_sirt_factor(const satpila_pila* p, double* w, void* stream);
                                  the chosen estimate's pixel.  Residual in global memory. */
 #define SAT_FLAG_WINDOW_GROUPS 16u /* with group_warps 2 or 4 (and no autotuning): the windowed
                                  move on that many warps per chain, residual in global memory */
+#define SAT_FLAG_NEAR_TIES 64u /* count near-tie decisions per chain (sat_stats.near_ties): one more
+                                 reduction per window of moves; windowed layouts only */
 #define SAT_FLAG_TEST_STALL 32u /* test hook for the timeout path: the sweep kernel never reports
                                  chain 0's first stage as done, so the task of its next stage waits
                                  until wait_ms runs out, gives up, and the call returns
@@ -210,7 +212,9 @@ typedef struct {
                                  the device's global timer read just before and after it (graphs) */
     int32_t plan;             /* SAT_PLAN_* layout the launches used (SAT_PLAN_RULES: the
                                  independent-pixel BoME kernel) */
-    int32_t pad;
+    int32_t near_ties;        /* with SAT_FLAG_NEAR_TIES and a windowed layout: decisions whose
+                                 margin (BoME gap, or Step 4's C' - C against T(-ln N1) or 0) was
+                                 within 2e-5 of the scale of their FP32 terms; else -1 */
 } sat_stats;
 
 /* Launch layouts (sat_stats.plan).  They differ in how chains map onto the

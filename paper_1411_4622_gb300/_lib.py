@@ -20,6 +20,7 @@ SAT_RESIDENT_AUTO, SAT_RESIDENT_SMEM, SAT_RESIDENT_GLOBAL = 0, 1, 2
 SAT_FLAG_NO_GRAPH, SAT_FLAG_AUTOTUNE, SAT_FLAG_HYBRID, SAT_FLAG_BOME_INDEPENDENT = 1, 2, 4, 8
 SAT_FLAG_WINDOW_GROUPS = 16
 SAT_FLAG_TEST_STALL = 32
+SAT_FLAG_NEAR_TIES = 64
 (SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
  SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4) = range(9)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
@@ -63,7 +64,7 @@ class SatStats(C.Structure):
                 ("final_cost", C.c_double), ("final_cost_incremental", C.c_double),
                 ("max_resync_drift", C.c_double), ("accepted", C.c_int64), ("proposed", C.c_int64),
                 ("t0_found", C.c_int32), ("status", C.c_int32), ("sweep_ms", C.c_double),
-                ("plan", C.c_int32), ("pad", C.c_int32)]
+                ("plan", C.c_int32), ("near_ties", C.c_int32)]
 
 
 class SatServerCfg(C.Structure):

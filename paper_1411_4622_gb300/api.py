@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib as L
 from ._lib import (PILA_F16, PILA_F32, PILA_U8, SAT_FLAG_AUTOTUNE, SAT_FLAG_BOME_INDEPENDENT, SAT_FLAG_HYBRID,  # noqa: F401
-                   SAT_FLAG_NO_GRAPH, SAT_FLAG_TEST_STALL, ERR_TIMEOUT,
+                   SAT_FLAG_NO_GRAPH, SAT_FLAG_TEST_STALL, SAT_FLAG_NEAR_TIES, ERR_TIMEOUT,
                    SAT_RESIDENT_AUTO,
                    SAT_RESIDENT_GLOBAL, SAT_RESIDENT_SMEM, SAT_SCHED_CUBIC, SAT_SCHED_GEOMETRIC,
                    SAT_SCHED_LINEAR, SIRT_SEQUENTIAL, SIRT_SIMULTANEOUS, SatpilaError)

@@ -315,6 +315,7 @@ extern "C" int sat_drt_run(int32_t n, int32_t n_angles, int32_t n_bins, const ui
             st.final_cost_incremental = st.final_cost;
             st.accepted = (int64_t)acc[c];
             st.proposed = (int64_t)prm->n_sweeps * (list.empty() ? 0 : a.moves);
+            st.near_ties = -1;
             st.sweep_ms = ms;
         }
     }

@@ -36,6 +36,9 @@ SweepFn window_kernel(int rt, bool smem, int jmax, int kmax);
 SweepFn hybrid_kernel(int rt, int jmax, int kmax);
 SweepFn bome_kernel(bool f16, int jmax, int kmax);
 SweepFn window_group_kernel(int rt, int jmax, int kmax, int warps_per_chain);
+SweepFn window_kernel_nt(int rt, bool smem, int jmax, int kmax);
+SweepFn hybrid_kernel_nt(int rt, int jmax, int kmax);
+SweepFn window_group_kernel_nt(int rt, int jmax, int kmax, int warps_per_chain);
 int bome_warps_per_cta();
 
 namespace {
@@ -43,12 +46,16 @@ namespace {
 // kind: 0 pipelined, 1 windowed, 2 hybrid, 3 independent-pixel BoME, 4 and 5
 // windowed on groups of 2 and 4 warps per chain; rt: the table precision
 // (one-byte tables are read by the one-warp windowed kernel only)
-SweepFn sweep_kernel(int rt, bool smem, int jmax, int kmax, int kind = 0) {
-    if (kind == 1) return window_kernel(rt, smem, jmax, kmax);
-    if (kind == 4 || kind == 5) return smem ? nullptr : window_group_kernel(rt, jmax, kmax, kind == 4 ? 2 : 4);
+SweepFn sweep_kernel(int rt, bool smem, int jmax, int kmax, int kind = 0, bool nt = false) {
+    if (kind == 1) return nt ? window_kernel_nt(rt, smem, jmax, kmax) : window_kernel(rt, smem, jmax, kmax);
+    if (kind == 4 || kind == 5) {
+        if (smem) return nullptr;
+        const int wpc = kind == 4 ? 2 : 4;
+        return nt ? window_group_kernel_nt(rt, jmax, kmax, wpc) : window_group_kernel(rt, jmax, kmax, wpc);
+    }
     if (rt == PILA_U8) return nullptr;
     const bool f16 = rt == PILA_F16;
-    if (kind == 2) return hybrid_kernel(rt, jmax, kmax);
+    if (kind == 2) return nt ? hybrid_kernel_nt(rt, jmax, kmax) : hybrid_kernel(rt, jmax, kmax);
     if (kind == 3) return bome_kernel(f16, jmax, kmax);
     if (f16) return smem ? sweep_kernel_f16_smem(jmax, kmax) : sweep_kernel_f16_glob(jmax, kmax);
     return smem ? sweep_kernel_f32_smem(jmax, kmax) : sweep_kernel_f32_glob(jmax, kmax);
@@ -57,9 +64,9 @@ SweepFn sweep_kernel(int rt, bool smem, int jmax, int kmax, int kind = 0) {
 int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : 32; }
 
 // The kernel's shared-memory limit must have been set (prepare_launches).
-cudaError_t launch_sweep(int rt, bool smem, int kind, int jmax, int kmax, const SatArgs& a, int grid,
+cudaError_t launch_sweep(int rt, bool smem, int kind, bool nt, int jmax, int kmax, const SatArgs& a, int grid,
                          int warps, size_t smem_bytes, cudaStream_t s) {
-    SweepFn k = sweep_kernel(rt, smem, jmax, kmax, kind);
+    SweepFn k = sweep_kernel(rt, smem, jmax, kmax, kind, nt);
     if (!k) return cudaErrorInvalidValue;
     k<<<grid, warps * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
@@ -439,7 +446,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
 namespace {
 
 struct BatchLayout {
-    size_t resid, S, T0, TN, found, acc, prog, claim, err, psq, pdr, dmax, c0, cF, Sinc, rayws, bytes;
+    size_t resid, S, T0, TN, found, acc, ties, prog, claim, err, psq, pdr, dmax, c0, cF, Sinc, rayws, bytes;
 };
 
 BatchLayout batch_layout(const Plan& pl, long long cap) {
@@ -457,6 +464,7 @@ BatchLayout batch_layout(const Plan& pl, long long cap) {
     L.TN = carve(n * 8);
     L.found = carve(n * 4);
     L.acc = carve(n * 8);
+    L.ties = carve(n * 4);
     L.prog = carve(n * 4);
     L.claim = carve(n * 4);
     L.err = carve(4);
@@ -484,6 +492,7 @@ void batch_carve(void* base, const Plan& pl, long long cap, BatchDev* b) {
     b->TN = (double*)(c + L.TN);
     b->found = (int*)(c + L.found);
     b->accepted = (unsigned long long*)(c + L.acc);
+    b->ties = (unsigned*)(c + L.ties);
     b->progress = (int*)(c + L.prog);
     b->claim = (int*)(c + L.claim);
     b->error = (int*)(c + L.err);
@@ -499,9 +508,16 @@ void batch_carve(void* base, const Plan& pl, long long cap, BatchDev* b) {
 cudaError_t prepare_launches(const satpila_pila* p, const Plan& pl, int bome_k) {
     cudaError_t e = prepare_projector();
     if (e != cudaSuccess) return e;
-    SweepFn k = sweep_kernel(p->precision, pl.smem, pl.jmax, kmax_for(bome_k), pl.kind);
-    if (!k) return cudaErrorInvalidValue;
-    return allow_max_smem(k);
+    for (bool nt : {false, true}) {  // both builds of the windowed kernels: either may be launched
+        SweepFn k = sweep_kernel(p->precision, pl.smem, pl.jmax, kmax_for(bome_k), pl.kind, nt);
+        if (!k) {
+            if (nt) break;
+            return cudaErrorInvalidValue;
+        }
+        const cudaError_t e = allow_max_smem(k);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev& b, int c0, int nc, bool drift,
@@ -634,12 +650,18 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.sweep_end = s_end;
     sa.wait_ns = (unsigned long long)(prm->wait_ms > 0 ? prm->wait_ms : 20000) * 1000000ull;
     sa.stall_chain = (prm->flags & SAT_FLAG_TEST_STALL) ? 0 : -1;
+    sa.ties = b.ties;
     const int spt = sa.stall_chain >= 0 ? 1 : pl.spt;  // the stall needs a second task of chain 0
     sa.sweeps_per_task = spt;
     sa.n_tasks = n_chains * ((s_end - s_begin + spt - 1) / spt);
     sa.task_counter = task_counter;
-    return launch_sweep(p->precision, pl.smem, pl.kind, pl.jmax, kmax_for(prm->bome_k), sa, pl.grid,
-                        pl.warps, pl.sweep_smem_bytes(), q);
+    return launch_sweep(p->precision, pl.smem, pl.kind, sweep_counts_ties(pl, prm), pl.jmax, kmax_for(prm->bome_k), sa,
+                        pl.grid, pl.warps, pl.sweep_smem_bytes(), q);
+}
+
+bool sweep_counts_ties(const Plan& pl, const sat_params* prm) {
+    const bool windowed = pl.kind == 1 || pl.kind == 2 || pl.kind == 4 || pl.kind == 5;
+    return windowed && (prm->flags & SAT_FLAG_NEAR_TIES);
 }
 
 cudaError_t enqueue_copy_f64(double* dst, const double* src, int n, cudaStream_t q) {
@@ -1059,6 +1081,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
     const size_t nc = (size_t)n_chains;
     std::vector<double> T0(nc), TN(nc), c0(nc), cF(nc), Sinc(nc), dmax(nc);
     std::vector<int> found(nc);
+    std::vector<unsigned> ties(nc, 0u);
     std::vector<unsigned long long> acc(nc);
     int err_code = 0;
     if (e == cudaSuccess && stats) {
@@ -1068,7 +1091,8 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             size_t bytes;
         } cps[] = {{T0.data(), b.T0, nc * 8},       {TN.data(), b.TN, nc * 8},       {c0.data(), b.cost0, nc * 8},
                    {cF.data(), b.costF, nc * 8},    {Sinc.data(), b.S_inc, nc * 8},  {dmax.data(), b.drift_max, nc * 8},
-                   {found.data(), b.found, nc * 4}, {acc.data(), b.accepted, nc * 8}};
+                   {found.data(), b.found, nc * 4}, {acc.data(), b.accepted, nc * 8},
+                   {ties.data(), b.ties, nc * 4}};
         for (auto& c : cps)
             if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, s);
     }
@@ -1130,6 +1154,7 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             st.status = err_code;
             st.sweep_ms = sweep_ms;
             st.plan = variant != PLAN_RULES ? variant : plan_code(pl);
+            st.near_ties = sweep_counts_ties(pl, prm) ? (int32_t)std::min<unsigned>(ties[c], 0x7fffffffu) : -1;
         }
     }
     if (err_code != 0) return fail(err_code, "sat_run: a device-side check failed");

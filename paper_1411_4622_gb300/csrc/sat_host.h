@@ -62,6 +62,7 @@ struct BatchDev {
     double* TN = nullptr;
     int* found = nullptr;          // uphill samples found by Eq. (8)
     unsigned long long* accepted = nullptr;
+    unsigned* ties = nullptr;      // near-tie decisions (windowed layouts with SAT_FLAG_NEAR_TIES)
     int* progress = nullptr;       // per chain: stages done in the current sweep launch
     int* claim = nullptr;          // per chain: 1 while a warp runs it (ready-first scheduling)
     int* error = nullptr;          // [1]
@@ -100,6 +101,8 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
                           int n_chains, int M, int s_total, int s_begin, int s_end, int* task_counter,
                           cudaStream_t q);
 cudaError_t enqueue_copy_f64(double* dst, const double* src, int n, cudaStream_t q);
+// True when the sweep launches of this plan count near-tie decisions.
+bool sweep_counts_ties(const Plan& pl, const sat_params* prm);
 
 // Drops cached graphs and plans that refer to p (called by pila_free).
 void sat_cache_purge(const satpila_pila* p);

@@ -89,6 +89,7 @@ struct SatArgs {
     const ChainCtl* ctl;         // [n_chains] or NULL
     int* claim;                  // windowed kernels: [n_chains] 1 while a warp runs the chain, or NULL
     unsigned long long wait_ns;  // bound on a wait for a chain's earlier stages (and for a chain to claim)
+    unsigned* ties;              // [n_chains] near-tie decisions (windowed kernels built to count them)
     int stall_chain;             // test hook: this chain's first task is never reported done (-1: none)
 };
 
@@ -104,7 +105,10 @@ constexpr int kDrawRing = 3 * kBatch;  // the batch in use, the next one, and on
 constexpr int kDrawRingBytes = kDrawRing * (4 * ((kMaxK + 2 + 3) / 4) + 1) * 4;
 // Shared memory of a chain group: header, one draw ring per warp, then the
 // PILA-row stages and (when resident) the residual.
-constexpr int kGroupHeader = 256;
+constexpr int kPartSlots = 8;   // window sums a warp of a group publishes per window (windowed kernel)
+constexpr int kPartOffset = 64;  // GroupShared::part: [2][kMaxGroupWarps][kPartSlots] floats
+constexpr int kFlagsOffset = kPartOffset + 2 * kMaxGroupWarps * kPartSlots * 4;  // GroupShared::flags: 8 ints
+constexpr int kGroupHeader = kFlagsOffset + 64;
 __host__ __device__ constexpr int group_ring_bytes(int W) { return kGroupHeader + W * kDrawRingBytes; }
 
 __device__ __forceinline__ double stage_temperature(int schedule, double t0, double tn, int s, int n_sweeps) {
@@ -194,7 +198,8 @@ __device__ __forceinline__ void rt_decode_stage(const unsigned char* stage, int 
 
 struct GroupShared {
     uint64_t* bar;         // one barrier: the residual's bulk copy at task start
-    float* part;           // [2][kMaxGroupWarps][4] partial (Gs, OV) per move parity
+    float* part;           // partial window sums per parity (pipelined: [2][kMaxGroupWarps][4]; windowed:
+                           // [2][kMaxGroupWarps][kPartSlots])
     volatile int* flags;   // [0] task, [2] progress-wait result
     uint32_t* draws;       // this warp's ring [kDrawRing][4 * blocks]: raw Philox words
     int* pix;              // this warp's ring [kDrawRing]: pixel of each move
@@ -608,8 +613,8 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
                                                int lane) {
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
-    G.part = reinterpret_cast<float*>(gb + 64);  // 2 * 4 * 4 floats
-    G.flags = reinterpret_cast<volatile int*>(gb + 192);
+    G.part = reinterpret_cast<float*>(gb + kPartOffset);  // the pipelined kernel uses 2 * 4 * 4 of its floats
+    G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
     G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * kDrawRingBytes);
     G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * kDrawRingBytes + kDrawRing * 4);
     G.stages = gb + group_ring_bytes(W);

@@ -33,10 +33,17 @@ __device__ __forceinline__ void cell_share(int ki, float a0, float a1, int kj, f
     s1 = d == 0 ? a1 : (d == -1 ? a0 : 0.0f);
 }
 
-template <int RT, bool SMEM, int JMAX, int KMAX, int WG = 1>
+// Near-ties (with SAT_FLAG_NEAR_TIES): a decision whose margin is within the
+// FP32 rounding of its own terms - the BoME gap between the best two
+// estimates, or Step 4's ΔC against T(-ln N1) or against 0, below 2e-5 of the
+// term scale 2|df| sum|r l| + df^2 sum l^2 (the FP64 comparison's tolerance) -
+// where an FP64 evaluation could decide otherwise.
+constexpr float kTieTol = 2e-5f;
+
+template <int RT, bool SMEM, int JMAX, int KMAX, int WG = 1, bool NT = false>
 __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupShared& G, const StageCtx& x,
                                                  float& S_hi, float& S_lo, unsigned long long& n_acc,
-                                                 const int (&rowbase)[JMAX]) {
+                                                 unsigned& n_ties, const int (&rowbase)[JMAX]) {
     constexpr int kWords = draw_words<KMAX>();
     const int M = x.M;
     if (M <= 0 || a.n_list <= 0) return;
@@ -107,7 +114,8 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         int k[kWin][JMAX];
         float l0[kWin][JMAX], l1[kWin][JMAX], v0[kWin][JMAX], v1[kWin][JMAX];
         float sh0[kPairs][JMAX], sh1[kPairs][JMAX];  // cell_share of each pair (i < j)
-        float red[kWin + kPairs];
+        constexpr int kRed = NT ? kWin + kPairs + kWin : kWin + kPairs;
+        float red[kRed];                             // Gs_j, OV_ij, and (near-ties) sum |r l_j|
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
             Recs<JMAX> r;
@@ -154,27 +162,36 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                     ++e;
                 }
         }
+        if constexpr (NT) {
+#pragma unroll
+            for (int j = 0; j < kWin; ++j) {
+                float s = 0.0f;
+#pragma unroll
+                for (int q = 0; q < JMAX; ++q) s = fmaf(fabsf(v0[j][q]), l0[j][q], fmaf(fabsf(v1[j][q]), l1[j][q], s));
+                red[kWin + kPairs + j] = s;
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int e = 0; e < kWin + kPairs; ++e) red[e] += __shfl_xor_sync(0xffffffffu, red[e], o);
+            for (int e = 0; e < kRed; ++e) red[e] += __shfl_xor_sync(0xffffffffu, red[e], o);
         if constexpr (WG > 1) {
             // each warp holds the sums over its own angles: add the warps'
             // sums in warp order (the same order in every warp).  Slots
             // alternate with the window parity; a warp can be at most one
             // window ahead of the others, so a slot is never overwritten
             // while another warp still reads it.
-            float* xr = G.part + (w & 1) * (4 * kMaxGroupWarps);
+            float* xr = G.part + (w & 1) * (kPartSlots * kMaxGroupWarps);
             float mine = 0.0f;
 #pragma unroll
-            for (int e = 0; e < kWin + kPairs; ++e) mine = x.lane == e ? red[e] : mine;
-            if (x.lane < kWin + kPairs) xr[4 * x.wig + x.lane] = mine;
+            for (int e = 0; e < kRed; ++e) mine = x.lane == e ? red[e] : mine;
+            if (x.lane < kRed) xr[kPartSlots * x.wig + x.lane] = mine;
             group_sync(x.gid, WG);
 #pragma unroll
-            for (int e = 0; e < kWin + kPairs; ++e) {
+            for (int e = 0; e < kRed; ++e) {
                 float t = xr[e];
 #pragma unroll
-                for (int q = 1; q < WG; ++q) t += xr[4 * q + e];
+                for (int q = 1; q < WG; ++q) t += xr[kPartSlots * q + e];
                 red[e] = t;
             }
         }
@@ -267,6 +284,25 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             const float xs = dS[0] * a.inv_BU;
             const float xm = xs - TL2;
             const bool accept = live && (xs <= 0.0f || xm < 0.0f || xm * xm < rhs);
+            if constexpr (NT) if (live) {
+                // margins of this decision against the scale of its terms
+                const float dfc = fcand[0] - f;
+                const float scale = fmaf(2.0f * fabsf(dfc), red[NT ? kWin + kPairs + j : 0], dfc * dfc * hc[j]);
+                float second = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int e = 0; e < KMAX; ++e)
+                    if (e < a.K && e != ci[0]) {
+                        const float d = dd[e];
+                        second = fminf(second, d * fmaf(d, hc[j], g2));
+                    }
+                const bool bome_tie = second - dS[0] <= kTieTol * scale;
+                const float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
+                const float den = sqrtf(fmaxf(0.0f, fmaf(C, C, xs))) + C;
+                const float dC = den > 0.0f ? xs / den : 0.0f;
+                const float tol_C = den > 0.0f ? kTieTol * scale * a.inv_BU / den : 0.0f;
+                const bool step4_tie = fabsf(dC) <= tol_C || (x.T > 0.0f && fabsf(dC - TL) <= tol_C);
+                n_ties += (bome_tie || step4_tie) ? 1u : 0u;
+            }
             df[j] = accept ? fcand[0] - f : 0.0f;
             fnew[j] = accept ? fcand[0] : f;
             if (x.tracing && live && x.gl == 0) {
@@ -335,12 +371,12 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 
 // Task loop of one warp with its residual in shared memory (gb, window_bytes
 // of shared memory; barrier id 1 + warp).
-template <int RT, bool SMEM, int JMAX, int KMAX>
+template <int RT, bool SMEM, int JMAX, int KMAX, bool NT>
 __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb, int warp, int lane) {
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
-    G.part = reinterpret_cast<float*>(gb + 64);
-    G.flags = reinterpret_cast<volatile int*>(gb + 192);
+    G.part = reinterpret_cast<float*>(gb + kPartOffset);
+    G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
     G.pix = reinterpret_cast<int*>(gb + kGroupHeader);
     G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + kDrawRing * 4);
     G.stages = gb + group_ring_bytes(1);
@@ -469,6 +505,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         float S_hi = (float)S;
         float S_lo = -(float)(S - (double)S_hi);
         unsigned long long n_acc = 0;
+        unsigned n_ties = 0;
         StageCtx x;
         x.M = a.moves;
         x.D = a.D;
@@ -488,7 +525,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
             x.s = s_base + s;
             x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<RT, SMEM, JMAX, KMAX>(a, G, x, S_hi, S_lo, n_acc, rowbase);
+            run_stage_window<RT, SMEM, JMAX, KMAX, 1, NT>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
             if (a.sweep_cost && lane == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
         }
@@ -504,6 +541,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         if (lane == 0) {
             a.S[c] = (double)S_hi - (double)S_lo;
             a.accepted[c] += n_acc;
+            if (NT) a.ties[c] += n_ties;
         }
         __threadfence();
         __syncwarp();
@@ -517,11 +555,11 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     }
 }
 
-template <int RT, bool SMEM, int JMAX, int KMAX>
+template <int RT, bool SMEM, int JMAX, int KMAX, bool NT>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    window_warp<RT, SMEM, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
+    window_warp<RT, SMEM, JMAX, KMAX, NT>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
 }
 
 // Both kinds of warp in one CTA, pulling from the same task queue: the first
@@ -529,17 +567,17 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_kernel(const Sat
 // work on it in global memory.  Both run the same windowed arithmetic, so a
 // chain's result does not depend on which warps ran its stages; faster warps
 // simply take more tasks.
-template <int RT, int JMAX, int KMAX>
+template <int RT, int JMAX, int KMAX, bool NT>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ns = a.hybrid_smem_warps;
     if (warp < ns) {
-        window_warp<RT, true, JMAX, KMAX>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
+        window_warp<RT, true, JMAX, KMAX, NT>(a, smem + (size_t)warp * a.group_smem_bytes, warp, lane);
     } else {
         const int g = warp - ns;
-        window_warp<RT, false, JMAX, KMAX>(a, smem + (size_t)ns * a.group_smem_bytes + (size_t)g * a.hybrid_glob_bytes,
-                                            warp, lane);
+        window_warp<RT, false, JMAX, KMAX, NT>(
+            a, smem + (size_t)ns * a.group_smem_bytes + (size_t)g * a.hybrid_glob_bytes, warp, lane);
     }
 }
 
@@ -548,12 +586,12 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const Sat
 // memory.  Every warp takes every decision itself (the same sums, draws and
 // pixel values) and writes the same pixel values, so the warps exchange
 // only the window sums; the residual cells of an angle belong to one lane.
-template <int RT, int JMAX, int KMAX, int WG>
+template <int RT, int JMAX, int KMAX, int WG, bool NT>
 __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb, int grp, int wig, int lane) {
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
-    G.part = reinterpret_cast<float*>(gb + 64);
-    G.flags = reinterpret_cast<volatile int*>(gb + 192);
+    G.part = reinterpret_cast<float*>(gb + kPartOffset);
+    G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
     G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * kDrawRingBytes);
     G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * kDrawRingBytes + kDrawRing * 4);
     G.stages = gb + group_ring_bytes(WG);
@@ -598,6 +636,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         float S_hi = (float)S;
         float S_lo = -(float)(S - (double)S_hi);
         unsigned long long n_acc = 0;
+        unsigned n_ties = 0;
         StageCtx x;
         x.M = a.moves;
         x.D = a.D;
@@ -617,13 +656,14 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
             x.s = s_base + s;
             x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<RT, false, JMAX, KMAX, WG>(a, G, x, S_hi, S_lo, n_acc, rowbase);
+            run_stage_window<RT, false, JMAX, KMAX, WG, NT>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
             if (a.sweep_cost && gl == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
         }
         if (gl == 0) {
             a.S[c] = (double)S_hi - (double)S_lo;
             a.accepted[c] += n_acc;
+            if (NT) a.ties[c] += n_ties;
         }
         __threadfence();
         group_sync(gid, WG);
@@ -631,12 +671,12 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
     }
 }
 
-template <int RT, int JMAX, int KMAX, int WG>
+template <int RT, int JMAX, int KMAX, int WG, bool NT>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_group_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = warp / WG;
-    window_group<RT, JMAX, KMAX, WG>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG, lane);
+    window_group<RT, JMAX, KMAX, WG, NT>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG, lane);
 }
 
 }  // namespace satpila

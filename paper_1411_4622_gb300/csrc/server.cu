@@ -599,7 +599,8 @@ cudaError_t satpila_server::finish_tick(Class* c) {
             s.t0_found = reinterpret_cast<const int*>(sc + (size_t)7 * cap)[i];
             s.status = err_code;
             s.sweep_ms = c->tick_ms;
-            s.plan = 0;
+            s.plan = plan_code(c->pl);
+            s.near_ties = -1;
             d.res.submit_ms = sl.t_submit;
             d.res.admit_ms = sl.t_admit;
             d.res.done_ms = t;
