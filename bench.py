@@ -38,7 +38,9 @@ PLAN_NAMES = {0: "independent-pixel BoME kernel", 1: "windowed, band residual in
               2: "windowed, residual in global memory", 3: "windowed hybrid",
               4: "pipelined, 1 warp per chain", 5: "pipelined, 2 warps per chain",
               6: "pipelined, 4 warps per chain", 7: "windowed, 2 warps per chain, residual in global memory",
-              8: "windowed, 4 warps per chain, residual in global memory"}
+              8: "windowed, 4 warps per chain, residual in global memory",
+              9: "windowed, 2 warps per chain, residual band in shared memory",
+              10: "windowed, 4 warps per chain, residual band in shared memory"}
 METRIC = "SAT pixel-moves/s at equal final RMSE (batched vs plain); slice p50/p99 ms"
 UNIT = "pixel-moves/s"
 
@@ -157,7 +159,7 @@ KERNEL_SOURCES = {
     "sat_window_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_inst.cuh", "sat_window.cu"],
     "sat_hybrid_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_inst.cuh", "sat_window.cu"],
     "sat_window_group_kernel": ["common.cuh", "sat_sweep.cuh", "sat_window.cuh", "sat_window_inst.cuh",
-                                "sat_window_group.cu"],
+                                "sat_window_group.cu", "sat_window_gsmem.cu"],
     "sat_sweep_kernel": ["common.cuh", "sat_sweep.cuh", "sat_f16_glob.cu", "sat_f16_smem.cu", "sat_f32_glob.cu",
                          "sat_f32_smem.cu"],
 }
@@ -173,7 +175,7 @@ def launch_name(plan, flags, pinned=0):
 # the sweep kernel each launch layout (sat_stats.plan) runs
 PLAN_KERNEL = {1: "sat_window_kernel", 2: "sat_window_kernel", 3: "sat_hybrid_kernel", 4: "sat_sweep_kernel",
                5: "sat_sweep_kernel", 6: "sat_sweep_kernel", 7: "sat_window_group_kernel",
-               8: "sat_window_group_kernel"}
+               8: "sat_window_group_kernel", 9: "sat_window_group_kernel", 10: "sat_window_group_kernel"}
 
 
 def kernel_source_hash(kernel):
@@ -1212,7 +1214,7 @@ def main():
     resid_bytes = 4 * E * (1 + acc)
     img_bytes = 4 * (1 + acc)
     kernel = PLAN_KERNEL.get(st[0]["plan"], "sat_window_kernel")
-    smem_resid = st[0]["plan"] in (1, 3)
+    smem_resid = st[0]["plan"] in (1, 3, 9, 10)
     table_in_l2 = info["table_bytes"] < 64e6
     levels = {
         "table_rows": {"level": "l2" if table_in_l2 else "hbm", "bytes_per_move": row_bytes,

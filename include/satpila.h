@@ -192,7 +192,7 @@ typedef struct {
     int32_t pipeline_depth;  /* PILA rows in flight per chain, 3..8; 0: default (4) */
     sat_trace_rec* trace;    /* n_sweeps*M records for trace_chain (host or device), or NULL */
     double* sweep_cost;      /* [n_chains][n_sweeps] cost after each sweep (host or device), or NULL */
-    int32_t plan;            /* SAT_PLAN_* launch layout to use (1..8; INVALID_ARG if it does not fit);
+    int32_t plan;            /* SAT_PLAN_* launch layout to use (1..10; INVALID_ARG if it does not fit);
                                 0: size rules, or the autotuner with SAT_FLAG_AUTOTUNE */
     int32_t wait_ms;         /* bound on every device-side wait of a chain for its earlier stages
                                 (ms); 0: 20000 */
@@ -230,6 +230,8 @@ typedef struct {
 #define SAT_PLAN_PIPE_4 6        /* pipelined, 4 warps per chain */
 #define SAT_PLAN_WINDOW_G2 7     /* windowed, 2 warps per chain, residual in global memory */
 #define SAT_PLAN_WINDOW_G4 8     /* windowed, 4 warps per chain, residual in global memory */
+#define SAT_PLAN_WINDOW_SMEM_G2 9  /* windowed, 2 warps per chain, residual band in shared memory */
+#define SAT_PLAN_WINDOW_SMEM_G4 10 /* windowed, 4 warps per chain, residual band in shared memory */
 
 /*
  * Anneal n_chains independent slices that share one PILA.  Chain c reads its

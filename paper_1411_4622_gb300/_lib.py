@@ -22,7 +22,8 @@ SAT_FLAG_WINDOW_GROUPS = 16
 SAT_FLAG_TEST_STALL = 32
 SAT_FLAG_NEAR_TIES = 64
 (SAT_PLAN_RULES, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_GLOBAL, SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_PIPE_1,
- SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4) = range(9)
+ SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4, SAT_PLAN_WINDOW_SMEM_G2,
+ SAT_PLAN_WINDOW_SMEM_G4) = range(11)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 PROBE_STREAM, PROBE_SECTOR = 0, 1
 

@@ -20,7 +20,7 @@ from ._lib import (PILA_F16, PILA_F32, PILA_U8, SAT_FLAG_AUTOTUNE, SAT_FLAG_BOME
 from ._lib import ERR_BUSY, ERR_INVALID_ARG, ERR_NOT_FOUND, ERR_PENDING  # noqa: F401
 from ._lib import (SAT_FLAG_WINDOW_GROUPS, SAT_PLAN_PIPE_1, SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4,  # noqa: F401
                    SAT_PLAN_RULES, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4, SAT_PLAN_WINDOW_GLOBAL,
-                   SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_WINDOW_SMEM)
+                   SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_SMEM_G2, SAT_PLAN_WINDOW_SMEM_G4)
 from ._lib import PROBE_SECTOR, PROBE_STREAM  # noqa: F401
 
 TRACE_DTYPE = np.dtype([("pixel", "<i4"), ("cstar", "<i4"), ("accepted", "<i4"), ("pad", "<i4"),

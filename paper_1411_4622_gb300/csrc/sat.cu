@@ -39,6 +39,8 @@ SweepFn window_group_kernel(int rt, int jmax, int kmax, int warps_per_chain);
 SweepFn window_kernel_nt(int rt, bool smem, int jmax, int kmax);
 SweepFn hybrid_kernel_nt(int rt, int jmax, int kmax);
 SweepFn window_group_kernel_nt(int rt, int jmax, int kmax, int warps_per_chain);
+SweepFn window_group_smem_kernel(int rt, int jmax, int kmax, int warps_per_chain);
+SweepFn window_group_smem_kernel_nt(int rt, int jmax, int kmax, int warps_per_chain);
 int bome_warps_per_cta();
 
 namespace {
@@ -49,8 +51,9 @@ namespace {
 SweepFn sweep_kernel(int rt, bool smem, int jmax, int kmax, int kind = 0, bool nt = false) {
     if (kind == 1) return nt ? window_kernel_nt(rt, smem, jmax, kmax) : window_kernel(rt, smem, jmax, kmax);
     if (kind == 4 || kind == 5) {
-        if (smem) return nullptr;
         const int wpc = kind == 4 ? 2 : 4;
+        if (smem)
+            return nt ? window_group_smem_kernel_nt(rt, jmax, kmax, wpc) : window_group_smem_kernel(rt, jmax, kmax, wpc);
         return nt ? window_group_kernel_nt(rt, jmax, kmax, wpc) : window_group_kernel(rt, jmax, kmax, wpc);
     }
     if (rt == PILA_U8) return nullptr;
@@ -208,8 +211,8 @@ int plan_code(const Plan& pl) {
         case 1: return pl.smem ? PLAN_WINDOW_SMEM : PLAN_WINDOW_GLOBAL;
         case 2: return PLAN_WINDOW_HYBRID;
         case 0: return pl.W == 1 ? PLAN_PIPE_1 : pl.W == 2 ? PLAN_PIPE_2 : PLAN_PIPE_4;
-        case 4: return PLAN_WINDOW_G2;
-        case 5: return PLAN_WINDOW_G4;
+        case 4: return pl.smem ? PLAN_WINDOW_SMEM_G2 : PLAN_WINDOW_G2;
+        case 5: return pl.smem ? PLAN_WINDOW_SMEM_G4 : PLAN_WINDOW_G4;
         default: return PLAN_RULES;  // the independent-pixel BoME kernel
     }
 }
@@ -289,6 +292,40 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
         return SATPILA_OK;
     }
     // The windowed kernel on groups of 2 or 4 warps per chain (their lanes
+    // split the angles) with the residual band in shared memory: the chain's
+    // per-move record work split over warps on different schedulers.
+    if (variant == PLAN_WINDOW_SMEM_G2 || variant == PLAN_WINDOW_SMEM_G4) {
+        const int Wg = variant == PLAN_WINDOW_SMEM_G2 ? 2 : 4;
+        if (rt == PILA_U8 || prm->residency == SAT_RESIDENT_GLOBAL || records_per_lane(Wg) > 4)
+            return fail(SATPILA_ERR_INVALID_ARG, "sat_run: no windowed shared-memory group launch for this table");
+        const int jw = records_per_lane(Wg) <= 2 ? 2 : 4;
+        const int stage = 512 * Wg * (jw / rpc);
+        const long long band_floats = (long long)p->U * pl->band_pitch + 64LL * Wg;  // then 2 dummy cells per lane
+        const size_t gsm =
+            align_up(group_ring_bytes(Wg, kmax_for(prm->bome_k)) + (size_t)2 * kWin * stage + (size_t)band_floats * 4, 128);
+        const int kmax = kmax_for(prm->bome_k);
+        const int groups = std::min(kSatMaxWarps / Wg, std::min(std::max(1, n_chains), (int)(maxopt / gsm)));
+        if (groups < 1) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: residual band does not fit in shared memory");
+        pl->band_floats = band_floats;
+        pl->kind = Wg == 2 ? 4 : 5;
+        pl->smem = true;
+        pl->W = Wg;
+        pl->J = pl->jmax = jw;
+        pl->D = 4;
+        pl->stage_bytes = stage;
+        pl->group_smem = (int)gsm;
+        pl->groups = groups;
+        pl->warps = groups * Wg;
+        int per_sm = sweep_blocks_per_sm(rt, true, pl->kind, jw, kmax, pl->warps, (size_t)groups * gsm);
+        if (per_sm < 1) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: windowed shared-memory group launch does not fit");
+        const long long slots = (long long)sms * per_sm * groups;
+        pl->spt = n_chains <= slots ? window : 1;
+        const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
+        const long long want = (std::min<long long>(tasks, slots) + groups - 1) / groups;
+        pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
+        return SATPILA_OK;
+    }
+    // The windowed kernel on groups of 2 or 4 warps per chain (their lanes
     // split the angles), residual in global memory: one gather round trip and
     // one exchange of sums between the warps per window of moves.  (The size
     // rules keep the pipelined kernel for wide tables: with it the serving
@@ -299,7 +336,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
             return fail(SATPILA_ERR_INVALID_ARG, "sat_run: no windowed group launch for this table");
         const int jw = records_per_lane(Wg) <= 2 ? 2 : 4;
         const int stage = 512 * Wg * (jw / rpc);
-        const size_t glob = align_up(group_ring_bytes(Wg) + (size_t)2 * kWin * stage, 128);
+        const size_t glob = align_up(group_ring_bytes(Wg, kmax_for(prm->bome_k)) + (size_t)2 * kWin * stage, 128);
         const int kmax = kmax_for(prm->bome_k);
         const int groups = std::max(1, std::min(kSatMaxWarps / Wg, std::min(n_chains, (int)(maxopt / glob))));
         pl->kind = Wg == 2 ? 4 : 5;
@@ -346,7 +383,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
                                                    (variant == PLAN_RULES && (prm->flags & SAT_FLAG_HYBRID)));
         const int jw = records_per_lane(1) <= 2 ? 2 : 4;
         const int stage = 512 * (jw / rpc);
-        const size_t ring1 = group_ring_bytes(1) + (size_t)2 * kWin * stage;
+        const size_t ring1 = group_ring_bytes(1, kmax_for(prm->bome_k)) + (size_t)2 * kWin * stage;
         const size_t gsm = align_up(ring1 + (size_t)pl->band_floats * 4, 128);  // shared-memory warp
         const size_t glob = align_up(ring1, 128);                                   // global-memory warp
         const int kmax = kmax_for(prm->bome_k);
@@ -411,7 +448,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->D = prm->pipeline_depth > 0 ? prm->pipeline_depth : 4;
     if (pl->D < 3 || pl->D > kMaxStages) return fail(SATPILA_ERR_INVALID_ARG, "sat_run: pipeline_depth must be in [3, 8]");
     pl->stage_bytes = 512 * W * (jmax / rpc);  // 16-byte chunks of all lanes
-    const size_t ring = group_ring_bytes(W) + (size_t)pl->D * pl->stage_bytes;
+    const size_t ring = group_ring_bytes(W, kmax_for(prm->bome_k)) + (size_t)pl->D * pl->stage_bytes;
     const size_t smem_group = align_up(ring + (size_t)pl->resid_floats * 4, 128);
     const size_t glob_group = align_up(ring, 128);
     bool smem = false;

@@ -22,12 +22,15 @@ enum PlanVariant {
     PLAN_PIPE_4,
     PLAN_WINDOW_G2,  // windowed, 2 or 4 warps per chain, residual in global memory
     PLAN_WINDOW_G4,
+    PLAN_WINDOW_SMEM_G2,  // windowed, 2 or 4 warps per chain, residual band in shared memory
+    PLAN_WINDOW_SMEM_G4,
     PLAN_COUNT
 };
 
 struct Plan {
     bool smem = false;
     int kind = 0;         // 0 pipelined, 1 windowed, 2 hybrid, 3 independent BoME, 4/5 windowed groups of 2/4 warps
+                          // (residual band in shared memory when smem)
     int hybrid_smem_warps = 0, hybrid_glob_bytes = 0;
     int jmax = 4, J = 4, D = 4;
     int W = 1, groups = 1, warps = 1, grid = 1;

@@ -102,14 +102,16 @@ constexpr int kSatMaxWarps = 8;
 constexpr int kMaxGroupWarps = 4;
 constexpr int kBatch = 8;       // moves per block of random draws
 constexpr int kDrawRing = 3 * kBatch;  // the batch in use, the next one, and one being drawn
-constexpr int kDrawRingBytes = kDrawRing * (4 * ((kMaxK + 2 + 3) / 4) + 1) * 4;
+// Bytes of one warp's draw ring for kmax estimates: the pixel of each slot,
+// then the draw words of each slot (a multiple of 16 bytes).
+__host__ __device__ constexpr int draw_ring_bytes(int kmax) { return kDrawRing * (4 * ((kmax + 2 + 3) / 4) + 1) * 4; }
 // Shared memory of a chain group: header, one draw ring per warp, then the
 // PILA-row stages and (when resident) the residual.
 constexpr int kPartSlots = 8;   // window sums a warp of a group publishes per window (windowed kernel)
 constexpr int kPartOffset = 64;  // GroupShared::part: [2][kMaxGroupWarps][kPartSlots] floats
 constexpr int kFlagsOffset = kPartOffset + 2 * kMaxGroupWarps * kPartSlots * 4;  // GroupShared::flags: 8 ints
 constexpr int kGroupHeader = kFlagsOffset + 64;
-__host__ __device__ constexpr int group_ring_bytes(int W) { return kGroupHeader + W * kDrawRingBytes; }
+__host__ __device__ constexpr int group_ring_bytes(int W, int kmax) { return kGroupHeader + W * draw_ring_bytes(kmax); }
 
 __device__ __forceinline__ double stage_temperature(int schedule, double t0, double tn, int s, int n_sweeps) {
     const double N = (double)n_sweeps, n = (double)s;
@@ -615,9 +617,9 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
     G.bar = reinterpret_cast<uint64_t*>(gb);
     G.part = reinterpret_cast<float*>(gb + kPartOffset);  // the pipelined kernel uses 2 * 4 * 4 of its floats
     G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
-    G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * kDrawRingBytes);
-    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * kDrawRingBytes + kDrawRing * 4);
-    G.stages = gb + group_ring_bytes(W);
+    G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX));
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX) + kDrawRing * 4);
+    G.stages = gb + group_ring_bytes(W, KMAX);
     float* rs = reinterpret_cast<float*>(G.stages + (size_t)a.D * a.stage_bytes);
     const int gid = 1 + grp;
     const int gl = lane + 32 * wig;  // lane index within the group

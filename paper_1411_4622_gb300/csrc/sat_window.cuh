@@ -379,7 +379,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
     G.pix = reinterpret_cast<int*>(gb + kGroupHeader);
     G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + kDrawRing * 4);
-    G.stages = gb + group_ring_bytes(1);
+    G.stages = gb + group_ring_bytes(1, KMAX);
     float* rs = reinterpret_cast<float*>(G.stages + (size_t)2 * kWin * a.stage_bytes);
 
     for (int e = lane; e < 2 * kWin * a.stage_bytes / 16; e += 32)
@@ -586,32 +586,49 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const Sat
 // memory.  Every warp takes every decision itself (the same sums, draws and
 // pixel values) and writes the same pixel values, so the warps exchange
 // only the window sums; the residual cells of an angle belong to one lane.
-template <int RT, int JMAX, int KMAX, int WG, bool NT>
+template <int RT, int JMAX, int KMAX, int WG, bool NT, bool SMEM>
 __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb, int grp, int wig, int lane) {
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
     G.part = reinterpret_cast<float*>(gb + kPartOffset);
     G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
-    G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * kDrawRingBytes);
-    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * kDrawRingBytes + kDrawRing * 4);
-    G.stages = gb + group_ring_bytes(WG);
+    G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX));
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX) + kDrawRing * 4);
+    G.stages = gb + group_ring_bytes(WG, KMAX);
+    float* rs = reinterpret_cast<float*>(G.stages + (size_t)2 * kWin * a.stage_bytes);  // SMEM: the band
     const int gl = lane + 32 * wig, gid = 1 + grp;
 
     for (int e = gl; e < 2 * kWin * a.stage_bytes / 16; e += 32 * WG)
         reinterpret_cast<uint4*>(G.stages)[e] = make_uint4(0u, 0u, 0u, 0u);
-    if (gl == 0)
+    if (gl == 0) {
         for (int i = 0; i < 8; ++i) G.flags[i] = 0;
+        if (SMEM) mbar_init(G.bar, 1);
+    }
+    if (SMEM) {
+        fence_proxy_async_smem();
+        if (gl == 0) fence_barrier_init();
+    }
     group_sync(gid, WG);
 
     // Cell (u, k) of the residual: R[rowbase + k]; group lanes past the last
-    // angle address two dummy cells of their own after the rows.
+    // angle address two dummy cells of their own after the rows.  In shared
+    // memory only the band of bins [band_lo, band_lo + band_pitch) is kept
+    // (every record of a reconstruction-space pixel addresses cells inside it),
+    // each warp of the group reading and writing the rows of its own angles.
+    const int rpitch = SMEM ? a.band_pitch : a.pitch;
+    const int rshift = SMEM ? a.band_lo : 0;
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int u = rt_record_of<RT>(gl, WG, j);
-        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * gl;
+        rowbase[j] = u < a.U ? u * rpitch - rshift : a.U * rpitch + 2 * gl;
+    }
+    if (SMEM) {
+        rs[a.U * rpitch + 2 * gl] = 0.0f;
+        rs[a.U * rpitch + 2 * gl + 1] = 0.0f;
     }
 
+    uint32_t phase = 0;
     for (;;) {
         if (gl == 0) G.flags[0] = atomicAdd(a.task_counter, 1);
         group_sync(gid, WG);
@@ -632,6 +649,33 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
                 break;
             }
         }
+        float* gres = a.resid + (long long)c * a.resid_floats;
+        if (SMEM) {
+            // The band of every residual row into shared memory, one bulk copy
+            // per row spread over the group's lanes, all completing on one
+            // barrier phase; the group leaves together if the wait runs out.
+            const uint32_t row_bytes = (uint32_t)a.band_pitch * 4u;
+            fence_proxy_async_smem();    // earlier generic accesses to the band before the async-proxy writes
+            fence_proxy_async_global();  // the chain's residual as the previous task left it
+            if (gl == 0) {
+                G.flags[3] = 1;
+                mbar_arrive_expect_tx(G.bar, row_bytes * (uint32_t)a.U);
+            }
+            group_sync(gid, WG);
+            for (int u = gl; u < a.U; u += 32 * WG)
+                bulk_copy_g2s(rs + (long long)u * a.band_pitch, gres + (long long)u * a.pitch + a.band_lo, row_bytes,
+                              G.bar);
+            const bool landed = __all_sync(0xffffffffu, mbar_wait_bounded(G.bar, phase));
+            phase ^= 1u;
+            if (!landed && lane == 0) G.flags[3] = 0;
+            group_sync(gid, WG);
+            const int ok = G.flags[3];
+            group_sync(gid, WG);
+            if (!ok) {
+                if (gl == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                break;
+            }
+        }
         const double S = a.S[c];
         float S_hi = (float)S;
         float S_lo = -(float)(S - (double)S_hi);
@@ -645,7 +689,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         x.lane = lane;
         x.gid = gid;
         x.gl = gl;
-        x.R = a.resid + (long long)c * a.resid_floats;
+        x.R = SMEM ? rs : gres;
         x.img = a.img + (long long)c * a.img_stride;
         const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
         const int s_base = cc ? cc->stage0 : 0, s_total = cc ? cc->n_sweeps : a.n_sweeps_total;
@@ -656,9 +700,18 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
             x.s = s_base + s;
             x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<RT, false, JMAX, KMAX, WG, NT>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
+            run_stage_window<RT, SMEM, JMAX, KMAX, WG, NT>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
             if (a.sweep_cost && gl == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
+        }
+        if (SMEM) {
+            group_sync(gid, WG);  // every warp's cells of the band are written
+            const int q4 = a.band_pitch / 4;
+            for (int e = gl; e < a.U * q4; e += 32 * WG) {
+                const int u = e / q4, q = e - u * q4;
+                *reinterpret_cast<float4*>(gres + (long long)u * a.pitch + a.band_lo + 4 * q) =
+                    *reinterpret_cast<const float4*>(rs + (long long)u * a.band_pitch + 4 * q);
+            }
         }
         if (gl == 0) {
             a.S[c] = (double)S_hi - (double)S_lo;
@@ -671,12 +724,12 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
     }
 }
 
-template <int RT, int JMAX, int KMAX, int WG, bool NT>
+template <int RT, int JMAX, int KMAX, int WG, bool NT, bool SMEM = false>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_group_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = warp / WG;
-    window_group<RT, JMAX, KMAX, WG, NT>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG, lane);
+    window_group<RT, JMAX, KMAX, WG, NT, SMEM>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG, lane);
 }
 
 }  // namespace satpila

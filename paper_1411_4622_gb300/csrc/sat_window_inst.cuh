@@ -78,4 +78,22 @@ SweepFn window_group_kernel_impl(int rt, int jmax, int kmax, int warps_per_chain
 #undef SAT_WGRP
 }
 
+// The windowed kernel on groups of 2 or 4 warps per chain with the residual
+// band in shared memory (FP32 and FP16 tables).
+template <bool NT>
+SweepFn window_group_smem_kernel_impl(int rt, int jmax, int kmax, int warps_per_chain) {
+#define SAT_WGS(RT, J, K, W) sat_window_group_kernel<RT, J, K, W, NT, true>
+#define SAT_WGS_K(RT, J, W) {SAT_WGS(RT, J, 4, W), SAT_WGS(RT, J, 8, W), SAT_WGS(RT, J, 32, W)}
+    const int kk = kmax_slot(kmax), jj = jmax_slot(jmax);
+    const int ww = warps_per_chain == 2 ? 0 : warps_per_chain == 4 ? 1 : -1;
+    if (kk < 0 || jj < 0 || ww < 0 || (rt != PILA_F16 && rt != PILA_F32)) return nullptr;
+    static const SweepFn t16[2][2][3] = {{SAT_WGS_K(PILA_F16, 2, 2), SAT_WGS_K(PILA_F16, 4, 2)},
+                                         {SAT_WGS_K(PILA_F16, 2, 4), SAT_WGS_K(PILA_F16, 4, 4)}};
+    static const SweepFn t32[2][2][3] = {{SAT_WGS_K(PILA_F32, 2, 2), SAT_WGS_K(PILA_F32, 4, 2)},
+                                         {SAT_WGS_K(PILA_F32, 2, 4), SAT_WGS_K(PILA_F32, 4, 4)}};
+    return rt == PILA_F16 ? t16[ww][jj][kk] : t32[ww][jj][kk];
+#undef SAT_WGS_K
+#undef SAT_WGS
+}
+
 }  // namespace satpila

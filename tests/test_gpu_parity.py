@@ -856,6 +856,38 @@ def test_window_groups_lockstep(api, W, U, prec):
     api.pila_free(p)
 
 
+@pytest.mark.parametrize("plan,n,U,prec", [(9, 128, 120, 1), (10, 128, 120, 1), (9, 64, 90, 0), (10, 96, 180, 1)])
+def test_window_smem_groups_lockstep(api, plan, n, U, prec):
+    """The windowed move on groups of 2 or 4 warps per chain with the residual
+    band in shared memory (each warp owning the rows of its angles): move by
+    move against the oracle, the same image as the one-warp windowed kernel
+    for the same chain, and batched chains equal to their runs alone."""
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    pm = synth.gaussian_noise(oracle.drt(synth.phantom(n, 8, 1010 + n), U, B), 0.01, 2010).astype(np.float32)
+    img0 = synth.initial_image(n, 0.5, mask)
+    S, M = 2, 1500
+    fmt = oracle.LEN_EXACT if prec == api.PILA_F32 else oracle.LEN_BINARY16
+    p = api.pila_build(n, U, B, prec, mask=mask)
+    kw = dict(bome_k=4, t0=-1.0, tn=-1.0, seed=3010, moves_per_sweep=M)
+    st, tr, img = _run_traced(api, p, pm, img0, S, M, plan=plan, **kw)
+    assert st["status"] == 0 and st["proposed"] == S * M and st["plan"] == plan
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=4, n_sweeps=S, seed=3010,
+                                 moves_per_sweep=M, mask=mask, length_format=fmt)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5, rep
+    # batch of 7 chains: chain 5 equals its run alone
+    kwb = {k: v for k, v in kw.items() if k != "seed"}
+    imgs = dev(np.stack([img0] * 7))
+    stb = api.sat_run(p, dev(np.stack([pm] * 7)), imgs, n_sweeps=S, seed=700, plan=plan, **kwb)
+    one = dev(img0[None])
+    st1 = api.sat_run(p, dev(pm[None]), one, n_sweeps=S, seed=705, plan=plan, **kwb)
+    assert np.array_equal(imgs.cpu().numpy()[5], one.cpu().numpy()[0])
+    assert stb[5]["accepted"] == st1[0]["accepted"]
+    api.pila_free(p)
+
+
 def test_hybrid_batch_matches_single_chains(api):
     """More chains than shared-memory slots: the batch runs on shared-memory
     and global-memory warps side by side, with chains moving between them
@@ -923,7 +955,7 @@ def test_autotune_picks_a_layout_and_is_repeatable(api):
         imgs = dev(img0)
         st = api.sat_run(p, dev(sinos), imgs, flags=api.SAT_FLAG_AUTOTUNE, **kw)
         assert all(s["status"] == 0 for s in st)
-        assert 1 <= st[0]["plan"] <= 8
+        assert 1 <= st[0]["plan"] <= 10
         outs.append((imgs.cpu().numpy(), [s["plan"] for s in st], [s["accepted"] for s in st]))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
     # the pick passed back as sat_params.plan reproduces the autotuned run exactly
@@ -933,7 +965,7 @@ def test_autotune_picks_a_layout_and_is_repeatable(api):
     assert np.array_equal(pinned.cpu().numpy(), outs[0][0])
     rule = dev(img0)
     st_r = api.sat_run(p, dev(sinos), rule, **kw)
-    assert 1 <= st_r[0]["plan"] <= 8  # the layout the size rules chose
+    assert 1 <= st_r[0]["plan"] <= 10  # the layout the size rules chose
     r_tuned = np.mean([synth.rmse(outs[0][0][c], ph[c]) for c in range(C)])
     r_rule = np.mean([synth.rmse(rule.cpu().numpy()[c], ph[c]) for c in range(C)])
     assert abs(r_tuned - r_rule) <= 0.02 * r_rule

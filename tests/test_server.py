@@ -136,3 +136,45 @@ def test_server_busy_pending_not_found(api):
         with pytest.raises(api.SatpilaError) as ei:
             srv.submit(r["sino"], n=r["n"], bome_k=0)
         assert ei.value.code == api.ERR_INVALID_ARG
+
+
+def test_served_chain_follows_oracle(api):
+    """A request served in a mixed stream (FP16 table, Poisson noise, K = 8,
+    the FP64-grade resync every tick), followed move by move by the oracle:
+    the served image equals sat_run's on that chain with resync_every =
+    stages_per_tick (bit for bit), and that run's trace is followed by the
+    oracle over the same binary16 lengths (decisions, Eq. (7) sums, T0)."""
+    n, U, K, S = 96, 72, 8, 6
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    ph = synth.phantom(n, 12, 321) * mask
+    pm = synth.poisson_noise(oracle.drt(ph, U, B), 1e5, 654).astype(np.float32)
+    target = dict(sino=pm, n=n, precision=api.PILA_F16, mask=mask, bome_k=K, n_sweeps=S, seed=4242, t0=-1.0, tn=-1.0)
+    reqs = _requests()
+    with api.Server(stages_per_tick=TICK) as srv:
+        tickets = [srv.submit(**r) for r in reqs[:4]]
+        tt = srv.submit(**target)
+        tickets += [srv.submit(**r) for r in reqs[4:]]
+        img, st = srv.wait(tt, 120000)
+        for t in tickets:
+            assert srv.wait(t, 120000) is not None
+    assert st["status"] == 0
+    M = int(mask.sum())
+    img0 = synth.initial_image(n, 0.5, mask).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    ref = torch.tensor(img0[None], device="cuda")
+    trace = torch.zeros(S * M * api.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    s1 = api.sat_run(p, torch.tensor(pm[None], device="cuda"), ref, bome_k=K, n_sweeps=S, seed=4242, t0=-1.0,
+                     tn=-1.0, resync_every=TICK, trace_chain=0, trace=trace)
+    api.pila_free(p)
+    assert np.array_equal(ref.cpu().numpy()[0], img)
+    assert s1[0]["accepted"] == st["accepted"] and s1[0]["t0"] == st["t0"]
+    tr = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=api.TRACE_DTYPE)
+    t0, found = oracle.sat_t0(pm, img0, seed=4242, mask=mask, length_format=oracle.LEN_BINARY16)
+    assert found == st["t0_found"] == 200 and abs(st["t0"] - t0) <= 1e-4 * t0
+    _, rep = oracle.sat_lockstep(pm, img0, tr, t0=st["t0"], tn=st["tn"], bome_k=K, n_sweeps=S, seed=4242, mask=mask,
+                                 length_format=oracle.LEN_BINARY16)
+    assert rep["moves"] == S * M
+    assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
+    assert rep["max_err_dS"] <= 1e-5 and rep["max_err_f"] <= 1e-5, rep
+    assert rep["near_ties"] <= 1e-3 * S * M, rep
