@@ -498,7 +498,10 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2
         # one 32-byte sector per angle, two when a record's entries straddle a
         # sector boundary (k0 = 7 mod 8: 1/8 of the records with two entries)
         sectors = U * (1.0 + (E / U - 1.0) / 8.0)
-        sector_resid = 32.0 * sectors * (1.0 + acc) + 8.0 * (1.0 + acc)
+        # sectors read (the gather) and written back (the scatter: the same
+        # sectors, just read, written when the move is accepted)
+        sector_resid = 32.0 * sectors + 8.0
+        sector_write = (32.0 * sectors + 8.0) * acc
         useful = row_bytes + 4.0 * E * (1.0 + acc) + 4.0 * (1.0 + acc)
         # seconds of memory time per move at the probe rates: rows streamed
         # from HBM (the table is 6-12x L2), residual sectors gathered from the
@@ -517,15 +520,20 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_eff, "unit": "GB/s",
                          "frac": achieved / peak_eff, "kernel": kernel,
                          "bytes_per_move": row_bytes + sector_resid, "row_bytes": row_bytes,
-                         "sector_bytes": sector_resid, "useful_bytes_per_move": useful,
-                         "peak_rule": "rows at the HBM stream rate, residual sectors at the sector-gather rate of "
-                                      "the chains' residual footprint (one 1.05 MB region per chain)",
+                         "sector_bytes": sector_resid, "sector_write_bytes": sector_write,
+                         "useful_bytes_per_move": useful,
+                         "peak_rule": "bytes read: rows at the HBM stream rate, residual sectors at the sector-gather "
+                                      "rate of the chains' residual footprint (one 1.05 MB region per chain); the "
+                                      "scatter's write-back of the same sectors is reported beside it",
+                         "frac_with_writes": (row_bytes / pk["hbm_stream_gbs"]
+                                              + (sector_resid + sector_write) / pk["ws_sector_gbs"]) * rate / 1e9,
                          "frac_rows": row_bytes * rate / 1e9 / pk["hbm_stream_gbs"],
                          "frac_sectors": sector_resid * rate / 1e9 / pk["ws_sector_gbs"],
                          "frac_sectors_vs_hbm_probe": sector_resid * rate / 1e9 / pk["hbm_sector_gbs"],
                          "ws_sector_gbs": pk["ws_sector_gbs"],
                          "traffic": tpm * chains * stages * M if tpm is not None else None,
-                         "traffic_over_sector_bytes": tpm / (row_bytes + sector_resid) if tpm is not None else None},
+                         "traffic_over_sector_bytes": (tpm / (row_bytes + sector_resid + sector_write)
+                                                       if tpm is not None else None)},
             "clocks": clk}
     return out
 
