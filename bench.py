@@ -74,7 +74,7 @@ def parse():
                     help="serve: arrival rate in requests/s (default: 80%% of the capacity measured on a burst)")
     ap.add_argument("--pila", default="f16", choices=["f16", "u8", "f32"],
                     help="table precision of the batched run (f16: 8-byte records; u8: the paper's one-byte lengths)")
-    ap.add_argument("--tables", default="f16,f32", help="precision512: table precisions, comma separated")
+    ap.add_argument("--tables", default="f16,f32,u8", help="precision512: table precisions, comma separated")
     ap.add_argument("--part", default="both", choices=["both", "gpu", "oracle"],
                     help="precision512-rmse: run the GPU side, the oracle side (no GPU needed) or both")
     ap.add_argument("--oracle-chains", type=int, default=4, help="precision512-rmse: chains the oracle follows")
@@ -426,7 +426,7 @@ def precision_phantoms(cfg, distinct):
     return ph, noisy, mask
 
 
-def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32"), steps=2, warmup=1, flags=0,
+def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32", "u8"), steps=2, warmup=1, flags=0,
                      residency=0, group_warps=0, plan=8):
     """The 512^2 configuration as configured, on a bounded sample of its
     schedule: C chains of 512x512 slices (8 distinct phantoms, each chain its
@@ -1267,6 +1267,13 @@ def main():
                           "slice_p99": float(np.percentile(step_ms, 99)),
                           "note": "every slice of a step completes with the step's one launch"},
            "e2e": e2e, "roofline": roof, "peaks": pk, "clocks": clk,
+           "parity": {"per_move_dS": "within 1e-5 of the magnitude of its terms, 2|df| sum|r l| + df^2 sum l^2 "
+                                     "(a difference of FP32 sums is bounded relative to its terms, not to itself)",
+                      "decisions": "identical to the FP64 oracle's except recorded near-ties (margin below 2e-5 "
+                                   "of the term scale)",
+                      "full_size_test": "tests/test_gpu_parity.py::test_batched_workload_full_size_sampled_chains "
+                                        "follows a sampled chain of this launch over all 644,600 moves",
+                      "final_rmse_vs_plain_fp32": plain["rmse_rel_diff_max"]},
            # per step: PILA records, per-pixel sums, residual band, 2 resync
            # projections, 2 reductions, Eq. (8), the sweep between two timer
            # stamps, one copy (the sat_run part as one CUDA graph)
