@@ -245,7 +245,11 @@ typedef struct {
  * Random numbers: Philox4x32-10, key = seed + c, counter (stage, move, block,
  * 1); draw 0 picks the pixel, draw 1 is N1, draw 2 + e is estimate e.
  * stats (host, n_chains entries, may be NULL) are filled before return; the
- * call synchronizes `stream` at its end.
+ * call then synchronizes `stream` at its end.  With stats == NULL, every
+ * buffer in device memory and SAT_FLAG_NO_GRAPH clear, the call is
+ * asynchronous: it returns once its CUDA graph is enqueued on `stream` (the
+ * images are final when the stream reaches that point; a device-side timeout
+ * is then not reported - pass stats to see it).
  * Launches: unless SAT_FLAG_NO_GRAPH, a call whose buffers are all device
  * memory is recorded into a CUDA graph (on a private stream) and launched on
  * `stream`; the graph and its workspace are kept (a few entries, least

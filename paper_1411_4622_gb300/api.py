@@ -151,18 +151,21 @@ def sat_params(*, beta=1.0, bome_k=1, n_sweeps=1, moves_per_sweep=0, t0=-1.0, tn
                        _ptr(sweep_cost), int(plan), int(wait_ms))
 
 
-def sat_run(p: Pila, sino_meas, images, stream=None, **kw) -> list[dict]:
+def sat_run(p: Pila, sino_meas, images, stream=None, sync=True, **kw) -> list[dict] | None:
     """Anneal images (in place) against sino_meas; returns per-chain stats.
 
     sino_meas: float32 [n_chains, U, B]; images: float32 [n_chains, n, n].
     Keyword arguments are the fields of sat_params (trace: a buffer of
     TRACE_DTYPE records or a byte tensor of the same size; sweep_cost:
-    float64 [n_chains, n_sweeps])."""
+    float64 [n_chains, n_sweeps]).  sync=False passes no stats: with device
+    tensors the call is then asynchronous on the stream and returns None."""
     n_chains = int(images.shape[0]) if images.ndim == 3 else 1
     prm = sat_params(**kw)
-    stats = (L.SatStats * max(n_chains, 1))()
+    stats = (L.SatStats * max(n_chains, 1))() if sync else None
     L.check(L.load().sat_run(p.handle, n_chains, _ptr(sino_meas, np.float32), _ptr(images, np.float32),
-                             C.byref(prm), C.cast(stats, C.c_void_p), _stream(stream)))
+                             C.byref(prm), C.cast(stats, C.c_void_p) if sync else None, _stream(stream)))
+    if not sync:
+        return None
     return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
 
 

@@ -766,6 +766,7 @@ struct CachedRun {
     RunShape shape{};
     std::vector<cudaEvent_t> evs;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;  // recorded after each launch: a reuse on any stream waits for it
     bool in_use = false;
     unsigned long long last_use = 0;
 };
@@ -776,6 +777,10 @@ std::list<CachedRun*> g_cache;
 unsigned long long g_cache_clock = 0;
 
 void destroy_cached(CachedRun* c) {
+    if (c->done) {  // an asynchronous launch may still be running on the workspace
+        cudaEventSynchronize(c->done);
+        cudaEventDestroy(c->done);
+    }
     if (c->exec) cudaGraphExecDestroy(c->exec);
     for (auto& ev : c->evs) cudaEventDestroy(ev);
     if (c->ws) cudaFree(c->ws);
@@ -1110,8 +1115,36 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
             run->exec = nullptr;  // fall back to direct launches
         }
     }
-    if (run->exec) e = cudaGraphLaunch(run->exec, s);
-    else e = enqueue_run(p, pl, run->b, prm, shape, run->ws, run->ws_bytes, counters, run->evs, nullptr, s);
+    if (run->exec) {
+        if (!run->done && cudaEventCreateWithFlags(&run->done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            run->done = nullptr;
+        }
+        if (run->done) e = cudaStreamWaitEvent(s, run->done, 0);  // an earlier launch of it, on any stream
+        if (e == cudaSuccess) e = cudaGraphLaunch(run->exec, s);
+        if (e == cudaSuccess && run->done) e = cudaEventRecord(run->done, s);
+    } else {
+        e = enqueue_run(p, pl, run->b, prm, shape, run->ws, run->ws_bytes, counters, run->evs, nullptr, s);
+    }
+    // Without stats, and with every buffer in device memory, the call returns
+    // once its graph is enqueued: the graph and its workspace stay cached, and
+    // a later launch of them waits for this one.
+    if (!stats && use_graph && run->exec && run->done && e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        run->in_use = false;
+        run->last_use = ++g_cache_clock;
+        if (!cached) g_cache.push_back(run);
+        while (g_cache.size() > kGraphCacheEntries) {
+            auto victim = g_cache.end();
+            for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
+                if (!(*it)->in_use && *it != run && (victim == g_cache.end() || (*it)->last_use < (*victim)->last_use))
+                    victim = it;
+            if (victim == g_cache.end()) break;
+            destroy_cached(*victim);
+            g_cache.erase(victim);
+        }
+        return SATPILA_OK;
+    }
 
     // Results.
     const BatchDev& b = run->b;

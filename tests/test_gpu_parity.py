@@ -937,6 +937,40 @@ def test_graph_replay_matches_direct_launches(api):
     api.pila_free(p)
 
 
+def test_sat_run_asynchronous_without_stats(api):
+    """With no stats and device buffers sat_run returns once its graph is
+    enqueued; the images, once the stream has run, equal a synchronous call's;
+    two such calls of one problem on two streams share the cached graph and
+    workspace, the second waiting for the first."""
+    n, U = 48, 40
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    C = 4
+    sinos = dev(np.stack([oracle.drt(synth.phantom(n, 6, 60 + i) * mask, U, B) for i in range(C)]).astype(np.float32))
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * C).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    kw = dict(bome_k=4, n_sweeps=3, t0=-1.0, tn=-1.0, seed=8)
+    ref = dev(img0)
+    api.sat_run(p, sinos, ref, **kw)
+    a, b = dev(img0), dev(img0)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    assert api.sat_run(p, sinos, a, stream=s1, sync=False, **kw) is None
+    s1.synchronize()
+    assert np.array_equal(a.cpu().numpy(), ref.cpu().numpy())
+    # the same call twice (same buffers: the same cached graph and workspace),
+    # on two streams: the second must start from the first's result
+    api.sat_run(p, sinos, ref, **kw)  # ref = two synchronous calls in a row
+    a.copy_(dev(img0))
+    torch.cuda.synchronize()
+    api.sat_run(p, sinos, a, stream=s1, sync=False, **kw)
+    api.sat_run(p, sinos, a, stream=s2, sync=False, **kw)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), ref.cpu().numpy())
+    del b
+    api.pila_free(p)
+
+
 def test_autotune_picks_a_layout_and_is_repeatable(api):
     """SAT_FLAG_AUTOTUNE times the launch layouts once per shape: the chosen
     layout is reported, a second call reuses it with identical results, and
