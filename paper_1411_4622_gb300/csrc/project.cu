@@ -111,7 +111,11 @@ __device__ __forceinline__ double cell_output(const ProjArgs& a, int item, int u
             const double r = val - (double)a.pm[(long long)item * a.pm_stride + cell];
             const float rf = (float)r;
             const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
-            float* dst = a.resid + (long long)item * a.resid_stride + (long long)u * pitch + k;
+            // plain rows, or pairs of rows interleaved by 8-cell blocks (the
+            // layout of the annealer's global-memory residuals)
+            const long long at = a.resid_il ? (long long)(u >> 1) * 2 * pitch + ((u & 1) << 3) + k + (k & ~7)
+                                            : (long long)u * pitch + k;
+            float* dst = a.resid + (long long)item * a.resid_stride + at;
             if (a.drift) *drift = fabsf(rf - *dst);
             *dst = rf;
             return r;

@@ -150,11 +150,11 @@ __global__ void __launch_bounds__(256) t0_kernel(const T0Args a) {
                 for (int u = lane; u < a.U; u += 32) {
                     const Entry2 e = decode_rec(row, u, RT);
                     if (e.l0 != 0.0f) {
-                        g = fmaf(R[u * a.pitch + e.k0], e.l0, g);
+                        g = fmaf(R[resid_cell(resid_row_base(u, a.pitch, a.resid_il), e.k0, a.resid_il)], e.l0, g);
                         h = fmaf(e.l0, e.l0, h);
                     }
                     if (e.l1 != 0.0f) {
-                        g = fmaf(R[u * a.pitch + e.k1], e.l1, g);
+                        g = fmaf(R[resid_cell(resid_row_base(u, a.pitch, a.resid_il), e.k1, a.resid_il)], e.l1, g);
                         h = fmaf(e.l1, e.l1, h);
                     }
                 }
@@ -222,7 +222,26 @@ size_t Plan::sweep_smem_bytes() const {
                      : (size_t)groups * group_smem;
 }
 
+namespace {
+int choose_plan_layout(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl);
+}
+
+// The launch layout, then the residual's storage: layouts that gather their
+// cells from global memory keep its rows in interleaved pairs (one DRAM
+// access serves neighbouring angles), the others plain rows.
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl) {
+    const int rc = choose_plan_layout(p, n_chains, window, prm, variant, pl);
+    if (rc != SATPILA_OK) return rc;
+    pl->resid_il = !pl->smem && (pl->kind == 0 || pl->kind == 1 || pl->kind == 4 || pl->kind == 5);
+    if (pl->resid_il) {
+        pl->pitch = (int)align_up((size_t)p->B + 1, 8);
+        pl->resid_floats = (long long)align_up((size_t)resid_rows_end(p->U, pl->pitch, true) + 64 * kMaxGroupWarps, 4);
+    }
+    return SATPILA_OK;
+}
+
+namespace {
+int choose_plan_layout(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl) {
     if (variant == PLAN_RULES && (prm->flags & SAT_FLAG_WINDOW_GROUPS)) {
         if (prm->group_warps != 2 && prm->group_warps != 4)
             return fail(SATPILA_ERR_INVALID_ARG, "sat_run: SAT_FLAG_WINDOW_GROUPS needs group_warps 2 or 4");
@@ -478,6 +497,7 @@ int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_param
     pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
     return SATPILA_OK;
 }
+}  // namespace
 
 
 namespace {
@@ -578,6 +598,7 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
     pa.resid = b.resid + (long long)c0 * pl.resid_floats;
     pa.resid_stride = pl.resid_floats;
     pa.resid_pitch = pl.pitch;
+    pa.resid_il = pl.resid_il ? 1 : 0;
     pa.part_sq = b.part_sq + (long long)c0 * G;
     pa.part_drift = b.part_drift + (long long)c0 * G;
     if (b.proj_ws) use_ray_projector(pa, p, b.proj_ws);
@@ -608,6 +629,7 @@ cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b,
     ta.U = p->U;
     ta.B = p->B;
     ta.pitch = pl.pitch;
+    ta.resid_il = pl.resid_il ? 1 : 0;
     ta.list = p->d_list;
     ta.n_list = p->n_mask;
     ta.beta = prm->beta;
@@ -646,6 +668,7 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.U = p->U;
     sa.B = p->B;
     sa.pitch = pl.pitch;
+    sa.resid_il = pl.resid_il ? 1 : 0;
     sa.band_lo = pl.band_lo;
     sa.band_pitch = pl.band_pitch;
     sa.band_floats = pl.band_floats;

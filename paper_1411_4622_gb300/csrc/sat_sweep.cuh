@@ -91,7 +91,27 @@ struct SatArgs {
     unsigned long long wait_ns;  // bound on a wait for a chain's earlier stages (and for a chain to claim)
     unsigned* ties;              // [n_chains] near-tie decisions (windowed kernels built to count them)
     int stall_chain;             // test hook: this chain's first task is never reported done (-1: none)
+    int resid_il;                // residual in global memory stored with row pairs interleaved (resid_row_base)
 };
+
+// Residual rows in global memory are stored plainly (cell (u, k) at
+// u * pitch + k) or, for layouts that gather their cells from global memory,
+// with each pair of rows (2i, 2i + 1) interleaved by 8-cell (32-byte) blocks:
+// [row 2i, cells 8b..8b+7][row 2i+1, cells 8b..8b+7] for b = 0, 1, ... (pitch
+// a multiple of 8).  A DRAM access fetches 64 bytes, so a cell's access also
+// brings the same bins of the neighbouring angle, which the same move mostly
+// needs (a pixel's bin moves by about one bin per angle step).  Cell (u, k)
+// sits at resid_row_base(u) + k + (k & ~7) in that layout.
+__host__ __device__ __forceinline__ int resid_row_base(int u, int pitch, bool il) {
+    return il ? (u >> 1) * 2 * pitch + ((u & 1) << 3) : u * pitch;
+}
+__host__ __device__ __forceinline__ int resid_cell(int row_base, int k, bool il) {
+    return row_base + k + (il ? (k & ~7) : 0);
+}
+// First cell after the rows (the lanes' dummy cells follow).
+__host__ __device__ __forceinline__ int resid_rows_end(int U, int pitch, bool il) {
+    return il ? ((U + 1) >> 1) * 2 * pitch : U * pitch;
+}
 
 // True unless the task just run is the stalled chain's first (test hook).
 __device__ __forceinline__ bool report_progress(const SatArgs& a, int c, int s0) {
@@ -316,17 +336,17 @@ __device__ __forceinline__ void settle_pixels(const GroupShared& G, PendingPixel
 // after the residual.  So loads and stores need no predicate.
 template <int JMAX>
 __device__ __forceinline__ void gather(const float* R, const int (&rowbase)[JMAX], const Recs<JMAX>& r,
-                                       float (&v0)[JMAX], float (&v1)[JMAX]) {
+                                       float (&v0)[JMAX], float (&v1)[JMAX], bool il) {
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        const float* q = R + rowbase[j] + r.k[j];
-        v0[j] = q[0];
-        v1[j] = q[1];
+        v0[j] = R[resid_cell(rowbase[j], r.k[j], il)];
+        v1[j] = R[resid_cell(rowbase[j], r.k[j] + 1, il)];
     }
 }
 
 struct StageCtx {
     int s, M, D, W, wig, lane, gid, gl;
+    bool il;  // the residual R is in global memory with interleaved row pairs
     float T;
     float* R;
     float* img;
@@ -364,7 +384,7 @@ __device__ __forceinline__ void start_prepare(const SatArgs& a, const GroupShare
     n.f = __ldcg(x.img + n.p);  // L2: never a line another store of this chain left stale in L1
     n.h = __ldg(a.hsum + n.p);
     decode_stage<F16, JMAX>(stage, x.gl, x.W, n.r);
-    gather<JMAX>(x.R, rowbase, n.r, n.v0, n.v1);
+    gather<JMAX>(x.R, rowbase, n.r, n.v0, n.v1, x.il);
 }
 
 // Partial sums of move n relative to the previous move's records `prev`,
@@ -485,11 +505,10 @@ __device__ __forceinline__ void move_step(const SatArgs& a, const GroupShared& G
     // ---- Eq. (6) for move m on the lane's own cells ----
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        float* q = x.R + rowbase[j] + cur.r.k[j];
         const float v0 = fmaf(cr.df_prev, cur.s0[j], cur.v0[j]);  // the previous move's update
         const float v1 = fmaf(cr.df_prev, cur.s1[j], cur.v1[j]);
-        q[0] = fmaf(df, cur.r.l0[j], v0);  // unchanged value when rejected or empty
-        q[1] = fmaf(df, cur.r.l1[j], v1);
+        x.R[resid_cell(rowbase[j], cur.r.k[j], x.il)] = fmaf(df, cur.r.l0[j], v0);  // unchanged when rejected or empty
+        x.R[resid_cell(rowbase[j], cur.r.k[j] + 1, x.il)] = fmaf(df, cur.r.l1[j], v1);
     }
     const float fnew = accept ? best_f : f;
     __stcg(x.img + cur.p, fnew);  // every warp of the group writes the same value
@@ -637,11 +656,12 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
 
     // Residual row offsets of the lane's angles; records past U use the
     // lane's two dummy cells after the residual rows.
+    const bool il = !SMEM && a.resid_il;
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int u = record_of<F16>(gl, W, j);
-        rowbase[j] = u < a.U ? u * a.pitch : a.U * a.pitch + 2 * gl;
+        rowbase[j] = u < a.U ? resid_row_base(u, a.pitch, il) : resid_rows_end(a.U, a.pitch, il) + 2 * gl;
     }
 
     uint32_t phase = 0;
@@ -700,6 +720,7 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
         x.lane = lane;
         x.gid = gid;
         x.gl = gl;
+        x.il = il;
         x.R = R;
         x.img = a.img + (long long)c * a.img_stride;
         const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
@@ -748,6 +769,7 @@ struct T0Args {
     int f16;  // table precision (PILA_F32, PILA_F16, PILA_U8)
     int n, U, B;
     int pitch;
+    int resid_il;  // residual rows in interleaved pairs (resid_row_base)
     const int32_t* list;
     int n_list;
     float beta;

@@ -125,13 +125,13 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                 k[j][s] = r.k[s];
                 l0[j][s] = r.l0[s];
                 l1[j][s] = r.l1[s];
-                const float* q = x.R + rowbase[s] + r.k[s];
                 if (SMEM) {
+                    const float* q = x.R + rowbase[s] + r.k[s];
                     v0[j][s] = q[0];
                     v1[j][s] = q[1];
                 } else {
-                    v0[j][s] = __ldcg(q);
-                    v1[j][s] = __ldcg(q + 1);
+                    v0[j][s] = __ldcg(x.R + resid_cell(rowbase[s], r.k[s], x.il));
+                    v1[j][s] = __ldcg(x.R + resid_cell(rowbase[s], r.k[s] + 1, x.il));
                 }
             }
         }
@@ -349,13 +349,13 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                         }
                         ++e;
                     }
-                float* q = x.R + rowbase[s] + k[j][s];
                 if (SMEM) {
+                    float* q = x.R + rowbase[s] + k[j][s];
                     q[0] = fmaf(df[j], l0[j][s], c0);
                     q[1] = fmaf(df[j], l1[j][s], c1);
                 } else {
-                    __stcg(q, fmaf(df[j], l0[j][s], c0));
-                    __stcg(q + 1, fmaf(df[j], l1[j][s], c1));
+                    __stcg(x.R + resid_cell(rowbase[s], k[j][s], x.il), fmaf(df[j], l0[j][s], c0));
+                    __stcg(x.R + resid_cell(rowbase[s], k[j][s] + 1, x.il), fmaf(df[j], l1[j][s], c1));
                 }
             }
             if (pc[j] >= 0) __stcg(x.img + pc[j], fnew[j]);
@@ -399,11 +399,12 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     // the last angle address two dummy cells of their own.
     const int rpitch = SMEM ? a.band_pitch : a.pitch;
     const int rshift = SMEM ? a.band_lo : 0;
+    const bool il = !SMEM && a.resid_il;  // global residual with interleaved row pairs
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int u = rt_record_of<RT>(lane, 1, j);
-        rowbase[j] = u < a.U ? u * rpitch - rshift : a.U * rpitch + 2 * lane;
+        rowbase[j] = u < a.U ? resid_row_base(u, rpitch, il) - rshift : resid_rows_end(a.U, rpitch, il) + 2 * lane;
     }
     if (SMEM) {
         rs[a.U * rpitch + 2 * lane] = 0.0f;
@@ -514,6 +515,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         x.lane = lane;
         x.gid = 1 + warp;
         x.gl = lane;
+        x.il = il;
         x.R = SMEM ? rs : gres;
         x.img = a.img + (long long)c * a.img_stride;
         const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
@@ -617,11 +619,12 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
     // each warp of the group reading and writing the rows of its own angles.
     const int rpitch = SMEM ? a.band_pitch : a.pitch;
     const int rshift = SMEM ? a.band_lo : 0;
+    const bool il = !SMEM && a.resid_il;  // global residual with interleaved row pairs
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int u = rt_record_of<RT>(gl, WG, j);
-        rowbase[j] = u < a.U ? u * rpitch - rshift : a.U * rpitch + 2 * gl;
+        rowbase[j] = u < a.U ? resid_row_base(u, rpitch, il) - rshift : resid_rows_end(a.U, rpitch, il) + 2 * gl;
     }
     if (SMEM) {
         rs[a.U * rpitch + 2 * gl] = 0.0f;
@@ -689,6 +692,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         x.lane = lane;
         x.gid = gid;
         x.gl = gl;
+        x.il = il;
         x.R = SMEM ? rs : gres;
         x.img = a.img + (long long)c * a.img_stride;
         const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
