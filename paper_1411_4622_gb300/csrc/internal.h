@@ -87,7 +87,7 @@ struct ProjArgs {
     float* resid;               // RESYNC: residual P_c - P_m; SIRT: correction
     long long resid_stride;
     int resid_pitch;            // row pitch of resid (B when 0)
-    int resid_il;               // RESYNC: resid rows stored in interleaved pairs (sat_sweep.cuh, resid_row_base)
+    int resid_il;               // RESYNC: 0, or resid rows (u, u + resid_il) stored in interleaved pairs (resid_row_base)
     const float* w;             // SIRT: factor matrix (float)
     double* part_sq;            // [item][U] per-angle sums of (P_c - P_m)^2
     float* part_drift;          // [item][U]

@@ -90,6 +90,15 @@ __device__ __forceinline__ void add_entry(long long* row, int k, const FixedSpli
     atomicAdd(reinterpret_cast<unsigned long long*>(&row[k]), (unsigned long long)t);
 }
 
+// Offset of cell (u, k) in a residual whose rows (u, u + il) are stored in
+// interleaved pairs of 8-cell blocks (the annealer's layout for residuals it
+// gathers from global memory; the same formula as its kernels use).
+__device__ __forceinline__ long long resid_cell_at(int u, int k, int pitch, int il) {
+    const int ls = il == 4 ? 2 : il == 2 ? 1 : 0;
+    const long long pair = ((long long)(u >> (ls + 1)) << ls) + (u & (il - 1));
+    return pair * 2 * pitch + (((u >> ls) & 1) << 3) + k + (k & ~7);
+}
+
 // Outputs of cell (u, k) of image item from its fixed-point sum; returns
 // P_c - P_m (RESYNC, SIRT; else 0), whose square the row sums add with one
 // rounding (an explicit fused multiply-add, the same in every path), and,
@@ -113,8 +122,7 @@ __device__ __forceinline__ double cell_output(const ProjArgs& a, int item, int u
             const int pitch = a.resid_pitch > 0 ? a.resid_pitch : B;
             // plain rows, or pairs of rows interleaved by 8-cell blocks (the
             // layout of the annealer's global-memory residuals)
-            const long long at = a.resid_il ? (long long)(u >> 1) * 2 * pitch + ((u & 1) << 3) + k + (k & ~7)
-                                            : (long long)u * pitch + k;
+            const long long at = a.resid_il ? resid_cell_at(u, k, pitch, a.resid_il) : (long long)u * pitch + k;
             float* dst = a.resid + (long long)item * a.resid_stride + at;
             if (a.drift) *drift = fabsf(rf - *dst);
             *dst = rf;

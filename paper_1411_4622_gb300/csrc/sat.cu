@@ -232,10 +232,13 @@ int choose_plan_layout(const satpila_pila* p, int n_chains, int window, const sa
 int choose_plan(const satpila_pila* p, int n_chains, int window, const sat_params* prm, int variant, Plan* pl) {
     const int rc = choose_plan_layout(p, n_chains, window, prm, variant, pl);
     if (rc != SATPILA_OK) return rc;
-    pl->resid_il = !pl->smem && (pl->kind == 0 || pl->kind == 1 || pl->kind == 4 || pl->kind == 5);
+    const bool gathers = !pl->smem && (pl->kind == 0 || pl->kind == 1 || pl->kind == 4 || pl->kind == 5);
+    // pair stride: the records per 16-byte chunk of the table
+    pl->resid_il = gathers ? (p->precision == PILA_U8 ? 4 : p->precision == PILA_F16 ? 2 : 1) : 0;
     if (pl->resid_il) {
         pl->pitch = (int)align_up((size_t)p->B + 1, 8);
-        pl->resid_floats = (long long)align_up((size_t)resid_rows_end(p->U, pl->pitch, true) + 64 * kMaxGroupWarps, 4);
+        pl->resid_floats =
+            (long long)align_up((size_t)resid_rows_end(p->U, pl->pitch, pl->resid_il) + 64 * kMaxGroupWarps, 4);
     }
     return SATPILA_OK;
 }
@@ -598,7 +601,7 @@ cudaError_t enqueue_resync(const satpila_pila* p, const Plan& pl, const BatchDev
     pa.resid = b.resid + (long long)c0 * pl.resid_floats;
     pa.resid_stride = pl.resid_floats;
     pa.resid_pitch = pl.pitch;
-    pa.resid_il = pl.resid_il ? 1 : 0;
+    pa.resid_il = pl.resid_il;
     pa.part_sq = b.part_sq + (long long)c0 * G;
     pa.part_drift = b.part_drift + (long long)c0 * G;
     if (b.proj_ws) use_ray_projector(pa, p, b.proj_ws);
@@ -629,7 +632,7 @@ cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b,
     ta.U = p->U;
     ta.B = p->B;
     ta.pitch = pl.pitch;
-    ta.resid_il = pl.resid_il ? 1 : 0;
+    ta.resid_il = pl.resid_il;
     ta.list = p->d_list;
     ta.n_list = p->n_mask;
     ta.beta = prm->beta;
@@ -668,7 +671,7 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.U = p->U;
     sa.B = p->B;
     sa.pitch = pl.pitch;
-    sa.resid_il = pl.resid_il ? 1 : 0;
+    sa.resid_il = pl.resid_il;
     sa.band_lo = pl.band_lo;
     sa.band_pitch = pl.band_pitch;
     sa.band_floats = pl.band_floats;

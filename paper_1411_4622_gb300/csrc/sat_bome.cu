@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kBomeWarps * 32) sat_bome_kernel(const SatArgs
         x.lane = lane;
         x.gid = 1 + warp;
         x.gl = lane;
-        x.il = false;  // plain rows (this kernel's plans never interleave them)
+        x.il = 0;  // plain rows (this kernel's plans never interleave them)
         x.R = a.resid + (long long)c * a.resid_floats;
         x.img = a.img + (long long)c * a.img_stride;
         const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;

@@ -37,7 +37,7 @@ struct Plan {
     int stage_bytes = 0, group_smem = 0;
     long long resid_floats = 0;
     int pitch = 0;               // residual row pitch in global memory (floats, multiple of 4; of 8 when resid_il)
-    bool resid_il = false;       // global residual rows stored in interleaved pairs (resid_row_base)
+    int resid_il = 0;            // global residual rows stored in pairs (u, u + resid_il) interleaved (resid_row_base)
     int band_lo = 0;             // first bin of the shared-memory band (multiple of 4)
     int band_pitch = 0;          // band row length in shared memory (floats, multiple of 4)
     long long band_floats = 0;   // shared-memory residual of a windowed warp

@@ -91,26 +91,32 @@ struct SatArgs {
     unsigned long long wait_ns;  // bound on a wait for a chain's earlier stages (and for a chain to claim)
     unsigned* ties;              // [n_chains] near-tie decisions (windowed kernels built to count them)
     int stall_chain;             // test hook: this chain's first task is never reported done (-1: none)
-    int resid_il;                // residual in global memory stored with row pairs interleaved (resid_row_base)
+    int resid_il;                // 0: plain residual rows; 1, 2, 4: rows u and u + resid_il interleaved (resid_row_base)
 };
 
 // Residual rows in global memory are stored plainly (cell (u, k) at
 // u * pitch + k) or, for layouts that gather their cells from global memory,
-// with each pair of rows (2i, 2i + 1) interleaved by 8-cell (32-byte) blocks:
-// [row 2i, cells 8b..8b+7][row 2i+1, cells 8b..8b+7] for b = 0, 1, ... (pitch
+// in pairs of rows (u, u + s) interleaved by 8-cell (32-byte) blocks:
+// [row u, cells 8b..8b+7][row u + s, cells 8b..8b+7] for b = 0, 1, ... (pitch
 // a multiple of 8).  A DRAM access fetches 64 bytes, so a cell's access also
-// brings the same bins of the neighbouring angle, which the same move mostly
-// needs (a pixel's bin moves by about one bin per angle step).  Cell (u, k)
-// sits at resid_row_base(u) + k + (k & ~7) in that layout.
-__host__ __device__ __forceinline__ int resid_row_base(int u, int pitch, bool il) {
-    return il ? (u >> 1) * 2 * pitch + ((u & 1) << 3) : u * pitch;
+// brings the same bins of an angle s steps away, which the same move mostly
+// needs (a pixel's bin moves by about one bin per angle step).  s is the
+// number of records per 16-byte chunk of the table (1 FP32, 2 FP16, 4 one-byte):
+// the lanes of one warp instruction then hold the two rows of a pair in
+// neighbouring lanes, so both halves of the 64 bytes travel in one request.
+// Cell (u, k) sits at resid_row_base(u) + k + (k & ~7) in that layout.
+__host__ __device__ __forceinline__ int resid_row_base(int u, int pitch, int il) {
+    if (!il) return u * pitch;
+    const int ls = il == 4 ? 2 : il == 2 ? 1 : 0;  // log2 of the pair stride s
+    const int pair = ((u >> (ls + 1)) << ls) + (u & (il - 1));
+    return pair * 2 * pitch + (((u >> ls) & 1) << 3);
 }
-__host__ __device__ __forceinline__ int resid_cell(int row_base, int k, bool il) {
+__host__ __device__ __forceinline__ int resid_cell(int row_base, int k, int il) {
     return row_base + k + (il ? (k & ~7) : 0);
 }
 // First cell after the rows (the lanes' dummy cells follow).
-__host__ __device__ __forceinline__ int resid_rows_end(int U, int pitch, bool il) {
-    return il ? ((U + 1) >> 1) * 2 * pitch : U * pitch;
+__host__ __device__ __forceinline__ int resid_rows_end(int U, int pitch, int il) {
+    return il ? (U + 2 * il - 1) / (2 * il) * (2 * il) * pitch : U * pitch;
 }
 
 // True unless the task just run is the stalled chain's first (test hook).
@@ -336,7 +342,7 @@ __device__ __forceinline__ void settle_pixels(const GroupShared& G, PendingPixel
 // after the residual.  So loads and stores need no predicate.
 template <int JMAX>
 __device__ __forceinline__ void gather(const float* R, const int (&rowbase)[JMAX], const Recs<JMAX>& r,
-                                       float (&v0)[JMAX], float (&v1)[JMAX], bool il) {
+                                       float (&v0)[JMAX], float (&v1)[JMAX], int il) {
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         v0[j] = R[resid_cell(rowbase[j], r.k[j], il)];
@@ -346,7 +352,7 @@ __device__ __forceinline__ void gather(const float* R, const int (&rowbase)[JMAX
 
 struct StageCtx {
     int s, M, D, W, wig, lane, gid, gl;
-    bool il;  // the residual R is in global memory with interleaved row pairs
+    int il;   // the residual R is in global memory with interleaved row pairs (their stride), or 0
     float T;
     float* R;
     float* img;
@@ -656,7 +662,7 @@ __device__ __forceinline__ void pipeline_group(const SatArgs& a, unsigned char* 
 
     // Residual row offsets of the lane's angles; records past U use the
     // lane's two dummy cells after the residual rows.
-    const bool il = !SMEM && a.resid_il;
+    const int il = SMEM ? 0 : a.resid_il;
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
@@ -769,7 +775,7 @@ struct T0Args {
     int f16;  // table precision (PILA_F32, PILA_F16, PILA_U8)
     int n, U, B;
     int pitch;
-    int resid_il;  // residual rows in interleaved pairs (resid_row_base)
+    int resid_il;  // residual rows in interleaved pairs (their stride; resid_row_base), or 0
     const int32_t* list;
     int n_list;
     float beta;

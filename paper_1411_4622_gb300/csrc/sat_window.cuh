@@ -399,7 +399,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     // the last angle address two dummy cells of their own.
     const int rpitch = SMEM ? a.band_pitch : a.pitch;
     const int rshift = SMEM ? a.band_lo : 0;
-    const bool il = !SMEM && a.resid_il;  // global residual with interleaved row pairs
+    const int il = SMEM ? 0 : a.resid_il;  // global residual with interleaved row pairs (their stride)
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
@@ -619,7 +619,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
     // each warp of the group reading and writing the rows of its own angles.
     const int rpitch = SMEM ? a.band_pitch : a.pitch;
     const int rshift = SMEM ? a.band_lo : 0;
-    const bool il = !SMEM && a.resid_il;  // global residual with interleaved row pairs
+    const int il = SMEM ? 0 : a.resid_il;  // global residual with interleaved row pairs (their stride)
     int rowbase[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
