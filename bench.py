@@ -523,10 +523,11 @@ def precision_sample(pk, *, chains=304, stages=2, tables=("f16", "f32", "u8"), s
                          "sector_bytes": sector_resid, "sector_write_bytes": sector_write,
                          "useful_bytes_per_move": useful,
                          "peak_rule": "bytes read: rows at the HBM stream rate, residual sectors at the sector-gather "
-                                      "rate of the chains' residual footprint (one 1.05 MB region per chain); the "
-                                      "scatter's write-back of the same sectors is reported beside it",
-                         "frac_with_writes": (row_bytes / pk["hbm_stream_gbs"]
-                                              + (sector_resid + sector_write) / pk["ws_sector_gbs"]) * rate / 1e9,
+                                      "rate of the chains' residual footprint (one 1.05 MB region per chain; the "
+                                      "probe's random sectors move 64 bytes of DRAM each, the residual's paired rows "
+                                      "put two needed sectors in most 64-byte blocks); every byte class, the "
+                                      "scatter's write-back included, against the HBM copy rate in frac_all_vs_hbm",
+                         "frac_all_vs_hbm": (row_bytes + sector_resid + sector_write) * rate / 1e9 / pk["hbm_copy_gbs"],
                          "frac_rows": row_bytes * rate / 1e9 / pk["hbm_stream_gbs"],
                          "frac_sectors": sector_resid * rate / 1e9 / pk["ws_sector_gbs"],
                          "frac_sectors_vs_hbm_probe": sector_resid * rate / 1e9 / pk["hbm_sector_gbs"],
