@@ -743,9 +743,11 @@ def serve_stream(nreq, rate=None, burst=400, seed=7):
                 time.sleep(min(0.001, max(0.0, due - time.perf_counter())))
             tickets.append(srv.submit(**reqs[i]))
         lat, done_moves, failed = [], 0, 0
-        for x in tickets:
+        by_size = {s: [] for s in (64, 128, 256, 512)}
+        for i, x in enumerate(tickets):
             img, st = srv.wait(x)
             lat.append(st["done_ms"] - st["submit_ms"])
+            by_size[int(sizes[i])].append(lat[-1])
             done_moves += st["proposed"]
             failed += int(st["status"] != 0)
         wall = time.perf_counter() - t0
@@ -753,9 +755,11 @@ def serve_stream(nreq, rate=None, burst=400, seed=7):
         info = srv.info()
     return {"moves_per_s": done_moves / wall, "wall_ms": wall * 1e3, "requests": nreq,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "latency_p50_ms_by_size": {str(s): float(np.percentile(v, 50)) for s, v in by_size.items() if v},
             "rate_per_s": rate, "capacity_moves_per_s": cap, "failed": failed,
             "config": {"sizes": [64, 128, 256, 512], "stages": 50, "k": [1, 4, 8], "pila": "f16",
-                       "budget_bytes": budget, "arrival": "poisson", "geometries": len(sinos)},
+                       "budget_bytes": budget, "arrival": "poisson", "geometries": len(sinos),
+                       "launches": "one per window for each image size's classes (windowed kernel, 4-warp groups)"},
             "server": {k: info[k] for k in ("ticks", "bytes_peak", "geometries", "classes")}, "clocks": clk}
 
 
@@ -775,7 +779,8 @@ def run_serve(args):
            "config": dict(workload="serve", requests=args.requests, rate_per_s=r["rate_per_s"],
                           rate_rule="given" if args.rate else "80% of burst capacity",
                           capacity_moves_per_s=r["capacity_moves_per_s"], **r["config"]),
-           "latency_ms": r["latency_ms"], "failed": r["failed"], "server": r["server"], "clocks": r["clocks"]}
+           "latency_ms": r["latency_ms"], "latency_p50_ms_by_size": r["latency_p50_ms_by_size"], "failed": r["failed"],
+           "server": r["server"], "clocks": r["clocks"]}
     print(json.dumps(out))
 
 

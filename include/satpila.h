@@ -279,7 +279,13 @@ typedef struct {
     int32_t queue_limit;     /* waiting requests beyond which submit returns SATPILA_ERR_BUSY; 0: 65536 */
     uint64_t mem_budget;     /* device bytes for tables and chain state; 0: 120 GB (1.2e11 bytes); capped at the
                                 device's free memory less 2 GiB */
+    uint32_t flags;          /* SAT_SERVER_* */
 } sat_server_cfg;
+
+/* sat_server_cfg.flags: every class ticks on its own stream with its own
+ * launches (the layout sat_run's size rules pick), instead of sharing its
+ * image size's launches. */
+#define SAT_SERVER_PER_CLASS 1u
 
 typedef struct {
     int32_t n, n_angles, n_bins; /* geometry, as pila_geom */
@@ -306,13 +312,21 @@ typedef struct {
 
 /*
  * Start a server: one engine thread that owns the device work.  Requests
- * sharing geometry, bome_k, beta and moves per stage anneal together in one
- * persistent sweep launch per tick (each chain at its own stage of its own
- * schedule); different such classes run on their own streams.  Between ticks
- * finished chains are copied out and waiting requests are admitted, in
- * arrival order, while chain slots and the memory budget allow (PILA tables
- * are cached per geometry and unused ones dropped when memory is needed).
- * A chain's result is the same alone and in any mix.
+ * sharing geometry, bome_k, beta and moves per stage form a class, whose
+ * chains live in the class's arrays, each at its own stage of its own
+ * schedule.  The classes of one image size and table precision share one
+ * persistent sweep launch per window of stages_per_tick stages (the windowed
+ * kernel on groups of 4 warps, every chain reading its own class's table and
+ * geometry; for tables of at most 512 angles and bome_k <= 8 without a
+ * requested layout), followed by each class's resync; other classes, and all
+ * of them with SAT_SERVER_PER_CLASS, run their own launches on their own
+ * streams.  Between ticks finished chains are copied out and waiting
+ * requests are admitted, in arrival order, while chain slots and the memory
+ * budget allow (PILA tables are cached per geometry and unused ones dropped
+ * when memory is needed).  A chain's result is the same alone and in any mix:
+ * sat_run on that chain with resync_every = stages_per_tick and
+ * plan = SAT_PLAN_WINDOW_G4 for a request of a shared launch (the size rules'
+ * layout with SAT_SERVER_PER_CLASS or for other requests).
  * Errors: INVALID_ARG (no such device), OOM.
  */
 int sat_server_create(const sat_server_cfg* cfg, satpila_server** out);

@@ -26,6 +26,7 @@ SAT_FLAG_NEAR_TIES = 64
  SAT_PLAN_WINDOW_SMEM_G4) = range(11)
 SIRT_SIMULTANEOUS, SIRT_SEQUENTIAL = 0, 1
 PROBE_STREAM, PROBE_SECTOR = 0, 1
+SAT_SERVER_PER_CLASS = 1
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["satpila_last_error", "satpila_version", "pila_build", "pila_free", "pila_info", "pila_export",
@@ -70,7 +71,7 @@ class SatStats(C.Structure):
 
 class SatServerCfg(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_active", C.c_int32), ("stages_per_tick", C.c_int32),
-                ("queue_limit", C.c_int32), ("mem_budget", C.c_uint64)]
+                ("queue_limit", C.c_int32), ("mem_budget", C.c_uint64), ("flags", C.c_uint32)]
 
 
 class SatRequest(C.Structure):

@@ -21,7 +21,7 @@ from ._lib import ERR_BUSY, ERR_INVALID_ARG, ERR_NOT_FOUND, ERR_PENDING  # noqa:
 from ._lib import (SAT_FLAG_WINDOW_GROUPS, SAT_PLAN_PIPE_1, SAT_PLAN_PIPE_2, SAT_PLAN_PIPE_4,  # noqa: F401
                    SAT_PLAN_RULES, SAT_PLAN_WINDOW_G2, SAT_PLAN_WINDOW_G4, SAT_PLAN_WINDOW_GLOBAL,
                    SAT_PLAN_WINDOW_HYBRID, SAT_PLAN_WINDOW_SMEM, SAT_PLAN_WINDOW_SMEM_G2, SAT_PLAN_WINDOW_SMEM_G4)
-from ._lib import PROBE_SECTOR, PROBE_STREAM  # noqa: F401
+from ._lib import PROBE_SECTOR, PROBE_STREAM, SAT_SERVER_PER_CLASS  # noqa: F401
 
 TRACE_DTYPE = np.dtype([("pixel", "<i4"), ("cstar", "<i4"), ("accepted", "<i4"), ("pad", "<i4"),
                         ("dS", "<f4"), ("dC", "<f4"), ("fnew", "<f4"), ("pad2", "<f4")])
@@ -228,8 +228,9 @@ class Server:
     submit() copies the request's arrays and returns a ticket; poll()/wait()
     return (image [n, n] float32, result dict) once the request is done."""
 
-    def __init__(self, device=0, max_active=0, stages_per_tick=0, queue_limit=0, mem_budget=0):
-        cfg = L.SatServerCfg(int(device), int(max_active), int(stages_per_tick), int(queue_limit), int(mem_budget))
+    def __init__(self, device=0, max_active=0, stages_per_tick=0, queue_limit=0, mem_budget=0, flags=0):
+        cfg = L.SatServerCfg(int(device), int(max_active), int(stages_per_tick), int(queue_limit), int(mem_budget),
+                             int(flags))
         h = C.c_void_p()
         L.check(L.load().sat_server_create(C.byref(cfg), C.byref(h)))
         self.handle = h

@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libsatpila.so")
 SOURCES = ["api.cu", "pila.cu", "project.cu", "sat.cu", "sat_f32_smem.cu", "sat_f32_glob.cu", "sat_f16_smem.cu",
            "sat_f16_glob.cu", "sat_window.cu", "sat_window_nt.cu", "sat_window_group.cu", "sat_window_group_nt.cu",
-           "sat_window_gsmem.cu", "sat_window_gsmem_nt.cu", "sat_bome.cu", "drt.cu", "fbp.cu", "sirt.cu",
+           "sat_window_gsmem.cu", "sat_window_gsmem_nt.cu", "sat_window_multi.cu", "sat_bome.cu", "drt.cu", "fbp.cu", "sirt.cu",
            "server.cu", "probe.cu", "rays.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -41,6 +41,7 @@ SweepFn hybrid_kernel_nt(int rt, int jmax, int kmax);
 SweepFn window_group_kernel_nt(int rt, int jmax, int kmax, int warps_per_chain);
 SweepFn window_group_smem_kernel(int rt, int jmax, int kmax, int warps_per_chain);
 SweepFn window_group_smem_kernel_nt(int rt, int jmax, int kmax, int warps_per_chain);
+SweepFn window_multi_kernel(int rt);
 int bome_warps_per_cta();
 
 namespace {
@@ -360,7 +361,9 @@ int choose_plan_layout(const satpila_pila* p, int n_chains, int window, const sa
         const int stage = 512 * Wg * (jw / rpc);
         const size_t glob = align_up(group_ring_bytes(Wg, kmax_for(prm->bome_k)) + (size_t)2 * kWin * stage, 128);
         const int kmax = kmax_for(prm->bome_k);
-        const int groups = std::max(1, std::min(kSatMaxWarps / Wg, std::min(n_chains, (int)(maxopt / glob))));
+        // one chain per CTA while the chains fit one per SM, else as many as fit
+        const int groups =
+            n_chains <= sms ? 1 : std::max(1, std::min(kSatMaxWarps / Wg, std::min(n_chains, (int)(maxopt / glob))));
         pl->kind = Wg == 2 ? 4 : 5;
         pl->smem = false;
         pl->W = Wg;
@@ -657,10 +660,8 @@ cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b,
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm,
-                          int n_chains, int M, int s_total, int s_begin, int s_end, int* task_counter,
-                          cudaStream_t q) {
-    if (n_chains <= 0 || s_end <= s_begin) return cudaSuccess;
+SatArgs sweep_args(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm, int n_chains,
+                   int M, int s_total, int s_begin, int s_end, int* task_counter) {
     const long long P = (long long)p->n * p->n, cells = (long long)p->U * p->B;
     SatArgs sa{};
     sa.table = p->d_table;
@@ -718,8 +719,80 @@ cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev&
     sa.sweeps_per_task = spt;
     sa.n_tasks = n_chains * ((s_end - s_begin + spt - 1) / spt);
     sa.task_counter = task_counter;
+    return sa;
+}
+
+cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm,
+                          int n_chains, int M, int s_total, int s_begin, int s_end, int* task_counter,
+                          cudaStream_t q) {
+    if (n_chains <= 0 || s_end <= s_begin) return cudaSuccess;
+    const SatArgs sa = sweep_args(p, pl, b, prm, n_chains, M, s_total, s_begin, s_end, task_counter);
     return launch_sweep(p->precision, pl.smem, pl.kind, sweep_counts_ties(pl, prm), pl.jmax, kmax_for(prm->bome_k), sa,
                         pl.grid, pl.warps, pl.sweep_smem_bytes(), q);
+}
+
+// ---- one launch over chains of several tables ------------------------------
+
+bool multi_table_ok(const satpila_pila* p, const sat_params* prm) {
+    const int rpc = p->precision == PILA_U8 ? 4 : p->precision == PILA_F16 ? 2 : 1;
+    const int per_lane = rpc * ((p->row_records + 32 * rpc * 4 - 1) / (32 * rpc * 4));
+    return per_lane <= 4 && prm->bome_k >= 1 && prm->bome_k <= 8 && prm->residency != SAT_RESIDENT_SMEM &&
+           prm->group_warps <= 1 && prm->pipeline_depth == 0 && !(prm->flags & SAT_FLAG_BOME_INDEPENDENT);
+}
+
+int plan_multi(int rt, int n_chains, int window, Plan* pl) {
+    SweepFn k = window_multi_kernel(rt);
+    if (!k) return fail(SATPILA_ERR_INVALID_ARG, "sat_server: no launch over several tables for this precision");
+    int dev = 0, maxopt = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int rpc = rt == PILA_U8 ? 4 : rt == PILA_F16 ? 2 : 1;
+    constexpr int Wg = 4, jw = 4, kmax = 8;
+    const int stage = 512 * Wg * (jw / rpc);
+    const size_t glob = align_up(group_ring_bytes(Wg, kmax) + (size_t)2 * kWin * stage, 128);
+    // one chain per CTA while the chains fit one per SM (so two chains do not
+    // share an SM's schedulers while others stand idle), else two
+    const int groups = n_chains <= sms ? 1 : std::max(1, std::min(kSatMaxWarps / Wg, (int)(maxopt / glob)));
+    *pl = Plan{};
+    pl->kind = 5;
+    pl->smem = false;
+    pl->W = Wg;
+    pl->J = pl->jmax = jw;
+    pl->D = 4;
+    pl->stage_bytes = stage;
+    pl->group_smem = (int)glob;
+    pl->groups = groups;
+    pl->warps = groups * Wg;
+    cudaError_t e = allow_max_smem(k);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, pl->warps * 32, (size_t)groups * glob);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return fail(SATPILA_ERR_INVALID_ARG, "sat_server: launch over several tables does not fit");
+    }
+    const long long slots = (long long)sms * per_sm * groups;
+    pl->spt = n_chains <= slots ? window : 1;
+    const long long tasks = (long long)n_chains * ((window + pl->spt - 1) / pl->spt);
+    const long long want = (std::min<long long>(tasks, slots) + groups - 1) / groups;
+    pl->grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * per_sm));
+    return SATPILA_OK;
+}
+
+cudaError_t prepare_multi(int rt) {
+    cudaError_t e = prepare_projector();
+    SweepFn k = window_multi_kernel(rt);
+    if (e == cudaSuccess) e = k ? allow_max_smem(k) : cudaErrorInvalidValue;
+    return e;
+}
+
+cudaError_t enqueue_sweep_multi(int rt, const Plan& pl, const SatArgs& la, cudaStream_t q) {
+    if (la.n_chains <= 0 || la.sweep_end <= la.sweep_begin) return cudaSuccess;
+    SweepFn k = window_multi_kernel(rt);
+    if (!k) return cudaErrorInvalidValue;
+    k<<<pl.grid, pl.warps * 32, pl.sweep_smem_bytes(), q>>>(la);
+    return cudaGetLastError();
 }
 
 bool sweep_counts_ties(const Plan& pl, const sat_params* prm) {

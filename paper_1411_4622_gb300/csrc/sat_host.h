@@ -104,6 +104,21 @@ cudaError_t enqueue_t0(const satpila_pila* p, const Plan& pl, const BatchDev& b,
 cudaError_t enqueue_sweep(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm,
                           int n_chains, int M, int s_total, int s_begin, int s_end, int* task_counter,
                           cudaStream_t q);
+// The sweep launch's arguments for these chains (what enqueue_sweep launches).
+SatArgs sweep_args(const satpila_pila* p, const Plan& pl, const BatchDev& b, const sat_params* prm, int n_chains,
+                   int M, int s_total, int s_begin, int s_end, int* task_counter);
+// One launch over chains of several tables (the serving engine's classes of
+// one image size and table precision): the windowed kernel on groups of 4
+// warps, four records per lane, up to 8 estimates, residual in global memory.
+// multi_table_ok: a table and parameters that launch can take (at most 512
+// angles, K <= 8, no layout requested).  plan_multi: its launch shape for
+// n_chains chains and `window` stages per launch.  The per-class arguments
+// la.classes[q] are sweep_args of class q with the class plan of
+// PLAN_WINDOW_G4 (residual layout), stage_bytes from the multi plan.
+bool multi_table_ok(const satpila_pila* p, const sat_params* prm);
+int plan_multi(int rt, int n_chains, int window, Plan* pl);
+cudaError_t prepare_multi(int rt);
+cudaError_t enqueue_sweep_multi(int rt, const Plan& pl, const SatArgs& la, cudaStream_t q);
 cudaError_t enqueue_copy_f64(double* dst, const double* src, int n, cudaStream_t q);
 // True when the sweep launches of this plan count near-tie decisions.
 bool sweep_counts_ties(const Plan& pl, const sat_params* prm);

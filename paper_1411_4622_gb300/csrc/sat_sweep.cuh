@@ -92,6 +92,14 @@ struct SatArgs {
     unsigned* ties;              // [n_chains] near-tie decisions (windowed kernels built to count them)
     int stall_chain;             // test hook: this chain's first task is never reported done (-1: none)
     int resid_il;                // 0: plain residual rows; 1, 2, 4: rows u and u + resid_il interleaved (resid_row_base)
+    // A launch over chains of several tables (the serving engine's classes):
+    // the per-class arguments (table, geometry, move rules and the class's
+    // chain arrays), and for each chain of the launch its class and its index
+    // there.  The launch's own fields then hold the task queue, the progress
+    // flags (indexed by the launch's chain number), the error word and the
+    // shared-memory layout.  NULL: one table.
+    const SatArgs* classes;
+    const int2* chain_map;       // [n_chains]
 };
 
 // Residual rows in global memory are stored plainly (cell (u, k) at

@@ -588,8 +588,11 @@ __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_hybrid_kernel(const Sat
 // memory.  Every warp takes every decision itself (the same sums, draws and
 // pixel values) and writes the same pixel values, so the warps exchange
 // only the window sums; the residual cells of an angle belong to one lane.
-template <int RT, int JMAX, int KMAX, int WG, bool NT, bool SMEM>
+// MULTI: the launch carries chains of several tables (a.classes); a task's
+// table, geometry and chain arrays come from its chain's class.
+template <int RT, int JMAX, int KMAX, int WG, bool NT, bool SMEM, bool MULTI>
 __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb, int grp, int wig, int lane) {
+    static_assert(!(MULTI && SMEM), "launches over several tables keep the residual in global memory");
     GroupShared G;
     G.bar = reinterpret_cast<uint64_t*>(gb);
     G.part = reinterpret_cast<float*>(gb + kPartOffset);
@@ -617,21 +620,103 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
     // memory only the band of bins [band_lo, band_lo + band_pitch) is kept
     // (every record of a reconstruction-space pixel addresses cells inside it),
     // each warp of the group reading and writing the rows of its own angles.
-    const int rpitch = SMEM ? a.band_pitch : a.pitch;
-    const int rshift = SMEM ? a.band_lo : 0;
-    const int il = SMEM ? 0 : a.resid_il;  // global residual with interleaved row pairs (their stride)
-    int rowbase[JMAX];
+    auto row_bases = [&](const SatArgs& g, int (&rb)[JMAX]) {
+        const int rpitch = SMEM ? g.band_pitch : g.pitch;
+        const int rshift = SMEM ? g.band_lo : 0;
+        const int il = SMEM ? 0 : g.resid_il;  // global residual with interleaved row pairs (their stride)
 #pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        const int u = rt_record_of<RT>(gl, WG, j);
-        rowbase[j] = u < a.U ? resid_row_base(u, rpitch, il) - rshift : resid_rows_end(a.U, rpitch, il) + 2 * gl;
-    }
+        for (int j = 0; j < JMAX; ++j) {
+            const int u = rt_record_of<RT>(gl, WG, j);
+            rb[j] = u < g.U ? resid_row_base(u, rpitch, il) - rshift : resid_rows_end(g.U, rpitch, il) + 2 * gl;
+        }
+    };
+    int rowbase[JMAX];
+    if (!MULTI) row_bases(a, rowbase);
     if (SMEM) {
-        rs[a.U * rpitch + 2 * gl] = 0.0f;
-        rs[a.U * rpitch + 2 * gl + 1] = 0.0f;
+        rs[a.U * a.band_pitch + 2 * gl] = 0.0f;
+        rs[a.U * a.band_pitch + 2 * gl + 1] = 0.0f;
     }
 
     uint32_t phase = 0;
+    // Stages [s0, s1) of chain ci of the arguments ca (launch chain c);
+    // false when a wait ran out (the group leaves together).
+    auto run_task = [&](const SatArgs& ca, int ci, int c, int s0, int s1, const int (&rb)[JMAX]) -> bool {
+        float* gres = ca.resid + (long long)ci * ca.resid_floats;
+        if (SMEM) {
+            // The band of every residual row into shared memory, one bulk copy
+            // per row spread over the group's lanes, all completing on one
+            // barrier phase; the group leaves together if the wait runs out.
+            const uint32_t row_bytes = (uint32_t)ca.band_pitch * 4u;
+            fence_proxy_async_smem();    // earlier generic accesses to the band before the async-proxy writes
+            fence_proxy_async_global();  // the chain's residual as the previous task left it
+            if (gl == 0) {
+                G.flags[3] = 1;
+                mbar_arrive_expect_tx(G.bar, row_bytes * (uint32_t)ca.U);
+            }
+            group_sync(gid, WG);
+            for (int u = gl; u < ca.U; u += 32 * WG)
+                bulk_copy_g2s(rs + (long long)u * ca.band_pitch, gres + (long long)u * ca.pitch + ca.band_lo, row_bytes,
+                              G.bar);
+            const bool landed = __all_sync(0xffffffffu, mbar_wait_bounded(G.bar, phase));
+            phase ^= 1u;
+            if (!landed && lane == 0) G.flags[3] = 0;
+            group_sync(gid, WG);
+            const int ok = G.flags[3];
+            group_sync(gid, WG);
+            if (!ok) {
+                if (gl == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
+                return false;
+            }
+        }
+        const double S = ca.S[ci];
+        float S_hi = (float)S;
+        float S_lo = -(float)(S - (double)S_hi);
+        unsigned long long n_acc = 0;
+        unsigned n_ties = 0;
+        StageCtx x;
+        x.M = ca.moves;
+        x.D = a.D;
+        x.W = WG;
+        x.wig = wig;
+        x.lane = lane;
+        x.gid = gid;
+        x.gl = gl;
+        x.il = SMEM ? 0 : ca.resid_il;
+        x.R = SMEM ? rs : gres;
+        x.img = ca.img + (long long)ci * ca.img_stride;
+        const ChainCtl* cc = ca.ctl ? ca.ctl + ci : nullptr;
+        const int s_base = cc ? cc->stage0 : 0, s_total = cc ? cc->n_sweeps : ca.n_sweeps_total;
+        const int sched = cc ? cc->schedule : ca.schedule;
+        x.key = chain_key(cc ? cc->seed : ca.seed + (unsigned long long)ci);
+        x.tracing = ca.trace != nullptr && ci == ca.trace_chain;
+        const double T0 = ca.T0[ci], TN = ca.TN[ci];
+        for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
+            x.s = s_base + s;
+            x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
+            run_stage_window<RT, SMEM, JMAX, KMAX, WG, NT>(ca, G, x, S_hi, S_lo, n_acc, n_ties, rb);
+            if (ca.sweep_cost && gl == 0)
+                ca.sweep_cost[(long long)ci * ca.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * ca.inv_BU_d);
+        }
+        if (SMEM) {
+            group_sync(gid, WG);  // every warp's cells of the band are written
+            const int q4 = ca.band_pitch / 4;
+            for (int e = gl; e < ca.U * q4; e += 32 * WG) {
+                const int u = e / q4, q = e - u * q4;
+                *reinterpret_cast<float4*>(gres + (long long)u * ca.pitch + ca.band_lo + 4 * q) =
+                    *reinterpret_cast<const float4*>(rs + (long long)u * ca.band_pitch + 4 * q);
+            }
+        }
+        if (gl == 0) {
+            ca.S[ci] = (double)S_hi - (double)S_lo;
+            ca.accepted[ci] += n_acc;
+            if (NT) ca.ties[ci] += n_ties;
+        }
+        __threadfence();
+        group_sync(gid, WG);
+        if (gl == 0 && report_progress(a, c, s0)) st_release(&a.progress[c], s1);
+        return true;
+    };
+
     for (;;) {
         if (gl == 0) G.flags[0] = atomicAdd(a.task_counter, 1);
         group_sync(gid, WG);
@@ -652,88 +737,25 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
                 break;
             }
         }
-        float* gres = a.resid + (long long)c * a.resid_floats;
-        if (SMEM) {
-            // The band of every residual row into shared memory, one bulk copy
-            // per row spread over the group's lanes, all completing on one
-            // barrier phase; the group leaves together if the wait runs out.
-            const uint32_t row_bytes = (uint32_t)a.band_pitch * 4u;
-            fence_proxy_async_smem();    // earlier generic accesses to the band before the async-proxy writes
-            fence_proxy_async_global();  // the chain's residual as the previous task left it
-            if (gl == 0) {
-                G.flags[3] = 1;
-                mbar_arrive_expect_tx(G.bar, row_bytes * (uint32_t)a.U);
-            }
-            group_sync(gid, WG);
-            for (int u = gl; u < a.U; u += 32 * WG)
-                bulk_copy_g2s(rs + (long long)u * a.band_pitch, gres + (long long)u * a.pitch + a.band_lo, row_bytes,
-                              G.bar);
-            const bool landed = __all_sync(0xffffffffu, mbar_wait_bounded(G.bar, phase));
-            phase ^= 1u;
-            if (!landed && lane == 0) G.flags[3] = 0;
-            group_sync(gid, WG);
-            const int ok = G.flags[3];
-            group_sync(gid, WG);
-            if (!ok) {
-                if (gl == 0) raise_error(a.error, SATPILA_ERR_TIMEOUT);
-                break;
-            }
+        if constexpr (MULTI) {
+            const int2 m = a.chain_map[c];
+            const SatArgs ca = a.classes[m.x];
+            int rb[JMAX];
+            row_bases(ca, rb);
+            if (!run_task(ca, m.y, c, s0, s1, rb)) break;
+        } else {
+            if (!run_task(a, c, c, s0, s1, rowbase)) break;
         }
-        const double S = a.S[c];
-        float S_hi = (float)S;
-        float S_lo = -(float)(S - (double)S_hi);
-        unsigned long long n_acc = 0;
-        unsigned n_ties = 0;
-        StageCtx x;
-        x.M = a.moves;
-        x.D = a.D;
-        x.W = WG;
-        x.wig = wig;
-        x.lane = lane;
-        x.gid = gid;
-        x.gl = gl;
-        x.il = il;
-        x.R = SMEM ? rs : gres;
-        x.img = a.img + (long long)c * a.img_stride;
-        const ChainCtl* cc = a.ctl ? a.ctl + c : nullptr;
-        const int s_base = cc ? cc->stage0 : 0, s_total = cc ? cc->n_sweeps : a.n_sweeps_total;
-        const int sched = cc ? cc->schedule : a.schedule;
-        x.key = chain_key(cc ? cc->seed : a.seed + (unsigned long long)c);
-        x.tracing = a.trace != nullptr && c == a.trace_chain;
-        const double T0 = a.T0[c], TN = a.TN[c];
-        for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
-            x.s = s_base + s;
-            x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<RT, SMEM, JMAX, KMAX, WG, NT>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
-            if (a.sweep_cost && gl == 0)
-                a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
-        }
-        if (SMEM) {
-            group_sync(gid, WG);  // every warp's cells of the band are written
-            const int q4 = a.band_pitch / 4;
-            for (int e = gl; e < a.U * q4; e += 32 * WG) {
-                const int u = e / q4, q = e - u * q4;
-                *reinterpret_cast<float4*>(gres + (long long)u * a.pitch + a.band_lo + 4 * q) =
-                    *reinterpret_cast<const float4*>(rs + (long long)u * a.band_pitch + 4 * q);
-            }
-        }
-        if (gl == 0) {
-            a.S[c] = (double)S_hi - (double)S_lo;
-            a.accepted[c] += n_acc;
-            if (NT) a.ties[c] += n_ties;
-        }
-        __threadfence();
-        group_sync(gid, WG);
-        if (gl == 0 && report_progress(a, c, s0)) st_release(&a.progress[c], s1);
     }
 }
 
-template <int RT, int JMAX, int KMAX, int WG, bool NT, bool SMEM = false>
+template <int RT, int JMAX, int KMAX, int WG, bool NT, bool SMEM = false, bool MULTI = false>
 __global__ void __launch_bounds__(kSatMaxWarps * 32) sat_window_group_kernel(const SatArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = warp / WG;
-    window_group<RT, JMAX, KMAX, WG, NT, SMEM>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG, lane);
+    window_group<RT, JMAX, KMAX, WG, NT, SMEM, MULTI>(a, smem + (size_t)grp * a.group_smem_bytes, grp, warp % WG,
+                                                      lane);
 }
 
 }  // namespace satpila

@@ -13,6 +13,16 @@
 // ticks, and classes run on their own streams so their work overlaps.  PILA
 // tables are cached per geometry and dropped when unused and memory is needed.
 //
+// Classes whose tables the windowed group kernel takes (at most 512 angles,
+// K <= 8) are gathered into buckets, one per image size and table precision:
+// a bucket's tick is one sweep launch over the chains of all its classes
+// (each chain reading its own class's table, geometry and arrays), then each
+// class's resync.  So the many one-chain classes of a stream of mixed
+// geometries share launches and a few streams, instead of each holding a
+// stream whose long launches delay the others behind it in the device's
+// hardware queues.  Other classes (and all with SAT_SERVER_PER_CLASS) tick
+// on their own streams.
+//
 // A chain's result does not depend on what else is running: its random
 // stream is keyed by its own seed, its stages are numbered from its own
 // start, and its resyncs fall every stages_per_tick of its own stages.
@@ -128,8 +138,11 @@ struct Slot {
     double t_submit = 0.0, t_admit = 0.0;
 };
 
+struct Bucket;
+
 struct Class {
     Geometry* g = nullptr;
+    Bucket* bk = nullptr;  // the bucket whose launches run this class, or NULL (own stream and launches)
     int K = 1, M = 0;
     float beta = 1.0f;
     sat_params prm{};  // class-wide fields (K, beta, M, residency, group warps)
@@ -163,6 +176,32 @@ struct Class {
     double tick_ms = 0.0;
 };
 
+// Classes of one image size and table precision, run by one sweep launch
+// per window over all their chains (the windowed kernel on groups of 4 warps
+// reading each chain's class arguments).
+struct Bucket {
+    int n = 0, precision = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool in_flight = false;
+    std::vector<Class*> members;  // classes of the tick in flight
+    Plan pl;
+    int plan_chains = -1;
+    int cap_chains = 0, cap_classes = 0;
+    void* dev = nullptr;
+    size_t dev_bytes = 0;
+    int2* d_map = nullptr;         // [cap_chains] (class, chain in class)
+    int* d_progress = nullptr;     // [cap_chains]
+    SatArgs* d_classes = nullptr;  // [cap_classes]
+    int* d_counter = nullptr;      // [kMaxWindowsPerTick]
+    int* d_error = nullptr;
+    unsigned long long* d_stamps = nullptr;
+    int2* h_map = nullptr;
+    SatArgs* h_classes = nullptr;
+    size_t hb_map = 0, hb_classes = 0;
+    int windows = 1;
+};
+
 }  // namespace
 }  // namespace satpila
 
@@ -184,6 +223,7 @@ struct satpila_server {
     // engine-thread state
     std::list<std::unique_ptr<Geometry>> geoms;
     std::list<std::unique_ptr<Class>> classes;
+    std::list<std::unique_ptr<Bucket>> buckets;
     size_t bytes_in_use = 0;
     cudaStream_t build_stream = nullptr;
     cudaMemPool_t pool = nullptr;  // stream-ordered device memory of tables and classes
@@ -197,7 +237,12 @@ struct satpila_server {
     int grow(Class* c, int need);
     cudaError_t setup_chains(Class* c, int first, int count, std::vector<std::unique_ptr<Request>>& reqs);
     cudaError_t launch_tick(Class* c);
+    cudaError_t enqueue_results(Class* c, const int* d_error, const unsigned long long* d_stamps);
     cudaError_t finish_tick(Class* c);
+    Bucket* bucket_for(int n, int precision);
+    int bucket_reserve(Bucket* bk, int chains, int n_classes);
+    cudaError_t launch_bucket_tick(Bucket* bk);
+    void release_bucket(Bucket* bk);
     void release_class(Class* c);
     void fail_all(int code, const std::string& msg);
     size_t budget() const { return (size_t)cfg.mem_budget; }
@@ -250,10 +295,12 @@ Geometry* satpila_server::geometry_for(const Request& r, size_t budget_left) {
 
 Class* satpila_server::class_for(Geometry* g, const Request& r) {
     const int M = r.prm.moves_per_sweep > 0 ? r.prm.moves_per_sweep : g->p->n_mask;
+    const bool merged = !(cfg.flags & SAT_SERVER_PER_CLASS) && multi_table_ok(g->p, &r.prm);
     for (auto& c : classes)
         if (c->g == g && c->K == r.prm.bome_k && c->beta == r.prm.beta && c->M == M &&
             c->prm.residency == r.prm.residency && c->prm.group_warps == r.prm.group_warps &&
-            c->prm.pipeline_depth == r.prm.pipeline_depth)
+            c->prm.pipeline_depth == r.prm.pipeline_depth && (c->bk != nullptr) == merged &&
+            !(merged && c->in_flight))  // a bucket class in flight: a sibling class takes the request
             return c.get();
     auto c = std::make_unique<Class>();
     c->g = g;
@@ -265,12 +312,20 @@ Class* satpila_server::class_for(Geometry* g, const Request& r) {
     c->prm.trace = nullptr;
     c->prm.sweep_cost = nullptr;
     c->prm.trace_chain = -1;
-    if (choose_plan(g->p, 1, cfg.stages_per_tick, &c->prm, PLAN_RULES, &c->pl) != SATPILA_OK) return nullptr;
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        if (c->stream) cudaStreamDestroy(c->stream);
-        return nullptr;
+    if (merged) {
+        // the residual layout of the windowed group kernel (interleaved rows)
+        if (choose_plan(g->p, 1, cfg.stages_per_tick, &c->prm, PLAN_WINDOW_G4, &c->pl) != SATPILA_OK) return nullptr;
+        c->bk = bucket_for(g->p->n, g->p->precision);
+        if (!c->bk) return nullptr;
+        c->stream = c->bk->stream;
+    } else {
+        if (choose_plan(g->p, 1, cfg.stages_per_tick, &c->prm, PLAN_RULES, &c->pl) != SATPILA_OK) return nullptr;
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->stream) cudaStreamDestroy(c->stream);
+            return nullptr;
+        }
     }
     g->users++;
     classes.push_back(std::move(c));
@@ -397,8 +452,10 @@ void satpila_server::release_class(Class* c) {
     pinned.put(c->h_img, c->hb_img);
     for (auto& b : c->staging) pinned.put(b.first, b.second);
     c->staging.clear();
-    if (c->ev) cudaEventDestroy(c->ev);
-    if (c->stream) cudaStreamDestroy(c->stream);  // returns at once; queued work still completes
+    if (!c->bk) {
+        if (c->ev) cudaEventDestroy(c->ev);
+        if (c->stream) cudaStreamDestroy(c->stream);  // returns at once; queued work still completes
+    }
     bytes_in_use -= c->dev_bytes;
     c->g->users--;
     c->g->last_use = now_ms(t0);
@@ -533,26 +590,229 @@ cudaError_t satpila_server::launch_tick(Class* c) {
         where = c->exec ? "graph launch" : "direct launches";
         return e;
     }
-    // statistics of every chain, images of the finishing ones
-    const double* src[8] = {c->b.T0, c->b.TN, c->b.cost0, c->b.costF, c->b.S_inc, c->b.drift_max,
-                            (const double*)c->b.accepted, nullptr};
+    e = enqueue_results(c, c->b.error, c->d_stamps);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev, c->stream);
+    if (e == cudaSuccess) c->in_flight = true;
+    else where = "result copies";
+    return e;
+}
+
+// Statistics of every chain of c, the images of its finishing ones, the
+// tick's error word and time stamps, copied out behind the tick.
+cudaError_t satpila_server::enqueue_results(Class* c, const int* d_error, const unsigned long long* d_stamps) {
+    const int n = (int)c->slots.size();
+    const double* src[7] = {c->b.T0, c->b.TN, c->b.cost0, c->b.costF, c->b.S_inc, c->b.drift_max,
+                            (const double*)c->b.accepted};
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < 7 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(c->h_scal + (size_t)k * c->cap, src[k], (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->h_scal + (size_t)7 * c->cap, c->b.found, (size_t)n * 4, cudaMemcpyDeviceToHost,
                             c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_err, c->b.error, 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->h_stamps, c->d_stamps, 16, cudaMemcpyDeviceToHost, c->stream);
-    const size_t P = (size_t)p->n * p->n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_err, d_error, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_stamps, d_stamps, 16, cudaMemcpyDeviceToHost, c->stream);
+    const size_t P = (size_t)c->g->p->n * c->g->p->n;
     for (int i : c->finishing)
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(c->h_img + (size_t)i * P, c->b.img + (size_t)i * P, P * 4, cudaMemcpyDeviceToHost,
                                 c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev, c->stream);
-    if (e == cudaSuccess) c->in_flight = true;
-    else where = "result copies";
     return e;
+}
+
+// ---- buckets: one sweep launch over the classes of an image size -----------
+
+Bucket* satpila_server::bucket_for(int n, int precision) {
+    for (auto& b : buckets)
+        if (b->n == n && b->precision == precision) return b.get();
+    auto b = std::make_unique<Bucket>();
+    b->n = n;
+    b->precision = precision;
+    if (prepare_multi(precision) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (b->stream) cudaStreamDestroy(b->stream);
+        return nullptr;
+    }
+    buckets.push_back(std::move(b));
+    return buckets.back().get();
+}
+
+// Room for `chains` chains of `n_classes` classes in the bucket's arrays (the
+// bucket is between ticks, so nothing in flight reads the old ones).  These
+// few kilobytes of launch bookkeeping sit outside the memory budget, which
+// bounds tables and chain state: a tick never waits for them.
+int satpila_server::bucket_reserve(Bucket* bk, int chains, int n_classes) {
+    if (chains <= bk->cap_chains && n_classes <= bk->cap_classes) return SATPILA_OK;
+    const int cc = std::max(chains, std::max(16, bk->cap_chains * 2));
+    const int nc = std::max(n_classes, std::max(8, bk->cap_classes * 2));
+    const size_t off_prog = align_up((size_t)cc * sizeof(int2), 256);
+    const size_t off_cls = align_up(off_prog + (size_t)cc * 4, 256);
+    const size_t off_cnt = align_up(off_cls + (size_t)nc * sizeof(SatArgs), 256);
+    const size_t off_err = align_up(off_cnt + (size_t)kMaxWindowsPerTick * 4, 256);
+    const size_t off_st = off_err + 256;
+    const size_t bytes = off_st + 256;
+    void* dev = nullptr;
+    if (cudaMallocFromPoolAsync(&dev, bytes, pool, bk->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SATPILA_ERR_OOM;
+    }
+    const size_t hb_map = (size_t)cc * sizeof(int2), hb_classes = (size_t)nc * sizeof(SatArgs);
+    auto* h_map = (int2*)pinned.get(hb_map);
+    auto* h_classes = (SatArgs*)pinned.get(hb_classes);
+    if (!h_map || !h_classes) {
+        pinned.put(h_map, hb_map);
+        pinned.put(h_classes, hb_classes);
+        cudaFreeAsync(dev, bk->stream);
+        return SATPILA_ERR_OOM;
+    }
+    if (bk->dev) cudaFreeAsync(bk->dev, bk->stream);
+    pinned.put(bk->h_map, bk->hb_map);
+    pinned.put(bk->h_classes, bk->hb_classes);
+    char* base = (char*)dev;
+    bk->dev = dev;
+    bk->dev_bytes = bytes;
+    bk->cap_chains = cc;
+    bk->cap_classes = nc;
+    bk->d_map = (int2*)base;
+    bk->d_progress = (int*)(base + off_prog);
+    bk->d_classes = (SatArgs*)(base + off_cls);
+    bk->d_counter = (int*)(base + off_cnt);
+    bk->d_error = (int*)(base + off_err);
+    bk->d_stamps = (unsigned long long*)(base + off_st);
+    bk->h_map = h_map;
+    bk->h_classes = h_classes;
+    bk->hb_map = hb_map;
+    bk->hb_classes = hb_classes;
+    if (cudaMemsetAsync(dev, 0, bytes, bk->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SATPILA_ERR_CUDA;
+    }
+    return SATPILA_OK;
+}
+
+// A tick of every class of the bucket with chains: `windows` windows of
+// stages_per_tick stages, each one sweep launch over all their chains
+// followed by every class's resync, then each class's results.
+cudaError_t satpila_server::launch_bucket_tick(Bucket* bk) {
+    bk->members.clear();
+    int total = 0;
+    for (auto& c : classes)
+        if (c->bk == bk && !c->slots.empty()) {
+            bk->members.push_back(c.get());
+            total += (int)c->slots.size();
+        }
+    if (bk->members.empty()) return cudaSuccess;
+    const int w = cfg.stages_per_tick;
+    const int T = bk->windows;
+    const int nq = (int)bk->members.size();
+    if (bucket_reserve(bk, total, nq) != SATPILA_OK) {
+        where = std::string("bucket arrays: ") + satpila_last_error();
+        return cudaErrorMemoryAllocation;
+    }
+    if (bk->plan_chains != total) {
+        if (plan_multi(bk->precision, total, w, &bk->pl) != SATPILA_OK) {
+            where = std::string("plan: ") + satpila_last_error();
+            return cudaErrorInvalidValue;
+        }
+        bk->plan_chains = total;
+    }
+    int off = 0;
+    for (int q = 0; q < nq; ++q) {
+        Class* c = bk->members[q];
+        const int n = (int)c->slots.size();
+        int max_total = 0;
+        c->finishing.clear();
+        c->tick_windows = T;
+        for (int i = 0; i < n; ++i) {
+            c->h_ctl[i] = c->slots[i].ctl;
+            max_total = std::max(max_total, c->slots[i].ctl.n_sweeps);
+            if (c->slots[i].ctl.stage0 + w * T >= c->slots[i].ctl.n_sweeps) c->finishing.push_back(i);
+            bk->h_map[off + i] = make_int2(q, i);
+        }
+        SatArgs ca = sweep_args(c->g->p, c->pl, c->b, &c->prm, n, c->M, max_total, 0, w, nullptr);
+        ca.stage_bytes = bk->pl.stage_bytes;
+        ca.D = bk->pl.D;
+        ca.W = bk->pl.W;
+        ca.group_smem_bytes = bk->pl.group_smem;
+        ca.classes = nullptr;
+        ca.chain_map = nullptr;
+        bk->h_classes[q] = ca;
+        off += n;
+    }
+    cudaStream_t q = bk->stream;
+    cudaError_t e = cudaSuccess;
+    for (Class* c : bk->members)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_ctl, c->h_ctl, c->slots.size() * sizeof(ChainCtl), cudaMemcpyHostToDevice, q);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bk->d_classes, bk->h_classes, (size_t)nq * sizeof(SatArgs), cudaMemcpyHostToDevice, q);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bk->d_map, bk->h_map, (size_t)total * sizeof(int2), cudaMemcpyHostToDevice, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bk->d_progress, 0, (size_t)total * 4, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bk->d_counter, 0, (size_t)T * 4, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bk->d_error, 0, 4, q);
+    if (e == cudaSuccess) {
+        tick_stamp_kernel<<<1, 1, 0, q>>>(bk->d_stamps);
+        e = cudaGetLastError();
+    }
+    const int spt = bk->pl.spt;
+    for (int t = 0; t < T && e == cudaSuccess; ++t) {
+        SatArgs la = bk->h_classes[0];
+        la.classes = bk->d_classes;
+        la.chain_map = bk->d_map;
+        la.n_chains = total;
+        la.progress = bk->d_progress;
+        la.error = bk->d_error;
+        la.claim = nullptr;
+        la.ctl = nullptr;
+        la.trace = nullptr;
+        la.sweep_cost = nullptr;
+        la.stall_chain = -1;
+        la.sweep_begin = t * w;
+        la.sweep_end = (t + 1) * w;
+        la.sweeps_per_task = spt;
+        la.n_tasks = total * ((w + spt - 1) / spt);
+        la.task_counter = bk->d_counter + t;
+        e = enqueue_sweep_multi(bk->precision, bk->pl, la, q);
+        for (Class* c : bk->members) {
+            const int n = (int)c->slots.size();
+            if (e == cudaSuccess) {
+                s_inc_kernel<<<(n + 127) / 128, 128, 0, q>>>(c->b.S_inc, c->b.S, c->d_ctl, n, t * w);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = enqueue_resync(c->g->p, c->pl, c->b, 0, n, true, c->b.costF, q);
+        }
+    }
+    if (e == cudaSuccess) {
+        tick_stamp_kernel<<<1, 1, 0, q>>>(bk->d_stamps + 1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        where = "bucket launches";
+        return e;
+    }
+    for (Class* c : bk->members)
+        if (e == cudaSuccess) e = enqueue_results(c, bk->d_error, bk->d_stamps);
+    if (e == cudaSuccess) e = cudaEventRecord(bk->ev, q);
+    if (e != cudaSuccess) {
+        where = "result copies";
+        return e;
+    }
+    bk->in_flight = true;
+    for (Class* c : bk->members) c->in_flight = true;
+    return cudaSuccess;
+}
+
+void satpila_server::release_bucket(Bucket* bk) {
+    if (bk->in_flight) cudaEventSynchronize(bk->ev);
+    if (bk->dev) cudaFreeAsync(bk->dev, bk->stream);
+    cudaStreamSynchronize(bk->stream);
+    pinned.put(bk->h_map, bk->hb_map);
+    pinned.put(bk->h_classes, bk->hb_classes);
+    if (bk->ev) cudaEventDestroy(bk->ev);
+    if (bk->stream) cudaStreamDestroy(bk->stream);
+    cudaGetLastError();
 }
 
 cudaError_t satpila_server::finish_tick(Class* c) {
@@ -782,7 +1042,7 @@ void satpila_server::run() {
         // 2. every class with chains and no tick in flight launches one (a
         //    chain with no stages left finishes with it)
         for (auto& c : classes) {
-            if (c->in_flight || c->slots.empty()) continue;
+            if (c->bk || c->in_flight || c->slots.empty()) continue;
             cudaError_t e = launch_tick(c.get());
             if (e != cudaSuccess) {
                 fail_all(SATPILA_ERR_CUDA, std::string("sat_server: tick launch (") + where + "): " + cudaGetErrorString(e));
@@ -792,9 +1052,47 @@ void satpila_server::run() {
             worked = true;
         }
         if (failed) break;
+        for (auto& b : buckets) {
+            if (b->in_flight) continue;
+            cudaError_t e = launch_bucket_tick(b.get());
+            if (e != cudaSuccess) {
+                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: tick launch (") + where + "): " + cudaGetErrorString(e));
+                failed = true;
+                break;
+            }
+            if (b->in_flight) worked = true;
+        }
+        if (failed) break;
         // 3. retire finished ticks
+        for (auto& b : buckets) {
+            if (!b->in_flight) continue;
+            const cudaError_t q = cudaEventQuery(b->ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                fail_all(SATPILA_ERR_CUDA, std::string("sat_server: tick: ") + cudaGetErrorString(q));
+                failed = true;
+                break;
+            }
+            b->in_flight = false;
+            double tick_ms = 0.0;
+            for (Class* c : b->members) {
+                cudaError_t e = finish_tick(c);
+                tick_ms = std::max(tick_ms, c->tick_ms);
+                if (e != cudaSuccess) {
+                    fail_all(SATPILA_ERR_CUDA, std::string("sat_server: retiring: ") + cudaGetErrorString(e));
+                    failed = true;
+                    break;
+                }
+            }
+            if (failed) break;
+            if (tick_ms < 0.5 * kTickTargetMs && b->windows < kMaxWindowsPerTick) b->windows *= 2;
+            else if (tick_ms > 4.0 * kTickTargetMs && b->windows > 1) b->windows /= 2;
+            b->members.clear();
+            worked = true;
+        }
+        if (failed) break;
         for (auto& c : classes) {
-            if (!c->in_flight) continue;
+            if (c->bk || !c->in_flight) continue;
             const cudaError_t q = cudaEventQuery(c->ev);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) {
@@ -839,11 +1137,15 @@ void satpila_server::run() {
     }
     // shutdown: every class and table back, then wait for this server's
     // device work before its host blocks go
+    for (auto& b : buckets)
+        if (b->in_flight) cudaEventSynchronize(b->ev);
     for (auto& c : classes) {
-        if (c->in_flight) cudaEventSynchronize(c->ev);
+        if (!c->bk && c->in_flight) cudaEventSynchronize(c->ev);
         release_class(c.get());
     }
     classes.clear();
+    for (auto& b : buckets) release_bucket(b.get());
+    buckets.clear();
     for (auto& g : geoms) {
         for (cudaEvent_t ev : g->released) {
             cudaStreamWaitEvent(build_stream, ev, 0);
@@ -929,8 +1231,8 @@ extern "C" int sat_server_submit(satpila_server* s, const sat_request* r, uint64
         return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: unknown precision");
     if (r->precision != PILA_F32 && r->n_bins > 32767)
         return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: too many bins for 16-bit indices");
-    if (r->precision == PILA_U8 && r->n_angles > 128)
-        return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: one-byte tables take at most 128 angles");
+    if (r->precision == PILA_U8 && r->n_angles > 512)
+        return fail(SATPILA_ERR_INVALID_ARG, "sat_server_submit: one-byte tables take at most 512 angles");
     if (prm.bome_k < 1 || prm.bome_k > kMaxK || !(prm.beta > 0.0f) || prm.n_sweeps < 0 || prm.moves_per_sweep < 0 ||
         prm.schedule < SAT_SCHED_LINEAR || prm.schedule > SAT_SCHED_CUBIC || prm.residency < SAT_RESIDENT_AUTO ||
         prm.residency > SAT_RESIDENT_GLOBAL)

@@ -70,6 +70,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.SatParams) == 96
     assert C.sizeof(_lib.PilaGeom) == 32
     assert C.sizeof(_lib.SatStats) == 88
+    assert C.sizeof(_lib.SatServerCfg) == 32
 
 
 def header_constants():

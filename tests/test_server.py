@@ -2,7 +2,10 @@
 
 A request's result must be the same whether it runs alone or in a mix of
 other requests of other sizes admitted while it runs, and the same as
-sat_run on that one chain with resync_every = stages_per_tick."""
+sat_run on that one chain with resync_every = stages_per_tick: with the
+windowed 4-warp group layout when its image size's classes share launches
+(the default), with sat_run's size rules when every class runs its own
+(SAT_SERVER_PER_CLASS)."""
 import time
 
 import numpy as np
@@ -32,10 +35,21 @@ def api():
 TICK = 3
 
 
+@pytest.fixture(params=["shared", "per_class"])
+def mode(request, api):
+    """Server flags of the two launch layouts, and the sat_run plan each matches."""
+    if request.param == "shared":
+        return dict(flags=0, plan=api.SAT_PLAN_WINDOW_G4)
+    return dict(flags=api.SAT_SERVER_PER_CLASS, plan=api.SAT_PLAN_RULES)
+
+
 def _requests():
-    """Mixed sizes, precisions, K and schedule lengths (one with no stages)."""
+    """Mixed sizes, precisions, K and schedule lengths (one with no stages);
+    sizes 48 and 64 each with two angle counts, so one launch carries
+    several tables."""
     shapes = [(32, 24, 0, None, 1, 7), (48, 40, 1, "disk", 4, 5), (64, 60, 0, "disk", 8, 4), (48, 40, 1, "disk", 4, 9),
-              (32, 24, 0, None, 1, 0), (40, 30, 1, "disk", 4, 6), (64, 60, 0, "disk", 8, 2), (32, 24, 0, None, 1, 3)]
+              (32, 24, 0, None, 1, 0), (40, 30, 1, "disk", 4, 6), (64, 60, 0, "disk", 8, 2), (32, 24, 0, None, 1, 3),
+              (48, 30, 1, "disk", 8, 5), (64, 44, 0, "disk", 1, 4)]
     reqs = []
     for i, (n, U, prec, m, K, S) in enumerate(shapes):
         B = synth.bins_for(n)
@@ -47,19 +61,19 @@ def _requests():
     return reqs
 
 
-def _run_alone(api, reqs):
+def _run_alone(api, reqs, flags=0):
     out = []
-    with api.Server(stages_per_tick=TICK) as srv:
+    with api.Server(stages_per_tick=TICK, flags=flags) as srv:
         for r in reqs:
             t = srv.submit(**r)
             out.append(srv.wait(t, 60000))
     return out
 
 
-def test_server_same_alone_and_in_mix(api):
+def test_server_same_alone_and_in_mix(api, mode):
     reqs = _requests()
-    alone = _run_alone(api, reqs)
-    with api.Server(stages_per_tick=TICK) as srv:
+    alone = _run_alone(api, reqs, mode["flags"])
+    with api.Server(stages_per_tick=TICK, flags=mode["flags"]) as srv:
         # a first wave, then a second submitted while the first runs
         tickets = [srv.submit(**r) for r in reqs[:4]]
         first = srv.wait(tickets[0], 60000)
@@ -74,10 +88,10 @@ def test_server_same_alone_and_in_mix(api):
         assert sm["proposed"] == r["n_sweeps"] * (int(r["mask"].sum()) if r["mask"] is not None else r["n"] ** 2)
 
 
-def test_server_matches_sat_run(api):
+def test_server_matches_sat_run(api, mode):
     """Each request is sat_run on one chain with resync_every = stages_per_tick."""
     reqs = _requests()
-    with api.Server(stages_per_tick=TICK) as srv:
+    with api.Server(stages_per_tick=TICK, flags=mode["flags"]) as srv:
         tickets = [srv.submit(**r) for r in reqs]
         got = [srv.wait(t, 60000) for t in tickets]
     for (img, st), r in zip(got, reqs):
@@ -87,7 +101,8 @@ def test_server_matches_sat_run(api):
         init = synth.initial_image(n, 0.5, r["mask"]).astype(np.float32)[None]
         ref = torch.tensor(init, device="cuda")
         kw = {k: v for k, v in r.items() if k not in ("sino", "n", "precision", "mask")}
-        s1 = api.sat_run(p, torch.tensor(r["sino"][None], device="cuda"), ref, resync_every=TICK, **kw)
+        s1 = api.sat_run(p, torch.tensor(r["sino"][None], device="cuda"), ref, resync_every=TICK, plan=mode["plan"],
+                         **kw)
         api.pila_free(p)
         assert np.array_equal(ref.cpu().numpy()[0], img)
         assert s1[0]["accepted"] == st["accepted"] and s1[0]["t0"] == st["t0"]
@@ -165,7 +180,7 @@ def test_served_chain_follows_oracle(api):
     ref = torch.tensor(img0[None], device="cuda")
     trace = torch.zeros(S * M * api.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     s1 = api.sat_run(p, torch.tensor(pm[None], device="cuda"), ref, bome_k=K, n_sweeps=S, seed=4242, t0=-1.0,
-                     tn=-1.0, resync_every=TICK, trace_chain=0, trace=trace)
+                     tn=-1.0, resync_every=TICK, trace_chain=0, trace=trace, plan=api.SAT_PLAN_WINDOW_G4)
     api.pila_free(p)
     assert np.array_equal(ref.cpu().numpy()[0], img)
     assert s1[0]["accepted"] == st["accepted"] and s1[0]["t0"] == st["t0"]
@@ -178,3 +193,33 @@ def test_served_chain_follows_oracle(api):
     assert rep["pixel_mismatch"] == -1 and rep["hard_mismatch"] == -1, rep
     assert rep["max_err_dS"] <= 1e-5 and rep["max_err_f"] <= 1e-5, rep
     assert rep["near_ties"] <= 1e-3 * S * M, rep
+
+
+def test_server_wide_tables_share_a_launch(api):
+    """Tables of 200-400 angles (all three precisions) served together in one
+    image size's launch: the records of a lane's second chunk pair are real
+    angles here.  Each result equals sat_run's with the 4-warp group layout."""
+    n = 64
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    shapes = [(300, api.PILA_F16, 4), (200, api.PILA_U8, 8), (400, api.PILA_F32, 1), (300, api.PILA_F16, 8)]
+    reqs = []
+    for i, (U, prec, K) in enumerate(shapes):
+        ph = synth.phantom(n, 6, 700 + i) * mask
+        sino = oracle.drt(ph, U, B).astype(np.float32)
+        reqs.append(dict(sino=sino, n=n, precision=prec, mask=mask, bome_k=K, n_sweeps=4, seed=1300 + i,
+                         t0=-1.0, tn=-1.0))
+    with api.Server(stages_per_tick=2) as srv:
+        tickets = [srv.submit(**r) for r in reqs]
+        got = [srv.wait(t, 120000) for t in tickets]
+    for (img, st), r in zip(got, reqs):
+        assert st["status"] == 0
+        U = r["sino"].shape[0]
+        p = api.pila_build(n, U, B, r["precision"], mask=mask)
+        ref = torch.tensor(synth.initial_image(n, 0.5, mask).astype(np.float32)[None], device="cuda")
+        kw = {k: v for k, v in r.items() if k not in ("sino", "n", "precision", "mask")}
+        s1 = api.sat_run(p, torch.tensor(r["sino"][None], device="cuda"), ref, resync_every=2,
+                         plan=api.SAT_PLAN_WINDOW_G4, **kw)
+        api.pila_free(p)
+        assert np.array_equal(ref.cpu().numpy()[0], img)
+        assert s1[0]["accepted"] == st["accepted"] and s1[0]["t0"] == st["t0"]
