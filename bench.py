@@ -944,8 +944,9 @@ def run_rows(args):
       a9 SIRT, simultaneous: per iteration the table read twice (forward and
          back projection) plus the sinogram, the factor matrix, the correction
          and the image;
-      one 256^2 chain (K = 8): a single chain is sequential, so it is reported
-         as time per stage and moves/s."""
+      one 256^2 chain (K = 8) and one 512^2 chain (360 angles, K = 8, FP16
+         table): a single chain is sequential, so each is reported as time per
+         stage (a sweep of every reconstruction-space pixel) and moves/s."""
     import torch
 
     from paper_1411_4622_gb300 import api
@@ -1031,12 +1032,34 @@ def run_rows(args):
              "launch": launch_name(st[0]["plan"], kw["flags"]), "bome_k": cfg["bome_k"], "pila": "f16"}
     api.pila_free(p)
     api.pila_free(pf)
+    # one chain of the 512^2 configuration (the 4-warp windowed layout: the
+    # autotuner's pick for one chain of this table)
+    c4 = synth.WORKLOADS["precision512"]
+    n4, U4, B4, K4 = c4["n"], c4["n_angles"], c4["n_bins"], c4["bome_k"]
+    mask4 = synth.disk_mask(n4)
+    ph4 = synth.phantom(n4, c4["ellipses"], synth.slice_seeds(0)[0]) * mask4
+    pf4 = api.pila_build(n4, U4, B4, api.PILA_F32, mask=mask4)
+    clean4 = api.pila_forward(pf4, torch.tensor(ph4[None], dtype=torch.float32, device="cuda")).cpu().numpy()[0]
+    sino4 = torch.tensor(synth.poisson_noise(clean4, c4["noise"][1], synth.slice_seeds(0)[1])[None],
+                         dtype=torch.float32, device="cuda").contiguous()
+    api.pila_free(pf4)
+    p4 = api.pila_build(n4, U4, B4, api.PILA_F16, mask=mask4)
+    st4 = api.sat_run(p4, sino4, torch.tensor(synth.initial_image(n4, 0.5, mask4)[None], dtype=torch.float32,
+                                              device="cuda"),
+                      bome_k=K4, n_sweeps=2, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2], resync_every=1,
+                      plan=api.SAT_PLAN_WINDOW_G4)
+    api.pila_free(p4)
+    M4 = int(mask4.sum())
+    chain512 = {"stages": 2, "moves_per_stage": M4, "sweep_ms": st4[0]["sweep_ms"],
+                "ms_per_stage": st4[0]["sweep_ms"] / 2, "moves_per_s": 2 * M4 / (st4[0]["sweep_ms"] / 1e3),
+                "us_per_move": st4[0]["sweep_ms"] * 1e3 / (2 * M4), "launch": launch_name(st4[0]["plan"], 0, 8),
+                "bome_k": K4, "pila": "f16", "resync_every": 1}
     out = {"metric": "SIRT-PILA iterations/s, 256x256 slice (180 angles, FP32 table)", "value": sirt["FP32"],
            "unit": "iterations/s", "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": 1e3 / sirt["FP32"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "rows", "l2": "flushed before each timed call (256 MB write)",
                       "peak_kind": peak_kind},
-           "rows": rows, "chain256": chain}
+           "rows": rows, "chain256": chain, "chain512": chain512}
     print(json.dumps(out))
 
 
