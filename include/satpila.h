@@ -262,6 +262,21 @@ typedef struct {
 int sat_run(const satpila_pila* p, int32_t n_chains, const float* sino_meas, float* images,
             const sat_params* prm, sat_stats* stats, void* stream);
 
+/*
+ * sat_run over chains given one buffer each: sino_meas[c] ([U][B]) and
+ * images[c] ([n][n], annealed in place) for c < n_chains, each host or device
+ * memory independently (the arrays of pointers are host memory).  The chains
+ * are copied into one contiguous device batch on `stream`, annealed exactly as
+ * sat_run anneals that batch (same results, bit for bit), and the images copied
+ * back on `stream`.  The batch is allocated stream-ordered and freed after the
+ * copies back.  With stats (host, n_chains entries) the call synchronizes
+ * `stream` before it returns; without, and with device buffers only, it returns
+ * once the work is enqueued.  The caller owns every buffer.
+ * Errors: INVALID_ARG (a null pointer), OOM, CUDA; otherwise sat_run's.
+ */
+int sat_run_ptrs(const satpila_pila* p, int32_t n_chains, const float* const* sino_meas, float* const* images,
+                 const sat_params* prm, sat_stats* stats, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of annealing requests (no counterpart in the  */
 /* paper, which reconstructs one slice at a time; each request runs Steps 1-4 */

@@ -30,7 +30,7 @@ SAT_SERVER_PER_CLASS = 1
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["satpila_last_error", "satpila_version", "pila_build", "pila_free", "pila_info", "pila_export",
-           "pila_forward", "pila_sirt_factor", "sat_run", "sat_server_create", "sat_server_submit", "sat_server_poll",
+           "pila_forward", "pila_sirt_factor", "sat_run", "sat_run_ptrs", "sat_server_create", "sat_server_submit", "sat_server_poll",
            "sat_server_wait", "sat_server_info", "sat_server_destroy", "drt_bilinear", "sat_drt_run", "fbp", "fbp_prior", "sirt_run",
            "sirt_run_noalloc", "satpila_probe_read", "satpila_probe_smem"]
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -119,6 +119,7 @@ def load():
         lib.pila_forward.argtypes = [V, C.c_int32, V, V, V]
         lib.pila_sirt_factor.argtypes = [V, V, V]
         lib.sat_run.argtypes = [V, C.c_int32, V, V, C.POINTER(SatParams), V, V]
+        lib.sat_run_ptrs.argtypes = [V, C.c_int32, V, V, C.POINTER(SatParams), V, V]
         lib.sat_server_create.argtypes = [C.POINTER(SatServerCfg), C.POINTER(V)]
         lib.sat_server_submit.argtypes = [V, C.POINTER(SatRequest), C.POINTER(C.c_uint64)]
         lib.sat_server_poll.argtypes = [V, C.c_uint64, V, C.POINTER(SatResult)]

@@ -169,6 +169,24 @@ def sat_run(p: Pila, sino_meas, images, stream=None, sync=True, **kw) -> list[di
     return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
 
 
+def sat_run_ptrs(p: Pila, sinos, images, stream=None, sync=True, **kw) -> list[dict] | None:
+    """sat_run over chains given one buffer each: sinos[c] float32 [U, B] and
+    images[c] float32 [n, n] (annealed in place), tensors or arrays, host or
+    device; the same results as sat_run on the stacked batch."""
+    if len(sinos) != len(images):
+        raise ValueError("one sinogram per image")
+    n_chains = len(images)
+    sp = (C.c_void_p * max(n_chains, 1))(*[_ptr(x, np.float32) for x in sinos])
+    ip = (C.c_void_p * max(n_chains, 1))(*[_ptr(x, np.float32) for x in images])
+    prm = sat_params(**kw)
+    stats = (L.SatStats * max(n_chains, 1))() if sync else None
+    L.check(L.load().sat_run_ptrs(p.handle, n_chains, sp, ip, C.byref(prm),
+                                  C.cast(stats, C.c_void_p) if sync else None, _stream(stream)))
+    if not sync:
+        return None
+    return [{f: getattr(s, f) for f, _ in L.SatStats._fields_} for s in stats[:n_chains]]
+
+
 def drt_bilinear(images, n_angles, n_bins, stream=None):
     """Bilinear-interpolation DRT (Sec. III-A's conventional forward model) of
     device images [items, n, n] -> float32 [items, U, B] tensor."""

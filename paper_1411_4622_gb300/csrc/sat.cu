@@ -1329,3 +1329,43 @@ extern "C" int sat_run(const satpila_pila* p, int32_t n_chains, const float* sin
     if (err_code != 0) return fail(err_code, "sat_run: a device-side check failed");
     return SATPILA_OK;
 }
+
+// sat_run over chains given one buffer each: the chains are gathered into
+// one contiguous device batch (stream-ordered copies), annealed by sat_run,
+// and the images scattered back, all on `stream`.
+extern "C" int sat_run_ptrs(const satpila_pila* p, int32_t n_chains, const float* const* sino_meas,
+                            float* const* images, const sat_params* prm, sat_stats* stats, void* stream) {
+    if (!p || !prm || n_chains < 0) return fail(SATPILA_ERR_INVALID_ARG, "sat_run_ptrs: bad argument");
+    if (n_chains == 0) return SATPILA_OK;
+    if (!sino_meas || !images) return fail(SATPILA_ERR_INVALID_ARG, "sat_run_ptrs: null pointer array");
+    for (int32_t c = 0; c < n_chains; ++c)
+        if (!sino_meas[c] || !images[c]) return fail(SATPILA_ERR_INVALID_ARG, "sat_run_ptrs: null chain buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = (size_t)p->n * p->n, cells = (size_t)p->U * p->B;
+    float* d_sino = nullptr;
+    float* d_img = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_sino, (size_t)n_chains * cells * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_img, (size_t)n_chains * P * sizeof(float), s);
+    for (int32_t c = 0; c < n_chains && e == cudaSuccess; ++c) {
+        e = cudaMemcpyAsync(d_sino + (size_t)c * cells, sino_meas[c], cells * sizeof(float), cudaMemcpyDefault, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_img + (size_t)c * P, images[c], P * sizeof(float), cudaMemcpyDefault, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (d_sino) cudaFreeAsync(d_sino, s);
+        if (d_img) cudaFreeAsync(d_img, s);
+        return e == cudaErrorMemoryAllocation ? fail(SATPILA_ERR_OOM, "sat_run_ptrs: batch buffers")
+                                              : cuda_fail(e, "sat_run_ptrs: gathering the chains");
+    }
+    const int rc = sat_run(p, n_chains, d_sino, d_img, prm, stats, stream);
+    // the images go back whatever sat_run reported (a device-side timeout
+    // still leaves every chain's image at a stage boundary)
+    for (int32_t c = 0; c < n_chains && e == cudaSuccess; ++c)
+        e = cudaMemcpyAsync(images[c], d_img + (size_t)c * P, P * sizeof(float), cudaMemcpyDefault, s);
+    cudaFreeAsync(d_sino, s);
+    cudaFreeAsync(d_img, s);
+    if (e == cudaSuccess && stats) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sat_run_ptrs: returning the images");
+    return rc;
+}

@@ -53,6 +53,7 @@ def test_host_side_argument_checks(lib):
     assert lib.pila_build(C.byref(g), _lib.PILA_F16, None, C.byref(out)) == _lib.ERR_INVALID_ARG
     prm = _lib.SatParams()
     assert lib.sat_run(None, 1, None, None, C.byref(prm), None, None) == _lib.ERR_INVALID_ARG
+    assert lib.sat_run_ptrs(None, 1, None, None, C.byref(prm), None, None) == _lib.ERR_INVALID_ARG
     sp = _lib.SirtParams(1, 5, 1.0, 0)
     assert lib.sirt_run(None, 1, None, None, C.byref(sp), None, None) == _lib.ERR_INVALID_ARG
     assert lib.pila_free(None) == 0

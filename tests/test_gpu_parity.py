@@ -971,6 +971,43 @@ def test_sat_run_asynchronous_without_stats(api):
     api.pila_free(p)
 
 
+def test_sat_run_ptrs_matches_the_stacked_batch(api):
+    """sat_run_ptrs over one buffer per chain (separate device tensors and a
+    host array, mixed) gives sat_run's results on the stacked batch, bit for
+    bit, and without stats it is asynchronous for device buffers."""
+    n, U = 48, 40
+    B = synth.bins_for(n)
+    mask = synth.disk_mask(n)
+    C = 3
+    sinos = np.stack([oracle.drt(synth.phantom(n, 6, 80 + i) * mask, U, B) for i in range(C)]).astype(np.float32)
+    img0 = np.stack([synth.initial_image(n, 0.5, mask)] * C).astype(np.float32)
+    p = api.pila_build(n, U, B, api.PILA_F16, mask=mask)
+    kw = dict(bome_k=4, n_sweeps=4, t0=-1.0, tn=-1.0, resync_every=2, seed=31)
+    ref = dev(img0)
+    s_ref = api.sat_run(p, dev(sinos), ref, **kw)
+    ref = ref.cpu().numpy()
+    imgs = [dev(img0[0]), img0[1].copy(), dev(img0[2])]
+    ins = [dev(sinos[0]), sinos[1].copy(), dev(sinos[2])]
+    st = api.sat_run_ptrs(p, ins, imgs, **kw)
+    for c in range(C):
+        got = imgs[c].cpu().numpy() if hasattr(imgs[c], "cpu") else imgs[c]
+        assert np.array_equal(got, ref[c]), c
+        assert st[c]["accepted"] == s_ref[c]["accepted"] and st[c]["final_cost"] == s_ref[c]["final_cost"]
+        assert st[c]["plan"] == s_ref[c]["plan"]
+    # device buffers, no stats: enqueued on the stream, the same images
+    dimgs = [dev(img0[c]) for c in range(C)]
+    dins = [dev(sinos[c]) for c in range(C)]
+    s1 = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    assert api.sat_run_ptrs(p, dins, dimgs, stream=s1, sync=False, **kw) is None
+    s1.synchronize()
+    for c in range(C):
+        assert np.array_equal(dimgs[c].cpu().numpy(), ref[c]), c
+    with pytest.raises(api.SatpilaError):
+        api.sat_run_ptrs(p, dins, dimgs[:2] + [None], **kw)
+    api.pila_free(p)
+
+
 def test_autotune_picks_a_layout_and_is_repeatable(api):
     """SAT_FLAG_AUTOTUNE times the launch layouts once per shape: the chosen
     layout is reported, a second call reuses it with identical results, and
