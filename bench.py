@@ -62,7 +62,8 @@ def parse():
                     help="SAT_PLAN_* launch layout of the batched run (default 1, the windowed kernel with its "
                          "residual band in shared memory: the autotuner's pick for this shape); 0: rules/autotuner")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "precision512", "precision512-rmse", "serve", "bome", "drt", "fbp", "rows"],
+                    choices=[WORKLOAD, "precision512", "precision512-rmse", "serve", "bome", "drt", "fbp", "rows",
+                             "chain512"],
                     help="batch128x512 (default); precision512: 512^2 gather throughput; serve: request stream; "
                          "bome: convergence vs estimates, equal evaluations and schedules (Sec. III-B, III-C); "
                          "drt: speed of SAT with the PILA against SAT with a full DRT per move (Sec. III-A); "
@@ -1032,8 +1033,22 @@ def run_rows(args):
              "launch": launch_name(st[0]["plan"], kw["flags"]), "bome_k": cfg["bome_k"], "pila": "f16"}
     api.pila_free(p)
     api.pila_free(pf)
-    # one chain of the 512^2 configuration (the 4-warp windowed layout: the
-    # autotuner's pick for one chain of this table)
+    chain512 = single_chain_512(api, stages=2)
+    out = {"metric": "SIRT-PILA iterations/s, 256x256 slice (180 angles, FP32 table)", "value": sirt["FP32"],
+           "unit": "iterations/s", "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": 1e3 / sirt["FP32"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "rows", "l2": "flushed before each timed call (256 MB write)",
+                      "peak_kind": peak_kind},
+           "rows": rows, "chain256": chain, "chain512": chain512}
+    print(json.dumps(out))
+
+
+def single_chain_512(api, stages):
+    """One chain of the 512^2 configuration (360 angles, K = 8, FP16 table,
+    Poisson noise, resync every stage) on the 4-warp windowed layout, the
+    autotuner's pick for one chain of this table: time per stage."""
+    import torch
+
     c4 = synth.WORKLOADS["precision512"]
     n4, U4, B4, K4 = c4["n"], c4["n_angles"], c4["n_bins"], c4["bome_k"]
     mask4 = synth.disk_mask(n4)
@@ -1046,20 +1061,31 @@ def run_rows(args):
     p4 = api.pila_build(n4, U4, B4, api.PILA_F16, mask=mask4)
     st4 = api.sat_run(p4, sino4, torch.tensor(synth.initial_image(n4, 0.5, mask4)[None], dtype=torch.float32,
                                               device="cuda"),
-                      bome_k=K4, n_sweeps=2, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2], resync_every=1,
+                      bome_k=K4, n_sweeps=stages, t0=-1.0, tn=-1.0, seed=synth.slice_seeds(0)[2], resync_every=1,
                       plan=api.SAT_PLAN_WINDOW_G4)
     api.pila_free(p4)
     M4 = int(mask4.sum())
-    chain512 = {"stages": 2, "moves_per_stage": M4, "sweep_ms": st4[0]["sweep_ms"],
-                "ms_per_stage": st4[0]["sweep_ms"] / 2, "moves_per_s": 2 * M4 / (st4[0]["sweep_ms"] / 1e3),
-                "us_per_move": st4[0]["sweep_ms"] * 1e3 / (2 * M4), "launch": launch_name(st4[0]["plan"], 0, 8),
-                "bome_k": K4, "pila": "f16", "resync_every": 1}
-    out = {"metric": "SIRT-PILA iterations/s, 256x256 slice (180 angles, FP32 table)", "value": sirt["FP32"],
-           "unit": "iterations/s", "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": 1e3 / sirt["FP32"],
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "rows", "l2": "flushed before each timed call (256 MB write)",
-                      "peak_kind": peak_kind},
-           "rows": rows, "chain256": chain, "chain512": chain512}
+    return {"stages": stages, "moves_per_stage": M4, "sweep_ms": st4[0]["sweep_ms"],
+            "ms_per_stage": st4[0]["sweep_ms"] / stages, "moves_per_s": stages * M4 / (st4[0]["sweep_ms"] / 1e3),
+            "us_per_move": st4[0]["sweep_ms"] * 1e3 / (stages * M4), "launch": launch_name(st4[0]["plan"], 0, 8),
+            "bome_k": K4, "pila": "f16", "resync_every": 1}
+
+
+def run_chain512(args):
+    """--workload chain512: one chain of the 512^2 configuration alone (a single
+    chain is sequential: reported as time per stage); one JSON line."""
+    import torch
+
+    from paper_1411_4622_gb300 import api
+    from paper_1411_4622_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    c = single_chain_512(api, stages=args.sweeps or 2)
+    out = {"metric": "SAT ms per stage, one 512x512 chain (360 angles, K = 8)", "value": c["ms_per_stage"],
+           "unit": "ms/stage", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": c["sweep_ms"],
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "chain512"}, "chain512": c}
     print(json.dumps(out))
 
 
@@ -1121,8 +1147,9 @@ def run_fbp(args):
 def main():
     args = parse()
     # one hardware work queue per stream for up to 32 streams (the serving
-    # engine runs each class on its own stream); read when the CUDA context is
-    # created, so set before the first CUDA call
+    # engine runs each image size's shared launches, and any class outside
+    # them, on a stream of its own); read when the CUDA context is created,
+    # so set before the first CUDA call
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.workload == "precision512":
         return run_precision(args)
@@ -1130,6 +1157,8 @@ def main():
         return run_precision_rmse(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "chain512":
+        return run_chain512(args)
     if args.workload == "bome":
         return run_bome(args)
     if args.workload == "drt":
