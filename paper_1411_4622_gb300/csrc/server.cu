@@ -10,8 +10,9 @@
 // and statistics out), compacts the arrays, and admits waiting requests as
 // slots and device memory allow: a new chain is set up (sinogram and image
 // copied in, resync, Eq. (8)) while the other chains of its class are between
-// ticks, and classes run on their own streams so their work overlaps.  PILA
-// tables are cached per geometry and dropped when unused and memory is needed.
+// ticks, on the stream its class runs on, and the work of different streams
+// overlaps.  PILA tables are cached per geometry and dropped when unused and
+// memory is needed.
 //
 // Classes whose tables the windowed group kernel takes (at most 512 angles,
 // K <= 8) are gathered into buckets, one per image size and table precision:
