@@ -134,11 +134,18 @@ __device__ __forceinline__ bool report_progress(const SatArgs& a, int c, int s0)
 
 constexpr int kSatMaxWarps = 8;
 constexpr int kMaxGroupWarps = 4;
-constexpr int kBatch = 8;       // moves per block of random draws
+constexpr int kBatch = 8;       // moves per block of random draws (per-move pipelined kernel)
 constexpr int kDrawRing = 3 * kBatch;  // the batch in use, the next one, and one being drawn
+// Windowed kernels: 16 moves per block when a move takes at most two Philox
+// blocks (K <= 4), so that one warp-wide pass fills every lane; 8 otherwise.
+__host__ __device__ constexpr int batch_moves(int kmax) { return kmax <= 4 ? 16 : 8; }
+__host__ __device__ constexpr int ring_slots(int kmax) { return 3 * batch_moves(kmax); }
 // Bytes of one warp's draw ring for kmax estimates: the pixel of each slot,
-// then the draw words of each slot (a multiple of 16 bytes).
-__host__ __device__ constexpr int draw_ring_bytes(int kmax) { return kDrawRing * (4 * ((kmax + 2 + 3) / 4) + 1) * 4; }
+// then the draw words of each slot (a multiple of 16 bytes; room for the
+// windowed kernels' ring, which the pipelined kernel's fits in).
+__host__ __device__ constexpr int draw_ring_bytes(int kmax) {
+    return ring_slots(kmax) * (4 * ((kmax + 2 + 3) / 4) + 1) * 4;
+}
 // Shared memory of a chain group: header, one draw ring per warp, then the
 // PILA-row stages and (when resident) the residual.
 constexpr int kPartSlots = 8;   // window sums a warp of a group publishes per window (windowed kernel)
@@ -298,12 +305,12 @@ struct PendingPixel {
     int value[3];
 };
 
-template <int KMAX>
+template <int KMAX, int BATCH = kBatch>
 __device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& G, int s, int first, uint2 key,
                                            int lane, bool late, PendingPixel& pend) {
     constexpr int kWords = draw_words<KMAX>();
     const int nblk = (a.K + 2 + 3) / 4;
-    const int units = kBatch * nblk;  // <= 72
+    const int units = BATCH * nblk;  // <= 72 (16 x 2 or 8 x 9 at most)
     const uint32_t nl = (uint32_t)a.n_list;
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
@@ -314,7 +321,7 @@ __device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& 
         const int mv = first + unit / nblk, blk = unit % nblk;
         const uint4 x = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)mv, (uint32_t)blk, kStreamSat), key);
         const bool live = unit < units && mv < a.moves;
-        const int slot = mv % kDrawRing;
+        const int slot = mv % (3 * BATCH);
         // Stored ready for the move: word 0 raw (the pixel), word 1 as
         // L = -ln N1 of Step 4, the others as the uniforms of the estimates.
         const float w0 = unit_uniform(x.x), w1 = unit_uniform(x.y);

@@ -45,6 +45,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                                                  float& S_hi, float& S_lo, unsigned long long& n_acc,
                                                  unsigned& n_ties, const int (&rowbase)[JMAX]) {
     constexpr int kWords = draw_words<KMAX>();
+    constexpr int kB = batch_moves(KMAX), kR = ring_slots(KMAX);  // moves per draw block, ring slots
     const int M = x.M;
     if (M <= 0 || a.n_list <= 0) return;
     const int nwin = (M + kWin - 1) / kWin;
@@ -54,7 +55,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         for (int j = 0; j < kWin; ++j) {
             const int mv = w * kWin + j;
             if (mv < M) {
-                const unsigned char* row = a.table + (long long)G.pix[mv % kDrawRing] * a.row_stride;
+                const unsigned char* row = a.table + (long long)G.pix[mv % kR] * a.row_stride;
                 unsigned char* st = stage_of(w, j);
 #pragma unroll
                 for (int i = 0; i < rt_chunks_per_lane<RT, JMAX>(); ++i) {
@@ -67,8 +68,8 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     };
 
     PendingPixel pend;
-    draw_batch<KMAX>(a, G, x.s, 0, x.key, x.lane, false, pend);
-    draw_batch<KMAX>(a, G, x.s, kBatch, x.key, x.lane, false, pend);
+    draw_batch<KMAX, kB>(a, G, x.s, 0, x.key, x.lane, false, pend);
+    draw_batch<KMAX, kB>(a, G, x.s, kB, x.key, x.lane, false, pend);
     __syncwarp();
     fetch_window(0);
     // Pixel values of the next window are loaded before this window's
@@ -77,7 +78,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     float fn[kWin];
 #pragma unroll
     for (int j = 0; j < kWin; ++j) {
-        pn[j] = j < M ? G.pix[j % kDrawRing] : -1;
+        pn[j] = j < M ? G.pix[j % kR] : -1;
         fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
     }
     int pw_prev[kWin];
@@ -90,9 +91,9 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     for (int w = 0; w < nwin; ++w) {
         const int m0 = w * kWin;
         __syncwarp();
-        if ((m0 & (kBatch - 1)) == 0 && m0 + 2 * kBatch < M)
-            draw_batch<KMAX>(a, G, x.s, m0 + 2 * kBatch, x.key, x.lane, true, pend);
-        if ((m0 & (kBatch - 1)) == kBatch / 2) settle_pixels(G, pend);
+        if ((m0 & (kB - 1)) == 0 && m0 + 2 * kB < M)
+            draw_batch<KMAX, kB>(a, G, x.s, m0 + 2 * kB, x.key, x.lane, true, pend);
+        if ((m0 & (kB - 1)) == kB / 2) settle_pixels(G, pend);
         if (w + 1 < nwin) fetch_window(w + 1);
         else cp_async_commit();
         // this window's pixels and loaded values; the next window's loads
@@ -104,9 +105,9 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             fc0[j] = fn[j];
             hc[j] = pc[j] >= 0 ? __ldg(a.hsum + pc[j]) : 0.0f;
             const int mv = m0 + kWin + j;
-            pn[j] = mv < M ? G.pix[mv % kDrawRing] : -1;
+            pn[j] = mv < M ? G.pix[mv % kR] : -1;
             fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
-            if (mv + kWin < M && x.lane == j) prefetch_l1(a.hsum + G.pix[(mv + kWin) % kDrawRing]);
+            if (mv + kWin < M && x.lane == j) prefetch_l1(a.hsum + G.pix[(mv + kWin) % kR]);
         }
         cp_async_wait_pending(1);  // this window's rows have landed
 
@@ -213,7 +214,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 #pragma unroll
             for (int i = 0; i < kWin; ++i)
                 if (i < j) rep[j] = rep[j] || pc[i] == pc[j];
-            const uint32_t* drw = G.draws + ((m0 + j) % kDrawRing) * kWords;
+            const uint32_t* drw = G.draws + ((m0 + j) % kR) * kWords;
             const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
 #pragma unroll
             for (int e = 0; e < KMAX; ++e) {
@@ -236,7 +237,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                         ++e;
                     }
             }
-            const uint32_t* drw = G.draws + (m % kDrawRing) * kWords;
+            const uint32_t* drw = G.draws + (m % kR) * kWords;
             float f = fpre[j];
             float fcand[KMAX], dd[KMAX];
 #pragma unroll
@@ -378,7 +379,7 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
     G.part = reinterpret_cast<float*>(gb + kPartOffset);
     G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
     G.pix = reinterpret_cast<int*>(gb + kGroupHeader);
-    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + kDrawRing * 4);
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + ring_slots(KMAX) * 4);
     G.stages = gb + group_ring_bytes(1, KMAX);
     float* rs = reinterpret_cast<float*>(G.stages + (size_t)2 * kWin * a.stage_bytes);
 
@@ -598,7 +599,7 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
     G.part = reinterpret_cast<float*>(gb + kPartOffset);
     G.flags = reinterpret_cast<volatile int*>(gb + kFlagsOffset);
     G.pix = reinterpret_cast<int*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX));
-    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX) + kDrawRing * 4);
+    G.draws = reinterpret_cast<uint32_t*>(gb + kGroupHeader + wig * draw_ring_bytes(KMAX) + ring_slots(KMAX) * 4);
     G.stages = gb + group_ring_bytes(WG, KMAX);
     float* rs = reinterpret_cast<float*>(G.stages + (size_t)2 * kWin * a.stage_bytes);  // SMEM: the band
     const int gl = lane + 32 * wig, gid = 1 + grp;
