@@ -110,6 +110,22 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// st.global.cg of v under a predicate, without a branch around it.
+__device__ __forceinline__ void stcg_if(bool pred, float* p, float v) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.global.cg.f32 [%1], %2;\n\t}" ::"r"((int)pred),
+        "l"(p), "f"(v)
+        : "memory");
+}
+
+// The same prefetch under a predicate, without a branch around it (the
+// address is not touched when pred is false).
+__device__ __forceinline__ void prefetch_l1_if(bool pred, const void* p) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q prefetch.global.L1 [%1];\n\t}" ::"r"((int)pred),
+        "l"(p));
+}
+
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -40,7 +40,9 @@ __device__ __forceinline__ void cell_share(int ki, float a0, float a1, int kj, f
 // where an FP64 evaluation could decide otherwise.
 constexpr float kTieTol = 2e-5f;
 
-template <int RT, bool SMEM, int JMAX, int KMAX, int WG = 1, bool NT = false>
+// TRACE: the chain records its moves (x.tracing); a separate build so that
+// the untraced move carries no per-move test for it.
+template <int RT, bool SMEM, int JMAX, int KMAX, int WG = 1, bool NT = false, bool TRACE = false>
 __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupShared& G, const StageCtx& x,
                                                  float& S_hi, float& S_lo, unsigned long long& n_acc,
                                                  unsigned& n_ties, const int (&rowbase)[JMAX]) {
@@ -50,18 +52,21 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     if (M <= 0 || a.n_list <= 0) return;
     const int nwin = (M + kWin - 1) / kWin;
     auto stage_of = [&](int w, int j) { return G.stages + (size_t)((w & 1) * kWin + j) * a.stage_bytes; };
+    // Rows of window w's moves into its stages, one commit group (empty past
+    // the stage's last move: the copies are predicated, not branched around;
+    // a slot past the last move may hold any value, and its row is not read).
     auto fetch_window = [&](int w) {
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
             const int mv = w * kWin + j;
-            if (mv < M) {
-                const unsigned char* row = a.table + (long long)G.pix[mv % kR] * a.row_stride;
-                unsigned char* st = stage_of(w, j);
+            const bool live = mv < M;
+            const unsigned char* row = a.table + (long long)(live ? G.pix[mv % kR] : 0) * a.row_stride;
+            unsigned char* st = stage_of(w, j);
 #pragma unroll
-                for (int i = 0; i < rt_chunks_per_lane<RT, JMAX>(); ++i) {
-                    const int q = x.gl + 32 * WG * i;
-                    cp_async_16_pred(q < a.row_chunks, st + 16 * q, row + 16 * (q < a.row_chunks ? q : 0));
-                }
+            for (int i = 0; i < rt_chunks_per_lane<RT, JMAX>(); ++i) {
+                const int q = x.gl + 32 * WG * i;
+                const bool in = live && q < a.row_chunks;
+                cp_async_16_pred(in, st + 16 * q, row + 16 * (in ? q : 0));
             }
         }
         cp_async_commit();
@@ -94,8 +99,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         if ((m0 & (kB - 1)) == 0 && m0 + 2 * kB < M)
             draw_batch<KMAX, kB>(a, G, x.s, m0 + 2 * kB, x.key, x.lane, true, pend);
         if ((m0 & (kB - 1)) == kB / 2) settle_pixels(G, pend);
-        if (w + 1 < nwin) fetch_window(w + 1);
-        else cp_async_commit();
+        fetch_window(w + 1);  // an empty group after the last window
         // this window's pixels and loaded values; the next window's loads
         int pc[kWin];
         float fc0[kWin], hc[kWin];
@@ -107,7 +111,8 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             const int mv = m0 + kWin + j;
             pn[j] = mv < M ? G.pix[mv % kR] : -1;
             fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
-            if (mv + kWin < M && x.lane == j) prefetch_l1(a.hsum + G.pix[(mv + kWin) % kR]);
+            const bool pf = mv + kWin < M && x.lane == j;
+            prefetch_l1_if(pf, a.hsum + (pf ? G.pix[(mv + kWin) % kR] : 0));
         }
         cp_async_wait_pending(1);  // this window's rows have landed
 
@@ -306,7 +311,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             }
             df[j] = accept ? fcand[0] - f : 0.0f;
             fnew[j] = accept ? fcand[0] : f;
-            if (x.tracing && live && x.gl == 0) {
+            if (TRACE && live && x.gl == 0) {
                 const float C = sqrtf(fmaxf(0.0f, S_hi * a.inv_BU));
                 const float Cp = sqrtf(fmaxf(0.0f, fmaf(C, C, xs)));
                 const float den = Cp + C;
@@ -359,7 +364,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                     __stcg(x.R + resid_cell(rowbase[s], k[j][s] + 1, x.il), fmaf(df[j], l1[j][s], c1));
                 }
             }
-            if (pc[j] >= 0) __stcg(x.img + pc[j], fnew[j]);
+            stcg_if(pc[j] >= 0, x.img + (pc[j] >= 0 ? pc[j] : 0), fnew[j]);  // no store past the last move
         }
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
@@ -528,7 +533,8 @@ __device__ __forceinline__ void window_warp(const SatArgs& a, unsigned char* gb,
         for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
             x.s = s_base + s;
             x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<RT, SMEM, JMAX, KMAX, 1, NT>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
+            if (x.tracing) run_stage_window<RT, SMEM, JMAX, KMAX, 1, NT, true>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
+            else run_stage_window<RT, SMEM, JMAX, KMAX, 1, NT, false>(a, G, x, S_hi, S_lo, n_acc, n_ties, rowbase);
             if (a.sweep_cost && lane == 0)
                 a.sweep_cost[(long long)c * a.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * a.inv_BU_d);
         }
@@ -694,7 +700,8 @@ __device__ __forceinline__ void window_group(const SatArgs& a, unsigned char* gb
         for (int s = s0; s < s1 && s_base + s < s_total; ++s) {
             x.s = s_base + s;
             x.T = (float)stage_temperature(sched, T0, TN, x.s, s_total);
-            run_stage_window<RT, SMEM, JMAX, KMAX, WG, NT>(ca, G, x, S_hi, S_lo, n_acc, n_ties, rb);
+            if (x.tracing) run_stage_window<RT, SMEM, JMAX, KMAX, WG, NT, true>(ca, G, x, S_hi, S_lo, n_acc, n_ties, rb);
+            else run_stage_window<RT, SMEM, JMAX, KMAX, WG, NT, false>(ca, G, x, S_hi, S_lo, n_acc, n_ties, rb);
             if (ca.sweep_cost && gl == 0)
                 ca.sweep_cost[(long long)ci * ca.n_sweeps_total + s] = sqrt(((double)S_hi - (double)S_lo) * ca.inv_BU_d);
         }
