@@ -138,8 +138,10 @@ constexpr int kBatch = 8;       // moves per block of random draws (per-move pip
 constexpr int kDrawRing = 3 * kBatch;  // the batch in use, the next one, and one being drawn
 // Windowed kernels: 16 moves per block when a move takes at most two Philox
 // blocks (K <= 4), so that one warp-wide pass fills every lane; 8 otherwise.
+// Their ring holds 4 blocks (a power of two, so that a move's slot is one
+// AND): the block in use, the next one, one being drawn, one spare.
 __host__ __device__ constexpr int batch_moves(int kmax) { return kmax <= 4 ? 16 : 8; }
-__host__ __device__ constexpr int ring_slots(int kmax) { return 3 * batch_moves(kmax); }
+__host__ __device__ constexpr int ring_slots(int kmax) { return 4 * batch_moves(kmax); }
 // Bytes of one warp's draw ring for kmax estimates: the pixel of each slot,
 // then the draw words of each slot (a multiple of 16 bytes; room for the
 // windowed kernels' ring, which the pipelined kernel's fits in).
@@ -305,7 +307,7 @@ struct PendingPixel {
     int value[3];
 };
 
-template <int KMAX, int BATCH = kBatch>
+template <int KMAX, int BATCH = kBatch, int RING = kDrawRing>
 __device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& G, int s, int first, uint2 key,
                                            int lane, bool late, PendingPixel& pend) {
     constexpr int kWords = draw_words<KMAX>();
@@ -321,7 +323,7 @@ __device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& 
         const int mv = first + unit / nblk, blk = unit % nblk;
         const uint4 x = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)mv, (uint32_t)blk, kStreamSat), key);
         const bool live = unit < units && mv < a.moves;
-        const int slot = mv % (3 * BATCH);
+        const int slot = (RING & (RING - 1)) == 0 ? (mv & (RING - 1)) : mv % RING;
         // Stored ready for the move: word 0 raw (the pixel), word 1 as
         // L = -ln N1 of Step 4, the others as the uniforms of the estimates.
         const float w0 = unit_uniform(x.x), w1 = unit_uniform(x.y);

@@ -47,7 +47,8 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                                                  float& S_hi, float& S_lo, unsigned long long& n_acc,
                                                  unsigned& n_ties, const int (&rowbase)[JMAX]) {
     constexpr int kWords = draw_words<KMAX>();
-    constexpr int kB = batch_moves(KMAX), kR = ring_slots(KMAX);  // moves per draw block, ring slots
+    constexpr int kB = batch_moves(KMAX), kR = ring_slots(KMAX);  // moves per draw block, ring slots (2^k)
+    static_assert((kR & (kR - 1)) == 0, "the draw ring is a power of two");
     const int M = x.M;
     if (M <= 0 || a.n_list <= 0) return;
     const int nwin = (M + kWin - 1) / kWin;
@@ -60,7 +61,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         for (int j = 0; j < kWin; ++j) {
             const int mv = w * kWin + j;
             const bool live = mv < M;
-            const unsigned char* row = a.table + (long long)(live ? G.pix[mv % kR] : 0) * a.row_stride;
+            const unsigned char* row = a.table + (long long)(live ? G.pix[mv & (kR - 1)] : 0) * a.row_stride;
             unsigned char* st = stage_of(w, j);
 #pragma unroll
             for (int i = 0; i < rt_chunks_per_lane<RT, JMAX>(); ++i) {
@@ -73,8 +74,8 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     };
 
     PendingPixel pend;
-    draw_batch<KMAX, kB>(a, G, x.s, 0, x.key, x.lane, false, pend);
-    draw_batch<KMAX, kB>(a, G, x.s, kB, x.key, x.lane, false, pend);
+    draw_batch<KMAX, kB, kR>(a, G, x.s, 0, x.key, x.lane, false, pend);
+    draw_batch<KMAX, kB, kR>(a, G, x.s, kB, x.key, x.lane, false, pend);
     __syncwarp();
     fetch_window(0);
     // Pixel values of the next window are loaded before this window's
@@ -83,7 +84,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     float fn[kWin];
 #pragma unroll
     for (int j = 0; j < kWin; ++j) {
-        pn[j] = j < M ? G.pix[j % kR] : -1;
+        pn[j] = j < M ? G.pix[j & (kR - 1)] : -1;
         fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
     }
     int pw_prev[kWin];
@@ -97,7 +98,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         const int m0 = w * kWin;
         __syncwarp();
         if ((m0 & (kB - 1)) == 0 && m0 + 2 * kB < M)
-            draw_batch<KMAX, kB>(a, G, x.s, m0 + 2 * kB, x.key, x.lane, true, pend);
+            draw_batch<KMAX, kB, kR>(a, G, x.s, m0 + 2 * kB, x.key, x.lane, true, pend);
         if ((m0 & (kB - 1)) == kB / 2) settle_pixels(G, pend);
         fetch_window(w + 1);  // an empty group after the last window
         // this window's pixels and loaded values; the next window's loads
@@ -109,10 +110,10 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             fc0[j] = fn[j];
             hc[j] = pc[j] >= 0 ? __ldg(a.hsum + pc[j]) : 0.0f;
             const int mv = m0 + kWin + j;
-            pn[j] = mv < M ? G.pix[mv % kR] : -1;
+            pn[j] = mv < M ? G.pix[mv & (kR - 1)] : -1;
             fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
             const bool pf = mv + kWin < M && x.lane == j;
-            prefetch_l1_if(pf, a.hsum + (pf ? G.pix[(mv + kWin) % kR] : 0));
+            prefetch_l1_if(pf, a.hsum + (pf ? G.pix[(mv + kWin) & (kR - 1)] : 0));
         }
         cp_async_wait_pending(1);  // this window's rows have landed
 
@@ -219,7 +220,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
 #pragma unroll
             for (int i = 0; i < kWin; ++i)
                 if (i < j) rep[j] = rep[j] || pc[i] == pc[j];
-            const uint32_t* drw = G.draws + ((m0 + j) % kR) * kWords;
+            const uint32_t* drw = G.draws + ((m0 + j) & (kR - 1)) * kWords;
             const float lo = fmaxf(0.0f, f - a.beta), span = fminf(a.beta, f + a.beta) - lo;
 #pragma unroll
             for (int e = 0; e < KMAX; ++e) {
@@ -242,7 +243,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                         ++e;
                     }
             }
-            const uint32_t* drw = G.draws + (m % kR) * kWords;
+            const uint32_t* drw = G.draws + (m & (kR - 1)) * kWords;
             float f = fpre[j];
             float fcand[KMAX], dd[KMAX];
 #pragma unroll
