@@ -96,10 +96,16 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     }
     for (int w = 0; w < nwin; ++w) {
         const int m0 = w * kWin;
-        __syncwarp();
-        if ((m0 & (kB - 1)) == 0 && m0 + 2 * kB < M)
+        // the draws and pixels written here are read a block later or more,
+        // by every lane: each write is followed by a warp barrier
+        if ((m0 & (kB - 1)) == 0 && m0 + 2 * kB < M) {
             draw_batch<KMAX, kB, kR>(a, G, x.s, m0 + 2 * kB, x.key, x.lane, true, pend);
-        if ((m0 & (kB - 1)) == kB / 2) settle_pixels(G, pend);
+            __syncwarp();
+        }
+        if ((m0 & (kB - 1)) == kB / 2) {
+            settle_pixels(G, pend);
+            __syncwarp();
+        }
         fetch_window(w + 1);  // an empty group after the last window
         // this window's pixels and loaded values; the next window's loads
         int pc[kWin];
