@@ -29,9 +29,10 @@ struct satpila_pila {
     int band_lo = 0, band_hi = 0;
     // Ray-major index of the table, read by the ray-driven projector: the
     // entries of ray (u, k) are d_ray_ent[d_ray_off[u*B + k] .. d_ray_off[u*B + k + 1]),
-    // each {pixel, the stored length decoded to float32 bits}, ascending pixel
-    // (rays longer than the sort's capacity keep their build order).  NULL
-    // when not built (the pixel-driven projector is used instead).
+    // each {pixel, the stored length l as (significand of l with its hidden
+    // bit) << 7 | biased exponent of l}, ascending pixel (rays longer than the
+    // sort's capacity keep their build order).  NULL when not built (the
+    // pixel-driven projector is used instead).
     uint32_t* d_ray_off = nullptr;  // [U*B + 1]
     uint2* d_ray_ent = nullptr;     // [entries]
     int64_t ray_bytes = 0;

@@ -387,21 +387,37 @@ __device__ __forceinline__ long long fixed_term_bits(uint32_t bf, uint32_t bl, i
     return (bf >> 31) ? -(long long)v : (long long)v;
 }
 
+__device__ __forceinline__ long long fixed_term(float f, float l, int F) {
+    return fixed_term_bits(__float_as_uint(f), __float_as_uint(l), F - 300);
+}
+
+// The two forms above for a length in the ray index's packed form y = ml << 7
+// | el (ml its 24-bit significand, el its biased exponent): the product of the
+// significands comes out already shifted by 15, from (mf << 8) * (ml << 7).
+__device__ __forceinline__ long long fixed_term_packed(uint32_t bf, uint32_t y, int ebias) {
+    const uint32_t ef = (bf >> 23) & 0xffu;
+    const uint32_t mf8 = ((bf << 8) & 0x7fffff00u) | (ef ? 0x80000000u : 0u);
+    const int e = (int)max(ef, 1u) + (int)(y & 0x7fu) + ebias;
+    const unsigned long long t = shr_clamp((unsigned long long)mf8 * (unsigned long long)(y & ~0x7fu), (uint32_t)(14 - e));
+    const unsigned long long v = (t + 1ull) >> 1;
+    return (bf >> 31) ? -(long long)v : (long long)v;
+}
+
 // The same term for a non-negative image value (its sign bit clear) of an
 // image whose F is at most 124: the hidden bit is set even for a zero or
 // subnormal f (ef = 0), but its exponent ef + el + ebias is then at most
 // 127 + 124 - 300 = -49 (l < 2), and a product below 2^48 times 2^-49 rounds
 // to 0, which is what the exact form gives for such f.
-__device__ __forceinline__ long long fixed_term_nonneg(uint32_t bf, uint32_t bl, int ebias) {
-    const int e = (int)(bf >> 23) + (int)(bl >> 23) + ebias;
-    const unsigned long long m =
-        (unsigned long long)((bf & 0x7fffffu) | 0x800000u) * (unsigned long long)((bl & 0x7fffffu) | 0x800000u);
-    const unsigned long long t = shr_clamp(m << 15, (uint32_t)(14 - e));
+__device__ __forceinline__ long long fixed_term_nonneg_packed(uint32_t bf, uint32_t y, int ebias) {
+    const int e = (int)(bf >> 23) + (int)(y & 0x7fu) + ebias;
+    const unsigned long long t =
+        shr_clamp((unsigned long long)((bf << 8) | 0x80000000u) * (unsigned long long)(y & ~0x7fu), (uint32_t)(14 - e));
     return (long long)((t + 1ull) >> 1);
 }
 
-__device__ __forceinline__ long long fixed_term(float f, float l, int F) {
-    return fixed_term_bits(__float_as_uint(f), __float_as_uint(l), F - 300);
+// float32 length of a packed index entry
+__device__ __forceinline__ float packed_length(uint32_t y) {
+    return __uint_as_float(((y >> 7) & 0x7fffffu) | ((y & 0x7fu) << 23));
 }
 
 // T[g][p][lane] = image (32 g + lane) at pixel p (-0 as +0: the same term),
@@ -444,12 +460,12 @@ __device__ __forceinline__ void ray_rows_sum(const ProjArgs& a, const float* T, 
             for (int j = 0; j < kRowUnroll; ++j) f[j] = __float_as_uint(T[(long long)en[j].x * 32]);
 #pragma unroll
             for (int j = 0; j < kRowUnroll; ++j)
-                acc += NONNEG ? fixed_term_nonneg(f[j], en[j].y, ebias) : fixed_term_bits(f[j], en[j].y, ebias);
+                acc += NONNEG ? fixed_term_nonneg_packed(f[j], en[j].y, ebias) : fixed_term_packed(f[j], en[j].y, ebias);
         }
         for (; e < e1; ++e) {
             const uint2 en = a.ray_ent[e];
             const uint32_t f = __float_as_uint(T[(long long)en.x * 32]);
-            acc += NONNEG ? fixed_term_nonneg(f, en.y, ebias) : fixed_term_bits(f, en.y, ebias);
+            acc += NONNEG ? fixed_term_nonneg_packed(f, en.y, ebias) : fixed_term_packed(f, en.y, ebias);
         }
         if (live) out[k] = acc;
     }
@@ -500,7 +516,7 @@ __global__ void __launch_bounds__(256) ray_cells_kernel(const ProjArgs a, int n_
     const uint32_t e1 = a.ray_off[ray + 1];
     for (uint32_t e = a.ray_off[ray] + lane; e < e1; e += 32) {
         const uint2 en = a.ray_ent[e];
-        const float l = __uint_as_float(en.y);
+        const float l = packed_length(en.y);
         const float f = factor ? (a.mask[en.x] ? l : 0.0f) : img[en.x];
         acc += fixed_term(f, l, F);
     }

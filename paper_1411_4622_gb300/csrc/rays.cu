@@ -4,7 +4,8 @@
 // forward projection (Eq. (1)) sums along rays, and with this index one warp
 // can sum a ray in registers instead of scattering pixel terms into shared
 // accumulators.  Built once per table from the records themselves, so the
-// lengths are exactly the stored (dequantised) values.
+// lengths are exactly the stored (dequantised) values (kept as significand and
+// exponent, the two parts of the exact term).
 //
 // Steps: count the entries of every ray (one thread per record), exclusive
 // scan, place the entries (per-ray cursors), then sort each ray by pixel so
@@ -145,6 +146,17 @@ __global__ void __launch_bounds__(kSortThreads) ray_sort_kernel(const uint32_t* 
         ent[e0 + i] = make_uint2((uint32_t)(key[i] >> 32), (uint32_t)key[i]);
 }
 
+// Last step: each entry's length from float32 bits to the form the
+// projector's exact terms take: its significand (hidden bit set) shifted left
+// by 7, with the biased exponent in the 7 low bits freed (a stored length is
+// at most sqrt 2, so the exponent is below 128).
+__global__ void ray_pack_kernel(uint2* ent, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t b = ent[i].y;
+    ent[i].y = (((b & 0x7fffffu) | 0x800000u) << 7) | ((b >> 23) & 0x7fu);
+}
+
 }  // namespace
 
 int build_ray_index(satpila_pila* p, cudaStream_t s, cudaMemPool_t pool) {
@@ -201,6 +213,10 @@ int build_ray_index(satpila_pila* p, cudaStream_t s, cudaMemPool_t pool) {
     }
     if (e == cudaSuccess) {
         ray_sort_kernel<<<(unsigned)rays, kSortThreads, 0, s>>>(p->d_ray_off, p->d_ray_ent);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && total > 0) {
+        ray_pack_kernel<<<(total + 255) / 256, 256, 0, s>>>(p->d_ray_ent, total);
         e = cudaGetLastError();
     }
     // `total` is read by the copy above before the call returns
