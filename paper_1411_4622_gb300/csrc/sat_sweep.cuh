@@ -311,7 +311,11 @@ template <int KMAX, int BATCH = kBatch, int RING = kDrawRing>
 __device__ __forceinline__ void draw_batch(const SatArgs& a, const GroupShared& G, int s, int first, uint2 key,
                                            int lane, bool late, PendingPixel& pend) {
     constexpr int kWords = draw_words<KMAX>();
-    const int nblk = (a.K + 2 + 3) / 4;
+    // Philox blocks per move: for the build's estimate capacity when it is at
+    // most 8 (a compile-time count, so the unit's move and block come by shifts;
+    // blocks past the call's K are drawn and never read, and a pass costs the
+    // same with them), else for the call's K.
+    const int nblk = KMAX <= 8 ? (KMAX + 2 + 3) / 4 : (a.K + 2 + 3) / 4;
     const int units = BATCH * nblk;  // <= 72 (16 x 2 or 8 x 9 at most)
     const uint32_t nl = (uint32_t)a.n_list;
 #pragma unroll
