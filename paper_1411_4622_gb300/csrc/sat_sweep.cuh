@@ -140,7 +140,7 @@ constexpr int kDrawRing = 3 * kBatch;  // the batch in use, the next one, and on
 // blocks (K <= 4), so that one warp-wide pass fills every lane; 8 otherwise.
 // Their ring holds 4 blocks (a power of two, so that a move's slot is one
 // AND): the block in use, the next one, one being drawn, one spare.
-__host__ __device__ constexpr int batch_moves(int kmax) { return kmax <= 4 ? 16 : 8; }
+__host__ __device__ constexpr int batch_moves(int kmax) { return kmax <= 4 ? 32 : 8; }
 __host__ __device__ constexpr int ring_slots(int kmax) { return 4 * batch_moves(kmax); }
 // Bytes of one warp's draw ring for kmax estimates: the pixel of each slot,
 // then the draw words of each slot (a multiple of 16 bytes; room for the
