@@ -94,6 +94,12 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         pw_prev[j] = -1;
         fw_prev[j] = 0.0f;
     }
+    // Records of the window being decided, decoded while the previous window
+    // was decided (its rows land a window ahead).
+    Recs<JMAX> rc[kWin];
+    cp_async_wait_pending(0);
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) rt_decode_stage<RT, JMAX>(stage_of(0, j), x.gl, WG, rc[j]);
     for (int w = 0; w < nwin; ++w) {
         const int m0 = w * kWin;
         // the draws and pixels written here are read a block later or more,
@@ -121,8 +127,6 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
             const bool pf = mv + kWin < M && x.lane == j;
             prefetch_l1_if(pf, a.hsum + (pf ? G.pix[(mv + kWin) & (kR - 1)] : 0));
         }
-        cp_async_wait_pending(1);  // this window's rows have landed
-
         // ---- records, residual sums and pairwise overlaps of the window ----
         int k[kWin][JMAX];
         float l0[kWin][JMAX], l1[kWin][JMAX], v0[kWin][JMAX], v1[kWin][JMAX];
@@ -131,8 +135,7 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         float red[kRed];                             // Gs_j, OV_ij, and (near-ties) sum |r l_j|
 #pragma unroll
         for (int j = 0; j < kWin; ++j) {
-            Recs<JMAX> r;
-            rt_decode_stage<RT, JMAX>(stage_of(w, j), x.gl, WG, r);
+            const Recs<JMAX>& r = rc[j];
 #pragma unroll
             for (int s = 0; s < JMAX; ++s) {
                 k[j][s] = r.k[s];
@@ -208,6 +211,11 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
                 red[e] = t;
             }
         }
+
+        // the next window's records (past the last window: stale rows, unused)
+        cp_async_wait_pending(0);
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) rt_decode_stage<RT, JMAX>(stage_of(w + 1, j), x.gl, WG, rc[j]);
 
         // ---- decisions, in move order ----
         float df[kWin], fnew[kWin];
