@@ -81,11 +81,12 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
     // Pixel values of the next window are loaded before this window's
     // writes and forwarded from them where a pixel repeats.
     int pn[kWin];
-    float fn[kWin];
+    float fn[kWin], hn[kWin];  // (and the pixels' sums of squared lengths)
 #pragma unroll
     for (int j = 0; j < kWin; ++j) {
         pn[j] = j < M ? G.pix[j & (kR - 1)] : -1;
         fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
+        hn[j] = pn[j] >= 0 ? __ldg(a.hsum + pn[j]) : 0.0f;
     }
     int pw_prev[kWin];
     float fw_prev[kWin];
@@ -120,12 +121,11 @@ __device__ __forceinline__ void run_stage_window(const SatArgs& a, const GroupSh
         for (int j = 0; j < kWin; ++j) {
             pc[j] = pn[j];
             fc0[j] = fn[j];
-            hc[j] = pc[j] >= 0 ? __ldg(a.hsum + pc[j]) : 0.0f;
+            hc[j] = hn[j];
             const int mv = m0 + kWin + j;
             pn[j] = mv < M ? G.pix[mv & (kR - 1)] : -1;
             fn[j] = pn[j] >= 0 ? __ldcg(x.img + pn[j]) : 0.0f;
-            const bool pf = mv + kWin < M && x.lane == j;
-            prefetch_l1_if(pf, a.hsum + (pf ? G.pix[(mv + kWin) & (kR - 1)] : 0));
+            hn[j] = pn[j] >= 0 ? __ldg(a.hsum + pn[j]) : 0.0f;
         }
         // ---- records, residual sums and pairwise overlaps of the window ----
         int k[kWin][JMAX];
